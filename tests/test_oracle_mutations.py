@@ -1,0 +1,84 @@
+"""Planted mistakes in the oracle must be caught by its pins.
+
+Each case swaps one oracle function for a copy with a plausible mistake (on
+the CPU, inside this process only) and checks that the corresponding pin from
+test_oracle_pins fails.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+import oracle.scheme as sch
+import synthetic as syn
+from tests.test_oracle_pins import cayley_step, dense_stencil, random_problem
+
+
+def _core_no_C2(W, U, tau):
+    p = U.shape[1]
+    I = np.eye(p)
+    C, S = W.T @ U, W.T @ W
+    M = I + (tau * tau / 4.0) * S                       # dropped -tau^2/4 C^2
+    B = np.linalg.solve(M, I)
+    return (2.0 / tau) * (I - B + (tau / 2.0) * (C @ B)), B, M
+
+
+def _core_sign(W, U, tau):
+    p = U.shape[1]
+    I = np.eye(p)
+    C, S = W.T @ U, W.T @ W
+    M = I + (tau * tau / 4.0) * (S - C @ C)
+    B = np.linalg.solve(M, I)
+    return (2.0 / tau) * (I - B - (tau / 2.0) * (C @ B)), B, M   # wrong sign
+
+
+def _core_half_tau(W, U, tau):
+    p = U.shape[1]
+    I = np.eye(p)
+    C, S = W.T @ U, W.T @ W
+    M = I + (tau * tau / 2.0) * (S - C @ C)             # tau^2/2 instead of tau^2/4
+    B = np.linalg.solve(M, I)
+    return (2.0 / tau) * (I - B + (tau / 2.0) * (C @ B)), B, M
+
+
+@pytest.mark.parametrize("mutant", [_core_no_C2, _core_sign, _core_half_tau])
+def test_core_mutants_break_cayley_pin(monkeypatch, mutant):
+    shape, lo, hi, V, H, sigma, _ = random_problem(13, (5, 4, 3), 3)
+    U = o.householder_orthonormalize(np.random.default_rng(3).standard_normal((60, 3)))
+    W = np.linalg.solve(H.toarray() + sigma * np.eye(60), U)
+    tau = o.default_tau(shape, lo, hi, V, sigma)
+    monkeypatch.setattr(sch, "core_matrices", mutant)
+    diff = np.abs(sch.scheme_step(U, W, tau) - cayley_step(U, W, tau)).max()
+    assert diff > 1e-6
+
+
+def test_stencil_factor_mutant_breaks_pointwise_pin(monkeypatch):
+    import scipy.sparse as sp
+
+    def wrong(m, h):
+        e = np.ones(m)
+        return sp.diags([-e[:-1], 2.0 * e, -e[:-1]], [-1, 0, 1], format="csr") / (h * h)
+
+    monkeypatch.setattr(sch, "_second_difference", wrong)
+    shape, lo, hi, V, H, _, _ = random_problem(0)
+    assert np.abs(H.toarray() - dense_stencil(shape, lo, hi, V)).max() > 1.0
+
+
+def test_axis_order_mutant_breaks_pointwise_pin():
+    # V laid out with z fastest instead of x fastest
+    shape, lo, hi = (5, 4, 3), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
+    V = np.random.default_rng(1).uniform(-1, 1, 60)
+    Vt = V.reshape(3, 4, 5).transpose(2, 1, 0).ravel()
+    Hm = o.hamiltonian(shape, lo, hi, Vt).toarray()
+    assert np.abs(Hm - dense_stencil(shape, lo, hi, V)).max() > 1e-3
+
+
+def test_update_sign_mutant_breaks_orthogonality():
+    P = syn.config_2d_laplace()
+    H = o.hamiltonian(P.shape, P.lo, P.hi, P.V)
+    U = o.householder_orthonormalize(syn.gaussian_block(0, P.n, P.p))
+    W = o.SourceSolver(H, 0.0).solve(U)
+    tau = o.default_tau(P.shape, P.lo, P.hi, P.V, 0.0)
+    A, B, _ = o.core_matrices(W, U, tau)
+    Ubad = U + tau * (U @ A) + tau * (W @ B)           # wrong sign on the U A term
+    assert o.orth_error(Ubad) > 1e-3
+    assert o.orth_error(o.update(U, W, A, B, tau)) < 1e-13
