@@ -1,0 +1,328 @@
+"""Throughput of the orthogonality-preserving scheme on one GB300 (per rank).
+
+One bench "step" is one time step of the scheme (Steps 1-4 of §4.1 plus the
+energy of Algorithm 1) on the 3D workload: 64^3 interior grid on [-8, 8]^3,
+V = |x|^2/2 plus 8 seeded Gaussian wells (depth U[1,5], width U[0.5,1.5]),
+p = 128 orbitals.  value = n * p * steps / second (orbital-updates/s), summed
+over ranks (each rank advances its own seeded instance: weak scaling).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64]
+                       [--impl ours|reference]
+Under torchrun (N > 1) every rank runs; rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as syn  # noqa: E402
+
+WORKLOAD = "3d_wells_64^3_p128"
+METRIC = "n*p orbital-updates/s"
+UNIT = "orbital-updates/s"
+
+# Algorithmic bytes per launch of each timed kernel group, per unit n (grid points),
+# for element size s and row width p (blocks are n x p; V is n values).
+ALGO_BYTES = {
+    "cg_apply": lambda n, p, s: n * s * (2 * p + 1),   # read P, V; write Q
+    "cg_axpy": lambda n, p, s: n * s * 6 * p,          # read W, R, P, Q; write W, R
+    "cg_dir": lambda n, p, s: n * s * 3 * p,           # read R, P; write P
+    "cg_init": lambda n, p, s: n * s * (4 * p + 1),    # read U, W, V; write R, P
+    "gram": lambda n, p, s: n * s * 2 * p,             # read U, W
+    "update": lambda n, p, s: n * s * 3 * p,           # read U, W; write U+
+    "energy": lambda n, p, s: n * s * (p + 1),         # read U, V
+}
+
+# DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# at this workload, keyed by kernel group and precision, valid for the kernel source
+# with the given SHA-1 prefix; null in the JSON line when the source has changed.
+NCU_TRAFFIC = {}
+
+
+def _sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def kernel_source_sha(group):
+    src = "stencil_cg.cu" if group.startswith("cg_") or group == "energy" else (
+        "gram.cu" if group == "gram" else "update.cu")
+    return _sha(os.path.join(ROOT, "paper_2511_06788_gb300", "csrc", src))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (median SM clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------
+# The oracle arm (CPU): the FP64 oracle as it stands, on a bounded sample
+# ----------------------------------------------------------------------------
+def oracle_sample(P, U0, p_sample, steps, warmup=0):
+    """Time `steps` oracle time steps (after `warmup`) of the workload restricted to
+    its first p_sample orbitals (Step 1 is p independent solves).  Returns
+    (orbital-updates/s, seconds, sample description)."""
+    import oracle as o
+    times = []
+    t_last = [time.perf_counter()]
+
+    def cb(n, U, W):
+        now = time.perf_counter()
+        times.append(now - t_last[0])
+        t_last[0] = now
+
+    t_last[0] = time.perf_counter()
+    o.run(P.shape, P.lo, P.hi, P.V, U0[:, :p_sample], stop="steps", max_steps=warmup + steps,
+          track_residual=False, callback=cb)
+    timed = times[warmup:]
+    secs = float(sum(timed))
+    desc = (f"{steps} time step(s) after {warmup} warm-up step(s) of the {WORKLOAD} problem "
+            f"restricted to its first {p_sample} of {P.p} orbitals (FP64 oracle: CG to 1e-13 "
+            f"for Step 1, numpy/scipy on the host)")
+    return P.n * p_sample * steps / secs, secs, desc
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    P = syn.config_3d_wells(0)
+    U0 = syn.gaussian_block(0, P.n, P.p)
+    p_sample = 8
+    v, secs, desc = oracle_sample(P, U0, p_sample, args.steps, args.warmup)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": P.n, "p": P.p, "p_sample": p_sample,
+                   "precision": "fp64", "seed": 0},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# Our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    import paper_2511_06788_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    seed = rank
+    P = syn.config_3d_wells(seed)
+    U0 = syn.gaussian_block(seed, P.n, P.p)
+    n, p = P.n, P.p
+    s_el = 4 if args.prec == "fp32" else 8
+
+    # inputs resident in HBM before timing: V and the raw U0 on the device
+    V_d = torch.from_numpy(P.V).to(dev)
+    U0_d = torch.from_numpy(U0).to(dev)
+    solver = pkg.Solver(P.shape, P.lo, P.hi, V_d, U0_d, p, prec=args.prec, stream=stream,
+                        device=True)
+    for _ in range(args.warmup):
+        solver.step(1)
+    solver.profile(True)
+    launches0 = pkg.lib().op_kernel_launches()
+    st0 = solver.stats()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        solver.step(1)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = pkg.lib().op_kernel_launches() - launches0
+    st1 = solver.stats()
+    prof = solver.profile_read()
+    solver.profile(False)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * p * args.steps * ws / (ms * 1e-3)
+
+    # roofline of the dominant kernel group (most device time in the timed region)
+    hbm, _, peak_kind = load_peaks()
+    groups = {k: v for k, v in prof.items() if k in ALGO_BYTES and v[1] > 0}
+    dom = max(groups, key=lambda k: groups[k][0])
+    tot_ms, cnt = groups[dom]
+    avg_s = tot_ms * 1e-3 / cnt
+    algo = ALGO_BYTES[dom](n, p, s_el)
+    achieved = algo / avg_s / 1e9
+    traffic = None
+    key = (dom, args.prec)
+    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_source_sha(dom):
+        traffic = NCU_TRAFFIC[key][0]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
+                "algo_bytes_per_launch": algo, "avg_launch_ms": 1e3 * avg_s,
+                "share_of_step_time": tot_ms / ms}
+    kernel_times = {k: {"ms": round(v[0], 3), "groups": v[1]} for k, v in prof.items() if v[1]}
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    e2e = None
+    if rank == 0 or ws > 1:
+        Vh = torch.from_numpy(P.V).pin_memory()
+        Uh = torch.from_numpy(U0).pin_memory()
+        Uout = torch.empty(n, p, dtype=torch.float64).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        with pkg.Solver(P.shape, P.lo, P.hi, Vh.numpy(), Uh.numpy(), p, prec=args.prec,
+                        stream=stream) as s2:
+            s2.step(args.steps)
+            U_back = s2.get_U()
+        Uout.numpy()[:] = U_back
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": n * p * args.steps * ws / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": (n + n * p) * 8 / args.steps,
+               "d2h_bytes_per_step": n * p * 8 / args.steps,
+               "includes": "op_init (upload V, U0; Cholesky-QR) + steps + op_get_U"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, secs, desc = oracle_sample(P, U0, 16, 1, 0)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": desc, "seconds": secs}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "p": p, "precision": args.prec,
+                       "seed_per_rank": "rank", "l2": "inputs larger than L2 (each n x p block "
+                       f"{n * p * s_el / 1e6:.0f} MB, working set > 0.8 GB)",
+                       "cg_iters_per_step": (st1["cg_iters"] - st0["cg_iters"]) / args.steps},
+            "roofline": roofline, "kernel_ms": kernel_times, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+            "stats": {"energy": st1["energy"], "orth": st1["orth"], "err_E": st1["err_E"]},
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * opevo.h - C ABI of the GB300 orthogonality-preserving eigensolver.
+ *
+ * Method: Chu, Dai, Wang, Zhou, "An orthogonality-preserving approach for
+ * eigenvalue problems" (arXiv 2511.06788).  Given a potential V on a box, the
+ * library computes the lowest p eigenpairs of H = -1/2 Delta_h + V (problem
+ * (2.2) of §2.2, finite differences instead of the paper's finite elements)
+ * by the midpoint time stepping (4.1) of §4.1, carried out as Steps 1-4:
+ *
+ *   Step 1  W = G U,  G = (H + sigma)^-1     p independent source problems
+ *   Step 2  B = (I + tau^2/4 <W,W> - tau^2/4 <W,U><W,U>)^-1
+ *   Step 3  tau/2 A = I - B + tau/2 <W,U> B
+ *   Step 4  U <- U - tau U A + tau W B
+ *
+ * iterated by Algorithm 1 of §4.1.  <X,Y> is the inner matrix of §2.1
+ * (<X,Y>_ij = x_i . y_j).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: an op_status; no exception, abort or exit crosses the ABI.
+ *     On error, op_last_error() returns a message for the calling thread.
+ *   - Grid ordering: point (ix, iy, iz) of an nx x ny x nz interior grid has
+ *     index ix + nx*(iy + ny*iz); its coordinate on axis d is
+ *     lo[d] + (i_d + 1) h_d with h_d = (hi[d] - lo[d]) / (n_d + 1); the
+ *     boundary of the box carries zero values (Dirichlet).
+ *   - Orbital blocks are row-major n x ld (ld >= p; the p values of one grid
+ *     point are contiguous; columns p..ld-1 are padding and are kept zero).
+ *   - Host pointers are caller-owned and only read or written during the call.
+ *     Device pointers are caller-owned, must stay valid until the work queued
+ *     on `stream` has finished, and must be 16-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Kernel-level calls only enqueue work; context-level calls
+ *     synchronise the context's stream where they say so.
+ *   - Inputs and outputs in FP64 unless stated; blocks of a context in
+ *     OP_FP32 mode are stored in FP32 on the device.
+ */
+#ifndef OPEVO_H
+#define OPEVO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OP_OK = 0,
+  OP_ERR_ARG = -1,       /* invalid argument (null pointer, size, alignment, mode) */
+  OP_ERR_CUDA = -2,      /* a CUDA runtime call failed (message has the detail)   */
+  OP_ERR_NOTSPD = -3,    /* a Cholesky pivot was not positive (Step 2 matrix or Cholesky-QR) */
+  OP_ERR_DIVERGED = -4,  /* non-finite energy / residual, or energy increase beyond roundoff */
+  OP_ERR_TIMEOUT = -5,   /* a bounded device wait gave up                           */
+  OP_ERR_OOM = -6,       /* device allocation failed                               */
+  OP_ERR_STATE = -7      /* call not valid in the context's current state          */
+} op_status;
+
+typedef enum {
+  OP_FP64 = 0,           /* blocks, stencil, CG, Gram and update in FP64           */
+  OP_FP32 = 1            /* blocks, stencil, CG and update in FP32; Gram partial sums
+                            flushed to FP64; Step 2-3 core in FP64                 */
+} op_prec;
+
+typedef enum {
+  OP_STOP_RESIDUAL = 0,  /* r <= tol, r = ||H U - U Theta||_F / (||H+sigma||_G sqrt(p)) */
+  OP_STOP_ERR_E = 1,     /* Algorithm 1: |E(U^{n+1}) - E(U^n)| / |E(U^n)| <= tol   */
+  OP_STOP_STEPS = 2      /* exactly max_steps steps                               */
+} op_stop;
+
+typedef enum {
+  OP_EIG_RITZ = 0,       /* eigenvalues of Theta = U^T H U (ascending)             */
+  OP_EIG_PAPER = 1       /* eigenvalues of <GU,U>^-1 minus sigma (error measures of §5) */
+} op_eig_kind;
+
+/* Problem description (the data of problem (2.2) plus the scheme's parameters). */
+typedef struct {
+  int dim;               /* 2 or 3                                                  */
+  int shape[3];          /* interior points per axis (shape[2] ignored for dim 2)   */
+  double lo[3], hi[3];   /* box                                                     */
+  int p;                 /* number of eigenpairs N (>= 1)                           */
+  double sigma;          /* shift of G = (H+sigma)^-1; NaN: max(0, 1 - L) with L =
+                            sum_d (2/h_d^2) sin^2(pi/(2(n_d+1))) + min V            */
+  double tau;            /* uniform time step; NaN: 1.5 (L + sigma)                 */
+  int prec;              /* op_prec                                                 */
+  double cg_rtol;        /* Step-1 CG: relative residual per column; <= 0 selects
+                            max(floor, min(1e-2, 0.1 g)) with g the relative
+                            G-residual sqrt(g_residual / tr<W,W>) of the previous
+                            step, floor 1e-13 (FP64) or 1e-6 (FP32)                 */
+  int cg_max_iter;       /* Step-1 CG iteration cap per step (<= 0: 2000)           */
+  int check_every;       /* op_solve: residual evaluated every this many steps (<= 0: 10) */
+} op_problem;
+
+/* Per-context statistics, filled by op_step / op_solve. */
+typedef struct {
+  int steps;             /* time steps taken since op_init                         */
+  int last_cg_iters;     /* CG iterations of the last step                          */
+  long long cg_iters;    /* CG iterations since op_init                             */
+  double energy;         /* E(U) = 1/2 tr(U^T H U) of the current U (unshifted)     */
+  double err_E;          /* |E(U^n) - E(U^{n-1})| / |E(U^{n-1})| of the last step   */
+  double residual;       /* last evaluated r (see OP_STOP_RESIDUAL), NaN if none    */
+  double g_residual;     /* tr(<W,W>) - ||<W,U>||_F^2 of the last step (G-residual^2) */
+  double orth;           /* ||<U,U> - I||_F of the U entering the last step         */
+  double sigma, tau;     /* parameters in use                                       */
+  double ms;             /* wall time of the last op_step / op_solve call (ms)      */
+} op_stats;
+
+typedef struct op_ctx op_ctx;
+
+/* ---------------------------------------------------------------------------
+ * Context-level API (problem statement (2.2); scheme (4.1); Algorithm 1)
+ * ------------------------------------------------------------------------- */
+
+/* Library version string (static storage). */
+const char *op_version(void);
+
+/* Message of the last failed call on this thread ("" if none). Static per thread. */
+const char *op_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all contexts). */
+long long op_kernel_launches(void);
+
+/* Create a context: validates `pb`, allocates the device blocks (cudaMalloc on the
+ * current device; the context owns them), uploads V (n FP64 values, host) and the
+ * raw initial block U0 (n x p FP64, host, row-major, ld = p), and orthonormalises
+ * U0 by Cholesky-QR in FP64 on the device (§5 starts from random orthonormal data).
+ * All work is queued on `stream` and the call synchronises it before returning.
+ * On error *ctx is NULL. */
+op_status op_init(op_ctx **ctx, const op_problem *pb, const double *V, const double *U0,
+                  void *stream);
+
+/* As op_init, but V (n FP64) and U0 (n x p FP64, ld = p) are device pointers. */
+op_status op_init_device(op_ctx **ctx, const op_problem *pb, const double *V_dev,
+                         const double *U0_dev, void *stream);
+
+/* Advance `nsteps` time steps (Steps 1-4 each, §4.1), updating the energy every step.
+ * Synchronises the stream at least once per step (Step-1 CG convergence checks).
+ * `st` may be NULL. */
+op_status op_step(op_ctx *ctx, int nsteps, op_stats *st);
+
+/* Algorithm 1: step until the stop rule `stop` (op_stop) holds for `tol`, or
+ * `max_steps` steps.  The residual is evaluated every pb->check_every steps and at
+ * the end.  Returns OP_OK when the rule holds (or after max_steps for OP_STOP_STEPS),
+ * OP_ERR_STATE if max_steps ran out first.  `st` may be NULL. */
+op_status op_solve(op_ctx *ctx, double tol, int max_steps, int stop, op_stats *st);
+
+/* E(U) = 1/2 tr(U^T H U) (§2.2) of the current U, unshifted H. Synchronises. */
+op_status op_energy(op_ctx *ctx, double *E);
+
+/* r of the current U (see OP_STOP_RESIDUAL); also sets stats.residual. Synchronises. */
+op_status op_residual(op_ctx *ctx, double *r);
+
+/* Copy the current U (n x p, FP64, ld = p) into caller-owned host memory. Synchronises. */
+op_status op_get_U(op_ctx *ctx, double *U_host);
+
+/* p eigenvalue estimates, ascending, into caller-owned host memory (kind: op_eig_kind).
+ * OP_EIG_PAPER runs one extra Step-1 solve for the current U. Synchronises. */
+op_status op_eigenvalues(op_ctx *ctx, double *lam, int kind);
+
+/* Current statistics (no device work). */
+op_status op_get_stats(op_ctx *ctx, op_stats *st);
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around each
+ * launch group of a step (kinds: op_profile_name(0 .. op_profile_kinds()-1)).
+ * Enabling (or disabling) synchronises the stream and resets the totals. */
+op_status op_profile_enable(op_ctx *ctx, int enable);
+int op_profile_kinds(void);
+const char *op_profile_name(int kind);  /* static storage; "" for an unknown kind */
+/* Total device time (ms) and number of timed launch groups of `kind` since enabling. */
+op_status op_profile_read(op_ctx *ctx, int kind, double *total_ms, long long *launches);
+
+/* Free the context's device memory. NULL is allowed. */
+void op_destroy(op_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Kernel-level API: single steps of the path on caller-owned device buffers.
+ * `prec` selects the element type T of the blocks: double (OP_FP64) or float
+ * (OP_FP32).  Blocks are n x ld, ld >= p, ld a multiple of 8.
+ * ------------------------------------------------------------------------- */
+
+/* Y = (H + sigma) X: the 5-point (2D) / 7-point (3D) stencil of -1/2 Delta_h plus
+ * diag(V + sigma) (the operator of the source problems of Step 1).
+ * Geometry, p and T (pb->prec) come from pb; V_t: n values of V in T (device);
+ * X, Y: n x ld blocks of T (device, must not alias). */
+op_status op_apply_H(const op_problem *pb, int ld, const void *V_t, double sigma,
+                     const void *X, void *Y, void *stream);
+
+/* Step 1: W = (H + sigma)^-1 U by p independent conjugate-gradient solves, warm-started
+ * from the W passed in, each column to ||u - (H+sigma) w|| <= rtol ||u||, at most
+ * max_iter iterations.  V_t as in op_apply_H; U, W: n x ld blocks of T.  Scratch: ws
+ * (device) of at least op_cg_workspace() bytes.  *iters (host) receives the iteration
+ * count.  Synchronises `stream` once per iteration (convergence checks). */
+op_status op_cg_solve(const op_problem *pb, int ld, const void *V_t, double sigma,
+                      const void *U, void *W, double rtol, int max_iter, void *ws,
+                      size_t ws_bytes, int *iters, void *stream);
+size_t op_cg_workspace(const op_problem *pb, int ld);
+
+/* Inner matrices of [U W] (§2.1): C = <W,U> (C_ij = w_i . u_j), S = <W,W>, D = <U,U>,
+ * each ld x ld FP64 row-major on the device (entries with i or j >= p are zero).
+ * Any of C, S, D may be NULL to skip it.  Partial sums over grid-point chunks are
+ * accumulated in FP64.  ws: device scratch of at least op_gram_workspace() bytes. */
+op_status op_gram(int prec, long long n, int p, int ld, const void *U, const void *W,
+                  double *C, double *S, double *D, void *ws, size_t ws_bytes, void *stream);
+size_t op_gram_workspace(int prec, long long n, int ld);
+
+/* Steps 2-3 of §4.1 in FP64: from C = <W,U>, S = <W,W> (ld x ld device, FP64) form
+ * M = I + tau^2/4 (S - C C) (symmetrised), B = M^-1 by Cholesky, A from Step 3,
+ * and the Step-4 coefficients KU = I - tau A = 2B - I - tau C B, KW = tau B
+ * (ld x ld FP64 device, zero outside p x p).  KU_t / KW_t (may be NULL) receive the
+ * same matrices in the block type of `prec`.  ws: at least op_core_workspace() bytes.
+ * A non-positive Cholesky pivot is reported by the next synchronising call on the
+ * same workspace via op_core_status(). */
+op_status op_core(int prec, int p, int ld, double tau, const double *C, const double *S,
+                  double *KU, double *KW, void *KU_t, void *KW_t, void *ws, size_t ws_bytes,
+                  void *stream);
+size_t op_core_workspace(int p, int ld);
+/* Synchronises `stream`; returns OP_ERR_NOTSPD if the last op_core on ws failed. */
+op_status op_core_status(void *ws, void *stream);
+
+/* Step 4: Unew = U KU + W KW (KU, KW: ld x ld in the block type T, device).
+ * Unew must not alias U or W. */
+op_status op_update(int prec, long long n, int p, int ld, const void *U, const void *W,
+                    const void *KU_t, const void *KW_t, void *Unew, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OPEVO_H */

@@ -1,0 +1,327 @@
+"""ctypes binding of the opevo C ABI (include/opevo.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  Device
+buffers for the kernel-level calls are torch CUDA tensors (PyTorch provides
+device memory and streams); host buffers are numpy arrays.  The binding fails
+loudly when ``libopevo.so`` is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libopevo.so")
+
+OP_OK, OP_ERR_ARG, OP_ERR_CUDA, OP_ERR_NOTSPD, OP_ERR_DIVERGED, OP_ERR_TIMEOUT, OP_ERR_OOM, \
+    OP_ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+OP_FP64, OP_FP32 = 0, 1
+OP_STOP_RESIDUAL, OP_STOP_ERR_E, OP_STOP_STEPS = 0, 1, 2
+OP_EIG_RITZ, OP_EIG_PAPER = 0, 1
+PRECS = {"fp64": OP_FP64, "fp32": OP_FP32}
+STATUS_NAMES = {0: "OP_OK", -1: "OP_ERR_ARG", -2: "OP_ERR_CUDA", -3: "OP_ERR_NOTSPD",
+                -4: "OP_ERR_DIVERGED", -5: "OP_ERR_TIMEOUT", -6: "OP_ERR_OOM",
+                -7: "OP_ERR_STATE"}
+
+
+class OpProblem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("shape", C.c_int * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("p", C.c_int), ("sigma", C.c_double),
+                ("tau", C.c_double), ("prec", C.c_int), ("cg_rtol", C.c_double),
+                ("cg_max_iter", C.c_int), ("check_every", C.c_int)]
+
+
+class OpStats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("last_cg_iters", C.c_int), ("cg_iters", C.c_longlong),
+                ("energy", C.c_double), ("err_E", C.c_double), ("residual", C.c_double),
+                ("g_residual", C.c_double), ("orth", C.c_double), ("sigma", C.c_double),
+                ("tau", C.c_double), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class OpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libopevo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    vp, sz, i32, f64 = C.c_void_p, C.c_size_t, C.c_int, C.c_double
+    P = C.POINTER
+    sigs = {
+        "op_version": (C.c_char_p, []),
+        "op_last_error": (C.c_char_p, []),
+        "op_kernel_launches": (C.c_longlong, []),
+        "op_init": (i32, [P(vp), P(OpProblem), P(f64), P(f64), vp]),
+        "op_init_device": (i32, [P(vp), P(OpProblem), vp, vp, vp]),
+        "op_step": (i32, [vp, i32, P(OpStats)]),
+        "op_solve": (i32, [vp, f64, i32, i32, P(OpStats)]),
+        "op_energy": (i32, [vp, P(f64)]),
+        "op_residual": (i32, [vp, P(f64)]),
+        "op_get_U": (i32, [vp, P(f64)]),
+        "op_eigenvalues": (i32, [vp, P(f64), i32]),
+        "op_get_stats": (i32, [vp, P(OpStats)]),
+        "op_profile_enable": (i32, [vp, i32]),
+        "op_profile_kinds": (i32, []),
+        "op_profile_name": (C.c_char_p, [i32]),
+        "op_profile_read": (i32, [vp, i32, P(f64), P(C.c_longlong)]),
+        "op_destroy": (None, [vp]),
+        "op_apply_H": (i32, [P(OpProblem), i32, vp, f64, vp, vp, vp]),
+        "op_cg_solve": (i32, [P(OpProblem), i32, vp, f64, vp, vp, f64, i32, vp, sz, P(i32), vp]),
+        "op_cg_workspace": (sz, [P(OpProblem), i32]),
+        "op_gram": (i32, [i32, C.c_longlong, i32, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
+        "op_gram_workspace": (sz, [i32, C.c_longlong, i32]),
+        "op_core": (i32, [i32, i32, i32, f64, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+        "op_core_workspace": (sz, [i32, i32]),
+        "op_core_status": (i32, [vp, vp]),
+        "op_update": (i32, [i32, C.c_longlong, i32, i32, vp, vp, vp, vp, vp, vp]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status: int):
+    if status != OP_OK:
+        raise OpError(status, lib().op_last_error().decode())
+
+
+def last_error() -> str:
+    return lib().op_last_error().decode()
+
+
+def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol=0.0,
+                 cg_max_iter=0, check_every=0) -> OpProblem:
+    pb = OpProblem()
+    dim = len(shape)
+    pb.dim = dim
+    for d in range(3):
+        pb.shape[d] = int(shape[d]) if d < dim else 1
+        pb.lo[d] = float(lo[d]) if d < dim else 0.0
+        pb.hi[d] = float(hi[d]) if d < dim else 1.0
+    pb.p = int(p)
+    pb.sigma = math.nan if sigma is None else float(sigma)
+    pb.tau = math.nan if tau is None else float(tau)
+    pb.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
+    pb.cg_rtol = float(cg_rtol)
+    pb.cg_max_iter = int(cg_max_iter)
+    pb.check_every = int(check_every)
+    return pb
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class Solver:
+    """A solver context (op_init ... op_destroy) for one eigenproblem."""
+
+    def __init__(self, shape, lo, hi, V, U0, p, *, prec="fp64", sigma=None, tau=None,
+                 cg_rtol=0.0, cg_max_iter=0, check_every=0, stream=None, device=False):
+        self.pb = make_problem(shape, lo, hi, p, prec=prec, sigma=sigma, tau=tau,
+                               cg_rtol=cg_rtol, cg_max_iter=cg_max_iter, check_every=check_every)
+        self.n = int(np.prod(shape))
+        self.p = int(p)
+        self._ctx = C.c_void_p()
+        L = lib()
+        st = _stream_ptr(stream)
+        if device:
+            # V, U0: torch CUDA tensors (float64, contiguous)
+            check(L.op_init_device(C.byref(self._ctx), C.byref(self.pb),
+                                   C.c_void_p(V.data_ptr()), C.c_void_p(U0.data_ptr()), st))
+        else:
+            V = np.ascontiguousarray(V, dtype=np.float64)
+            U0 = np.ascontiguousarray(U0, dtype=np.float64)
+            assert V.shape == (self.n,) and U0.shape == (self.n, self.p)
+            check(L.op_init(C.byref(self._ctx), C.byref(self.pb), _dptr(V), _dptr(U0), st))
+
+    def close(self):
+        if self._ctx:
+            lib().op_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, nsteps=1) -> dict:
+        st = OpStats()
+        check(lib().op_step(self._ctx, int(nsteps), C.byref(st)))
+        return st.as_dict()
+
+    def solve(self, tol, max_steps, stop=OP_STOP_RESIDUAL, raise_on_max=True) -> dict:
+        st = OpStats()
+        s = lib().op_solve(self._ctx, float(tol), int(max_steps), int(stop), C.byref(st))
+        if s != OP_OK and (raise_on_max or s != OP_ERR_STATE):
+            check(s)
+        d = st.as_dict()
+        d["converged"] = s == OP_OK
+        return d
+
+    def stats(self) -> dict:
+        st = OpStats()
+        check(lib().op_get_stats(self._ctx, C.byref(st)))
+        return st.as_dict()
+
+    def energy(self) -> float:
+        e = C.c_double()
+        check(lib().op_energy(self._ctx, C.byref(e)))
+        return e.value
+
+    def residual(self) -> float:
+        r = C.c_double()
+        check(lib().op_residual(self._ctx, C.byref(r)))
+        return r.value
+
+    def get_U(self) -> np.ndarray:
+        U = np.empty((self.n, self.p))
+        check(lib().op_get_U(self._ctx, _dptr(U)))
+        return U
+
+    def profile(self, enable=True):
+        """Enable (and reset) or disable per-kernel event timing."""
+        check(lib().op_profile_enable(self._ctx, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        """{kernel group: (total device ms, timed launch groups)} since enabling."""
+        L = lib()
+        out = {}
+        for k in range(L.op_profile_kinds()):
+            ms, cnt = C.c_double(), C.c_longlong()
+            check(L.op_profile_read(self._ctx, k, C.byref(ms), C.byref(cnt)))
+            out[L.op_profile_name(k).decode()] = (ms.value, cnt.value)
+        return out
+
+    def eigenvalues(self, kind=OP_EIG_RITZ) -> np.ndarray:
+        lam = np.empty(self.p)
+        check(lib().op_eigenvalues(self._ctx, _dptr(lam), int(kind)))
+        return lam
+
+
+# ----------------------------------------------------------------------------
+# Kernel-level calls on torch CUDA tensors
+# ----------------------------------------------------------------------------
+def _tptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _prec_of(t):
+    import torch
+    if t.dtype == torch.float64:
+        return OP_FP64
+    if t.dtype == torch.float32:
+        return OP_FP32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def apply_H(shape, lo, hi, V_t, sigma, X, Y=None, stream=None):
+    """Y = (H + sigma) X for an n x ld block X (torch CUDA, float32/float64)."""
+    import torch
+    n, ld = X.shape
+    prec = _prec_of(X)
+    pb = make_problem(shape, lo, hi, ld, prec=prec)
+    if Y is None:
+        Y = torch.empty_like(X)
+    check(lib().op_apply_H(C.byref(pb), ld, _tptr(V_t), float(sigma), _tptr(X), _tptr(Y),
+                           _stream_ptr(stream)))
+    return Y
+
+
+def cg_solve(shape, lo, hi, V_t, sigma, U, W, p, rtol, max_iter=5000, stream=None):
+    import torch
+    n, ld = U.shape
+    prec = _prec_of(U)
+    pb = make_problem(shape, lo, hi, p, prec=prec)
+    nbytes = lib().op_cg_workspace(C.byref(pb), ld)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=U.device)
+    it = C.c_int()
+    check(lib().op_cg_solve(C.byref(pb), ld, _tptr(V_t), float(sigma), _tptr(U), _tptr(W),
+                            float(rtol), int(max_iter), _tptr(ws), nbytes, C.byref(it),
+                            _stream_ptr(stream)))
+    return it.value
+
+
+def gram(U, W, p, want=("C", "S", "D"), stream=None):
+    """(C, S, D) = (<W,U>, <W,W>, <U,U>) as ld x ld float64 CUDA tensors."""
+    import torch
+    n, ld = U.shape
+    prec = _prec_of(U)
+    out = {k: (torch.empty(ld, ld, dtype=torch.float64, device=U.device) if k in want else None)
+           for k in ("C", "S", "D")}
+    nbytes = lib().op_gram_workspace(prec, n, ld)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=U.device)
+    check(lib().op_gram(prec, n, p, ld, _tptr(U), _tptr(W), _tptr(out["C"]), _tptr(out["S"]),
+                        _tptr(out["D"]), _tptr(ws), nbytes, _stream_ptr(stream)))
+    return out["C"], out["S"], out["D"]
+
+
+def core(Cm, Sm, p, tau, dtype=None, stream=None):
+    """Steps 2-3: returns (KU, KW) FP64 and (KU_t, KW_t) in `dtype` (ld x ld CUDA)."""
+    import torch
+    ld = Cm.shape[0]
+    dtype = dtype or torch.float64
+    prec = OP_FP64 if dtype == torch.float64 else OP_FP32
+    KU = torch.empty(ld, ld, dtype=torch.float64, device=Cm.device)
+    KW = torch.empty_like(KU)
+    KU_t = torch.empty(ld, ld, dtype=dtype, device=Cm.device)
+    KW_t = torch.empty_like(KU_t)
+    nbytes = lib().op_core_workspace(p, ld)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=Cm.device)
+    st = _stream_ptr(stream)
+    check(lib().op_core(prec, p, ld, float(tau), _tptr(Cm), _tptr(Sm), _tptr(KU), _tptr(KW),
+                        _tptr(KU_t), _tptr(KW_t), _tptr(ws), nbytes, st))
+    check(lib().op_core_status(_tptr(ws), st))
+    return KU, KW, KU_t, KW_t
+
+
+def update(U, W, KU_t, KW_t, p, out=None, stream=None):
+    import torch
+    n, ld = U.shape
+    prec = _prec_of(U)
+    if out is None:
+        out = torch.empty_like(U)
+    check(lib().op_update(prec, n, p, ld, _tptr(U), _tptr(W), _tptr(KU_t), _tptr(KW_t),
+                          _tptr(out), _stream_ptr(stream)))
+    return out

@@ -1,0 +1,772 @@
+// C ABI of the library (include/opevo.h): validation, the per-context device
+// state and the host loop of Algorithm 1 (§4.1) over the device kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <chrono>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace opevo {
+
+static thread_local char g_err[1024] = "";
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+op_status cuda_status(cudaError_t e, const char *what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return e == cudaErrorMemoryAllocation ? OP_ERR_OOM : OP_ERR_CUDA;
+}
+
+op_status make_geom(const op_problem *pb, Geom *g) {
+  if (!pb) {
+    set_error("null problem");
+    return OP_ERR_ARG;
+  }
+  if (pb->dim != 2 && pb->dim != 3) {
+    set_error("dim must be 2 or 3 (got %d)", pb->dim);
+    return OP_ERR_ARG;
+  }
+  g->dim = pb->dim;
+  g->nx = pb->shape[0];
+  g->ny = pb->shape[1];
+  g->nz = pb->dim == 3 ? pb->shape[2] : 1;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) {
+    set_error("grid shape must be positive");
+    return OP_ERR_ARG;
+  }
+  g->n = (long long)g->nx * g->ny * g->nz;
+  g->cdiag = 0.0;
+  g->c[0] = g->c[1] = g->c[2] = 0.0;
+  for (int d = 0; d < pb->dim; ++d) {
+    const double len = pb->hi[d] - pb->lo[d];
+    if (!(len > 0.0)) {
+      set_error("box must satisfy hi > lo on every axis");
+      return OP_ERR_ARG;
+    }
+    const double h = len / (pb->shape[d] + 1);
+    g->cdiag += 1.0 / (h * h);
+    g->c[d] = 0.5 / (h * h);
+  }
+  return OP_OK;
+}
+
+// Lower bound of spec(H): sum_d (2/h_d^2) sin^2(pi / (2 (n_d + 1))) + min V.
+static double spectrum_lower_bound(const op_problem *pb, double vmin) {
+  double lap = 0.0;
+  for (int d = 0; d < pb->dim; ++d) {
+    const double h = (pb->hi[d] - pb->lo[d]) / (pb->shape[d] + 1);
+    const double s = sin(M_PI / (2.0 * (pb->shape[d] + 1)));
+    lap += 2.0 / (h * h) * s * s;
+  }
+  return lap + vmin;
+}
+
+}  // namespace opevo
+
+using namespace opevo;
+
+struct op_ctx {
+  op_problem pb;
+  Geom g;
+  long long n;
+  int p, ld, prec, elem;
+  double sigma, tau, hnorm;
+  cudaStream_t st;
+  // blocks (element type T)
+  void *U, *U2, *W, *Vt;
+  // p x p (ld x ld) FP64 matrices
+  double *C, *S, *D, *KU, *KW, *Th, *eig_work, *lam_d;
+  void *KU_t, *KW_t;
+  void *cg_ws, *gram_ws, *core_ws;
+  size_t gram_bytes;
+  CGWork cgw;
+  Prof prof;
+  double *part;  // [max_blocks][2][ld] for quad / sumsq
+  double *dsc;   // device scalars: 0..2 core stats, 4..5 quad, 6 sumsq
+  double *hsc;   // pinned mirror
+  int *hpin_int;
+  op_stats stats;
+  double E;
+  double g_rel;  // last relative G-residual sqrt(g2 / trS)
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+op_status dev_alloc(op_ctx *c, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_status(e, "cudaMalloc");
+  }
+  c->allocs.push_back(*p);
+  return OP_OK;
+}
+
+void free_all(op_ctx *c) {
+  prof_destroy(&c->prof);
+  for (void *p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  if (c->hsc) cudaFreeHost(c->hsc);
+  if (c->hpin_int) cudaFreeHost(c->hpin_int);
+  c->hsc = nullptr;
+  c->hpin_int = nullptr;
+}
+
+op_status check_problem(const op_problem *pb) {
+  if (!pb) {
+    set_error("null problem");
+    return OP_ERR_ARG;
+  }
+  if (pb->p < 1) {
+    set_error("p must be >= 1 (got %d)", pb->p);
+    return OP_ERR_ARG;
+  }
+  if (pb->prec != OP_FP64 && pb->prec != OP_FP32) {
+    set_error("unsupported precision mode %d", pb->prec);
+    return OP_ERR_ARG;
+  }
+  Geom g;
+  OP_TRY(make_geom(pb, &g));
+  if (pb->p > g.n) {
+    set_error("p (%d) exceeds the number of grid points (%lld)", pb->p, g.n);
+    return OP_ERR_ARG;
+  }
+  if (round_up(pb->p, 8) > 4096) {
+    set_error("p too large (max 4096)");
+    return OP_ERR_ARG;
+  }
+  return OP_OK;
+}
+
+double cg_rtol_for(op_ctx *c) {
+  if (c->pb.cg_rtol > 0.0) return c->pb.cg_rtol;
+  const double floor = c->prec == OP_FP64 ? 1e-13 : 1e-6;
+  double r = 0.1 * c->g_rel;
+  if (!(r < 1e-2)) r = 1e-2;
+  if (r < floor) r = floor;
+  return r;
+}
+
+int cg_max_iter(op_ctx *c) { return c->pb.cg_max_iter > 0 ? c->pb.cg_max_iter : 2000; }
+
+template <typename T> op_status energy_impl(op_ctx *c) {
+  OP_TRY(launch_quad<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, c->ld, c->part, c->dsc + 4,
+                        c->st));
+  OP_CUDA(cudaMemcpyAsync(c->hsc + 4, c->dsc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->st));
+  OP_CUDA(cudaStreamSynchronize(c->st));
+  c->E = 0.5 * c->hsc[4];
+  c->stats.energy = c->E;
+  return OP_OK;
+}
+
+template <typename T> op_status step_impl(op_ctx *c) {
+  int iters = 0;
+  // Step 1: W = (H + sigma)^-1 U, warm-started from the previous W
+  OP_TRY(cg_solve<T>(c->g, (const T *)c->Vt, c->sigma, (const T *)c->U, (T *)c->W, c->p, c->ld,
+                     cg_rtol_for(c), cg_max_iter(c), c->cgw, &iters, c->st));
+  // inner matrices <W,U>, <W,W>, <U,U>
+  prof_begin(&c->prof, PK_GRAM, c->st);
+  OP_TRY(gram<T>(c->n, c->p, c->ld, (const T *)c->U, (const T *)c->W, c->C, c->S, c->D,
+                 c->gram_ws, c->gram_bytes, c->st));
+  prof_end(&c->prof, c->st);
+  // Steps 2-3 (FP64) and the Step-4 coefficients
+  prof_begin(&c->prof, PK_CORE, c->st);
+  OP_TRY(launch_core_stats(c->p, c->ld, c->C, c->S, c->D, c->dsc, c->st));
+  OP_TRY(core<T>(c->p, c->ld, c->tau, c->C, c->S, c->KU, c->KW, (T *)c->KU_t, (T *)c->KW_t,
+                 c->core_ws, c->st));
+  prof_end(&c->prof, c->st);
+  // Step 4
+  prof_begin(&c->prof, PK_UPDATE, c->st);
+  OP_TRY(update<T>(c->n, c->ld, (const T *)c->U, (const T *)c->W, (const T *)c->KU_t,
+                   (const T *)c->KW_t, (T *)c->U2, c->st));
+  prof_end(&c->prof, c->st);
+  void *tmp = c->U;
+  c->U = c->U2;
+  c->U2 = tmp;
+  // E(U^{n+1}) for Algorithm 1's err_E
+  prof_begin(&c->prof, PK_ENERGY, c->st);
+  OP_TRY(launch_quad<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, c->ld, c->part, c->dsc + 4,
+                        c->st));
+  prof_end(&c->prof, c->st);
+  OP_CUDA(cudaMemcpyAsync(c->hsc, c->dsc, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  OP_CUDA(cudaMemcpyAsync(c->hpin_int, c->core_ws, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  OP_CUDA(cudaStreamSynchronize(c->st));
+  prof_harvest(&c->prof);
+  if (*c->hpin_int) {
+    set_error("Step 2 matrix is not positive definite (Cholesky pivot <= 0)");
+    return OP_ERR_NOTSPD;
+  }
+  const double Enew = 0.5 * c->hsc[4];
+  if (!isfinite(Enew)) {
+    set_error("non-finite energy after step %d", c->stats.steps + 1);
+    return OP_ERR_DIVERGED;
+  }
+  c->stats.err_E = fabs(Enew - c->E) / fabs(c->E);
+  c->E = Enew;
+  c->stats.energy = Enew;
+  c->stats.g_residual = c->hsc[0];
+  c->stats.orth = c->hsc[1];
+  c->g_rel = (c->hsc[2] > 0.0 && c->hsc[0] > 0.0) ? sqrt(c->hsc[0] / c->hsc[2]) : 0.0;
+  c->stats.steps += 1;
+  c->stats.last_cg_iters = iters;
+  c->stats.cg_iters += iters;
+  return OP_OK;
+}
+
+// r = ||H U - U Theta||_F / (||H + sigma||_G sqrt(p)), Theta = U^T H U.
+template <typename T> op_status residual_impl(op_ctx *c, double *r) {
+  T *Y = (T *)c->cgw.Q, *Z = (T *)c->cgw.R;
+  prof_begin(&c->prof, PK_RESIDUAL, c->st);
+  OP_TRY(launch_apply<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, Y, c->ld, c->st));
+  OP_TRY(gram<T>(c->n, c->p, c->ld, (const T *)c->U, Y, c->Th, nullptr, nullptr, c->gram_ws,
+                 c->gram_bytes, c->st));
+  OP_TRY(launch_resid_coeff<T>(c->p, c->ld, c->Th, (T *)c->KU_t, (T *)c->KW_t, c->st));
+  OP_TRY(update<T>(c->n, c->ld, (const T *)c->U, Y, (const T *)c->KU_t, (const T *)c->KW_t, Z,
+                   c->st));
+  OP_TRY(launch_sumsq<T>(c->n, c->ld, Z, c->part, c->dsc + 6, c->st));
+  prof_end(&c->prof, c->st);
+  OP_CUDA(cudaMemcpyAsync(c->hsc + 6, c->dsc + 6, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  OP_CUDA(cudaStreamSynchronize(c->st));
+  prof_harvest(&c->prof);
+  *r = sqrt(c->hsc[6]) / (c->hnorm * sqrt((double)c->p));
+  c->stats.residual = *r;
+  return OP_OK;
+}
+
+template <typename T> op_status eig_impl(op_ctx *c, double *lam, int kind) {
+  if (kind == OP_EIG_RITZ) {
+    T *Y = (T *)c->cgw.Q;
+    OP_TRY(launch_apply<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, Y, c->ld, c->st));
+    OP_TRY(gram<T>(c->n, c->p, c->ld, (const T *)c->U, Y, c->Th, nullptr, nullptr, c->gram_ws,
+                   c->gram_bytes, c->st));
+    OP_TRY(sym_eigvals(c->p, c->ld, c->Th, c->eig_work, c->lam_d, c->st));
+  } else {
+    int iters = 0;
+    const double tight = c->prec == OP_FP64 ? 1e-13 : 1e-6;
+    OP_TRY(cg_solve<T>(c->g, (const T *)c->Vt, c->sigma, (const T *)c->U, (T *)c->W, c->p, c->ld,
+                       tight, 20000, c->cgw, &iters, c->st));
+    OP_TRY(gram<T>(c->n, c->p, c->ld, (const T *)c->U, (const T *)c->W, c->Th, nullptr, nullptr,
+                   c->gram_ws, c->gram_bytes, c->st));
+    OP_TRY(sym_eigvals(c->p, c->ld, c->Th, c->eig_work, c->eig_work + (size_t)c->p * c->p,
+                       c->st));
+    OP_TRY(launch_paper_lams(c->p, c->eig_work + (size_t)c->p * c->p, c->sigma, c->lam_d, c->st));
+  }
+  OP_CUDA(cudaMemcpyAsync(lam, c->lam_d, c->p * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  OP_CUDA(cudaStreamSynchronize(c->st));
+  return OP_OK;
+}
+
+// Cholesky-QR (FP64) of the raw n x p block at U0 (device) into c->U (T).
+template <typename T> op_status orthonormalise_impl(op_ctx *c, const double *U0_dev) {
+  void *A64 = nullptr, *Q64 = nullptr, *KW64 = nullptr, *gws = nullptr;
+  const size_t blk = (size_t)c->n * c->ld * sizeof(double);
+  op_status s = OP_OK;
+  auto cleanup = [&]() {
+    for (void *p : {A64, Q64, KW64, gws}) {
+      if (!p) continue;
+      cudaFree(p);
+      for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
+        if (*it == p) {
+          c->allocs.erase(it);
+          break;
+        }
+    }
+  };
+  const size_t gbytes = gram_workspace_bytes(c->n, c->ld, 8);
+  if ((s = dev_alloc(c, &A64, blk)) || (s = dev_alloc(c, &Q64, blk)) ||
+      (s = dev_alloc(c, &KW64, (size_t)c->ld * c->ld * 8)) || (s = dev_alloc(c, &gws, gbytes))) {
+    cleanup();
+    return s;
+  }
+  cudaError_t e = cudaMemsetAsync(KW64, 0, (size_t)c->ld * c->ld * 8, c->st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_status(e, "cudaMemsetAsync");
+  }
+  if ((s = launch_pad_copy<double>(c->n, c->p, c->ld, U0_dev, (double *)A64, c->st)) ||
+      (s = gram<double>(c->n, c->p, c->ld, (const double *)A64, (const double *)A64, nullptr,
+                        nullptr, c->D, gws, gbytes, c->st)) ||
+      (s = cholqr_coeff(c->p, c->ld, c->D, c->KU, c->core_ws, c->st)) ||
+      (s = update<double>(c->n, c->ld, (const double *)A64, (const double *)A64, c->KU,
+                          (const double *)KW64, (double *)Q64, c->st))) {
+    cleanup();
+    return s;
+  }
+  if (c->prec == OP_FP64) {
+    e = cudaMemcpyAsync(c->U, Q64, blk, cudaMemcpyDeviceToDevice, c->st);
+  } else {
+    // convert in chunks of at most 2^30 elements
+    const long long total = c->n * c->ld;
+    for (long long o = 0; o < total && !s; o += (1ll << 30)) {
+      const long long cnt = (total - o) < (1ll << 30) ? (total - o) : (1ll << 30);
+      s = launch_convert<T>((int)cnt, (const double *)Q64 + o, (T *)c->U + o, c->st);
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->hpin_int, c->core_ws, sizeof(int),
+                                            cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  cleanup();
+  if (e != cudaSuccess) return cuda_status(e, "orthonormalise");
+  if (s) return s;
+  if (*c->hpin_int) {
+    set_error("Cholesky-QR of U0 failed: U0^T U0 is not positive definite");
+    return OP_ERR_NOTSPD;
+  }
+  return OP_OK;
+}
+
+template <typename T>
+op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
+  const long long n = c->n;
+  const int ld = c->ld;
+  const size_t blk = (size_t)n * ld * sizeof(T);
+  // potential: min / max for the default shift and the residual normalisation
+  std::vector<double> Vh(n);
+  if (device) {
+    OP_CUDA(cudaMemcpy(Vh.data(), V, n * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(Vh.data(), V, n * sizeof(double));
+  }
+  double vmin = Vh[0], vmax = Vh[0];
+  for (long long i = 0; i < n; ++i) {
+    if (!isfinite(Vh[i])) {
+      set_error("V has a non-finite value at %lld", i);
+      return OP_ERR_ARG;
+    }
+    vmin = Vh[i] < vmin ? Vh[i] : vmin;
+    vmax = Vh[i] > vmax ? Vh[i] : vmax;
+  }
+  const double L = spectrum_lower_bound(&c->pb, vmin);
+  c->sigma = isnan(c->pb.sigma) ? (1.0 - L > 0.0 ? 1.0 - L : 0.0) : c->pb.sigma;
+  c->tau = isnan(c->pb.tau) ? 1.5 * (L + c->sigma) : c->pb.tau;
+  if (!(c->tau > 0.0) || !isfinite(c->sigma)) {
+    set_error("tau must be positive (got %g) and sigma finite", c->tau);
+    return OP_ERR_ARG;
+  }
+  c->hnorm = 2.0 * c->g.cdiag +
+             (fabs(vmax + c->sigma) > fabs(vmin + c->sigma) ? fabs(vmax + c->sigma)
+                                                            : fabs(vmin + c->sigma));
+  // device buffers
+  void *p;
+  OP_TRY(dev_alloc(c, &c->U, blk));
+  OP_TRY(dev_alloc(c, &c->U2, blk));
+  OP_TRY(dev_alloc(c, &c->W, blk));
+  OP_TRY(dev_alloc(c, &c->Vt, (size_t)n * sizeof(T)));
+  const size_t mat = (size_t)ld * ld * sizeof(double);
+  OP_TRY(dev_alloc(c, &p, 6 * mat));
+  c->C = (double *)p;
+  c->S = c->C + (size_t)ld * ld;
+  c->D = c->S + (size_t)ld * ld;
+  c->KU = c->D + (size_t)ld * ld;
+  c->KW = c->KU + (size_t)ld * ld;
+  c->Th = c->KW + (size_t)ld * ld;
+  OP_TRY(dev_alloc(c, &p, (2 * (size_t)c->p * c->p + c->p) * sizeof(double)));
+  c->eig_work = (double *)p;
+  c->lam_d = c->eig_work + 2 * (size_t)c->p * c->p;
+  OP_TRY(dev_alloc(c, &c->KU_t, (size_t)ld * ld * sizeof(T)));
+  OP_TRY(dev_alloc(c, &c->KW_t, (size_t)ld * ld * sizeof(T)));
+  OP_TRY(dev_alloc(c, &c->cg_ws, cg_workspace_bytes(n, ld, sizeof(T))));
+  cg_carve(c->cg_ws, n, ld, sizeof(T), &c->cgw);
+  c->cgw.prof = &c->prof;
+  c->gram_bytes = gram_workspace_bytes(n, ld, sizeof(T));
+  OP_TRY(dev_alloc(c, &c->gram_ws, c->gram_bytes));
+  OP_TRY(dev_alloc(c, &c->core_ws, core_workspace_bytes(c->p, ld)));
+  OP_TRY(dev_alloc(c, &p, (size_t)kNumSMs * 8 * 2 * ld * sizeof(double)));
+  c->part = (double *)p;
+  OP_TRY(dev_alloc(c, &p, 64 * sizeof(double)));
+  c->dsc = (double *)p;
+  OP_CUDA(cudaMallocHost((void **)&c->hsc, 64 * sizeof(double)));
+  OP_CUDA(cudaMallocHost((void **)&c->hpin_int, 16 * sizeof(int)));
+  c->cgw.nactive_host = c->hpin_int + 4;
+  OP_CUDA(cudaMemsetAsync(c->W, 0, blk, c->st));
+  OP_CUDA(cudaMemsetAsync(c->U2, 0, blk, c->st));
+
+  // V in T
+  void *V64 = nullptr;
+  OP_TRY(dev_alloc(c, &V64, n * sizeof(double)));
+  OP_CUDA(cudaMemcpyAsync(V64, device ? (const void *)V : (const void *)Vh.data(),
+                          n * sizeof(double),
+                          device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+  OP_TRY(launch_convert<T>((int)n, (const double *)V64, (T *)c->Vt, c->st));
+  // raw U0 (n x p FP64) on the device
+  void *U0d = nullptr;
+  OP_TRY(dev_alloc(c, &U0d, (size_t)n * c->p * sizeof(double)));
+  OP_CUDA(cudaMemcpyAsync(U0d, U0, (size_t)n * c->p * sizeof(double),
+                          device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+  op_status s = orthonormalise_impl<T>(c, (const double *)U0d);
+  OP_CUDA(cudaStreamSynchronize(c->st));
+  for (void *q : {V64, U0d}) {
+    cudaFree(q);
+    for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
+      if (*it == q) {
+        c->allocs.erase(it);
+        break;
+      }
+  }
+  if (s) return s;
+  c->g_rel = 1.0;
+  c->stats.sigma = c->sigma;
+  c->stats.tau = c->tau;
+  c->stats.residual = NAN;
+  OP_TRY(energy_impl<T>(c));
+  c->stats.err_E = fabs(c->E);  // err_E^0 = |E(U^0)| (Algorithm 1)
+  return OP_OK;
+}
+
+op_status init_common(op_ctx **out, const op_problem *pb, const double *V, const double *U0,
+                      void *stream, bool device) {
+  if (!out) {
+    set_error("null ctx pointer");
+    return OP_ERR_ARG;
+  }
+  *out = nullptr;
+  OP_TRY(check_problem(pb));
+  if (!V || !U0) {
+    set_error("V and U0 must be non-null");
+    return OP_ERR_ARG;
+  }
+  op_ctx *c = new op_ctx();
+  memset(&c->stats, 0, sizeof(c->stats));
+  c->pb = *pb;
+  make_geom(pb, &c->g);
+  c->n = c->g.n;
+  c->p = pb->p;
+  c->ld = round_up(pb->p, 8);
+  c->prec = pb->prec;
+  c->elem = pb->prec == OP_FP64 ? 8 : 4;
+  c->st = (cudaStream_t)stream;
+  op_status s = c->prec == OP_FP64 ? init_impl<double>(c, V, U0, device)
+                                   : init_impl<float>(c, V, U0, device);
+  if (s != OP_OK) {
+    cudaStreamSynchronize(c->st);
+    free_all(c);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return OP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *op_version(void) { return "opevo 0.1 (sm_103a)"; }
+
+const char *op_last_error(void) { return g_err; }
+
+long long op_kernel_launches(void) { return g_launches.load(); }
+
+op_status op_init(op_ctx **ctx, const op_problem *pb, const double *V, const double *U0,
+                  void *stream) {
+  g_err[0] = 0;
+  return init_common(ctx, pb, V, U0, stream, false);
+}
+
+op_status op_init_device(op_ctx **ctx, const op_problem *pb, const double *V_dev,
+                         const double *U0_dev, void *stream) {
+  g_err[0] = 0;
+  return init_common(ctx, pb, V_dev, U0_dev, stream, true);
+}
+
+op_status op_step(op_ctx *c, int nsteps, op_stats *st) {
+  if (!c || nsteps < 0) {
+    set_error("op_step: null context or negative step count");
+    return OP_ERR_ARG;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  for (int k = 0; k < nsteps; ++k) {
+    op_status s = c->prec == OP_FP64 ? step_impl<double>(c) : step_impl<float>(c);
+    if (s != OP_OK) return s;
+  }
+  c->stats.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                    .count();
+  if (st) *st = c->stats;
+  return OP_OK;
+}
+
+op_status op_residual(op_ctx *c, double *r) {
+  if (!c || !r) {
+    set_error("op_residual: null argument");
+    return OP_ERR_ARG;
+  }
+  return c->prec == OP_FP64 ? residual_impl<double>(c, r) : residual_impl<float>(c, r);
+}
+
+op_status op_solve(op_ctx *c, double tol, int max_steps, int stop, op_stats *st) {
+  if (!c || max_steps < 0 || (stop != OP_STOP_RESIDUAL && stop != OP_STOP_ERR_E &&
+                              stop != OP_STOP_STEPS)) {
+    set_error("op_solve: bad arguments");
+    return OP_ERR_ARG;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  const int every = c->pb.check_every > 0 ? c->pb.check_every : 10;
+  bool done = false;
+  double r = NAN;
+  for (int k = 0; k <= max_steps; ++k) {
+    if (stop == OP_STOP_ERR_E && c->stats.err_E <= tol) {
+      done = true;
+      break;
+    }
+    if (stop == OP_STOP_RESIDUAL && k % every == 0) {
+      OP_TRY(op_residual(c, &r));
+      if (r <= tol) {
+        done = true;
+        break;
+      }
+    }
+    if (k == max_steps) break;
+    op_status s = c->prec == OP_FP64 ? step_impl<double>(c) : step_impl<float>(c);
+    if (s != OP_OK) return s;
+  }
+  if (stop == OP_STOP_STEPS) done = true;
+  if (stop != OP_STOP_RESIDUAL || !done) OP_TRY(op_residual(c, &r));
+  c->stats.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                    .count();
+  if (st) *st = c->stats;
+  if (!done) {
+    set_error("op_solve: stop rule not met after %d steps", max_steps);
+    return OP_ERR_STATE;
+  }
+  return OP_OK;
+}
+
+op_status op_energy(op_ctx *c, double *E) {
+  if (!c || !E) {
+    set_error("op_energy: null argument");
+    return OP_ERR_ARG;
+  }
+  op_status s = c->prec == OP_FP64 ? energy_impl<double>(c) : energy_impl<float>(c);
+  if (s == OP_OK) *E = c->E;
+  return s;
+}
+
+op_status op_get_U(op_ctx *c, double *U_host) {
+  if (!c || !U_host) {
+    set_error("op_get_U: null argument");
+    return OP_ERR_ARG;
+  }
+  // stage through the CG scratch (3 blocks of T >= n x p doubles for ld <= 1.5 p... ) in
+  // row chunks that fit one scratch block of T
+  const size_t cap_rows = ((size_t)c->n * c->ld * c->elem) / ((size_t)c->p * sizeof(double));
+  const long long rows = cap_rows > 0 ? (long long)cap_rows : 1;
+  double *stage = (double *)c->cgw.R;
+  for (long long r0 = 0; r0 < c->n; r0 += rows) {
+    const long long cnt = (c->n - r0) < rows ? (c->n - r0) : rows;
+    op_status s;
+    if (c->prec == OP_FP64)
+      s = launch_unpad_copy<double>(cnt, c->p, c->ld, (const double *)c->U + r0 * c->ld, stage,
+                                    c->st);
+    else
+      s = launch_unpad_copy<float>(cnt, c->p, c->ld, (const float *)c->U + r0 * c->ld, stage,
+                                   c->st);
+    if (s) return s;
+    OP_CUDA(cudaMemcpyAsync(U_host + r0 * c->p, stage, (size_t)cnt * c->p * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->st));
+    OP_CUDA(cudaStreamSynchronize(c->st));
+  }
+  return OP_OK;
+}
+
+op_status op_eigenvalues(op_ctx *c, double *lam, int kind) {
+  if (!c || !lam || (kind != OP_EIG_RITZ && kind != OP_EIG_PAPER)) {
+    set_error("op_eigenvalues: bad arguments");
+    return OP_ERR_ARG;
+  }
+  return c->prec == OP_FP64 ? eig_impl<double>(c, lam, kind) : eig_impl<float>(c, lam, kind);
+}
+
+op_status op_profile_enable(op_ctx *c, int enable) {
+  if (!c) {
+    set_error("op_profile_enable: null context");
+    return OP_ERR_ARG;
+  }
+  OP_CUDA(cudaStreamSynchronize(c->st));
+  return prof_enable(&c->prof, enable != 0);
+}
+
+int op_profile_kinds(void) { return PK_COUNT; }
+
+const char *op_profile_name(int kind) { return prof_name(kind); }
+
+op_status op_profile_read(op_ctx *c, int kind, double *total_ms, long long *launches) {
+  if (!c || kind < 0 || kind >= PK_COUNT || !total_ms || !launches) {
+    set_error("op_profile_read: bad arguments");
+    return OP_ERR_ARG;
+  }
+  *total_ms = c->prof.ms[kind];
+  *launches = c->prof.cnt[kind];
+  return OP_OK;
+}
+
+op_status op_get_stats(op_ctx *c, op_stats *st) {
+  if (!c || !st) {
+    set_error("op_get_stats: null argument");
+    return OP_ERR_ARG;
+  }
+  *st = c->stats;
+  return OP_OK;
+}
+
+void op_destroy(op_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  free_all(c);
+  delete c;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel-level entry points
+// ---------------------------------------------------------------------------
+static op_status check_blocks(int prec, int p, int ld, const void *a, const void *b) {
+  if (prec != OP_FP64 && prec != OP_FP32) {
+    set_error("unsupported precision mode %d", prec);
+    return OP_ERR_ARG;
+  }
+  if (p < 1 || ld < p || ld % 8 != 0) {
+    set_error("need 1 <= p <= ld and ld %% 8 == 0 (p=%d ld=%d)", p, ld);
+    return OP_ERR_ARG;
+  }
+  if (!a || !b || ((uintptr_t)a & 15) || ((uintptr_t)b & 15)) {
+    set_error("block pointers must be non-null and 16-byte aligned");
+    return OP_ERR_ARG;
+  }
+  return OP_OK;
+}
+
+op_status op_apply_H(const op_problem *pb, int ld, const void *V_t, double sigma, const void *X,
+                     void *Y, void *stream) {
+  Geom g;
+  OP_TRY(make_geom(pb, &g));
+  OP_TRY(check_blocks(pb->prec, pb->p, ld, X, Y));
+  if (!V_t) {
+    set_error("null V");
+    return OP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (pb->prec == OP_FP64)
+    return launch_apply<double>(g, (const double *)V_t, sigma, (const double *)X, (double *)Y, ld,
+                                st);
+  return launch_apply<float>(g, (const float *)V_t, sigma, (const float *)X, (float *)Y, ld, st);
+}
+
+size_t op_cg_workspace(const op_problem *pb, int ld) {
+  Geom g;
+  if (!pb || make_geom(pb, &g) != OP_OK || ld < 8) return 0;
+  const int elem = pb->prec == OP_FP64 ? 8 : 4;
+  return cg_workspace_bytes(g.n, ld, elem) + 64;
+}
+
+op_status op_cg_solve(const op_problem *pb, int ld, const void *V_t, double sigma, const void *U,
+                      void *W, double rtol, int max_iter, void *ws, size_t ws_bytes, int *iters,
+                      void *stream) {
+  Geom g;
+  OP_TRY(make_geom(pb, &g));
+  OP_TRY(check_blocks(pb->prec, pb->p, ld, U, W));
+  if (!V_t || !ws || !iters || ws_bytes < op_cg_workspace(pb, ld) || max_iter < 0) {
+    set_error("op_cg_solve: bad V, workspace (%zu < %zu), iters or max_iter", ws_bytes,
+              op_cg_workspace(pb, ld));
+    return OP_ERR_ARG;
+  }
+  const int elem = pb->prec == OP_FP64 ? 8 : 4;
+  CGWork w;
+  cg_carve(ws, g.n, ld, elem, &w);
+  int nact = 0;
+  w.nactive_host = &nact;
+  cudaStream_t st = (cudaStream_t)stream;
+  op_status s;
+  if (pb->prec == OP_FP64)
+    s = cg_solve<double>(g, (const double *)V_t, sigma, (const double *)U, (double *)W, pb->p, ld,
+                         rtol, max_iter, w, iters, st);
+  else
+    s = cg_solve<float>(g, (const float *)V_t, sigma, (const float *)U, (float *)W, pb->p, ld,
+                        rtol, max_iter, w, iters, st);
+  return s;
+}
+
+size_t op_gram_workspace(int prec, long long n, int ld) {
+  return gram_workspace_bytes(n, ld, prec == OP_FP64 ? 8 : 4);
+}
+
+op_status op_gram(int prec, long long n, int p, int ld, const void *U, const void *W, double *C,
+                  double *S, double *D, void *ws, size_t ws_bytes, void *stream) {
+  OP_TRY(check_blocks(prec, p, ld, U, W));
+  if (n < 1) {
+    set_error("n must be positive");
+    return OP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == OP_FP64)
+    return gram<double>(n, p, ld, (const double *)U, (const double *)W, C, S, D, ws, ws_bytes, st);
+  return gram<float>(n, p, ld, (const float *)U, (const float *)W, C, S, D, ws, ws_bytes, st);
+}
+
+size_t op_core_workspace(int p, int ld) { return core_workspace_bytes(p, ld); }
+
+op_status op_core(int prec, int p, int ld, double tau, const double *C, const double *S,
+                  double *KU, double *KW, void *KU_t, void *KW_t, void *ws, size_t ws_bytes,
+                  void *stream) {
+  if (prec != OP_FP64 && prec != OP_FP32) {
+    set_error("unsupported precision mode %d", prec);
+    return OP_ERR_ARG;
+  }
+  if (p < 1 || ld < p || ld % 8 || !C || !S || !KU || !KW || !ws ||
+      ws_bytes < core_workspace_bytes(p, ld) || !(tau > 0.0)) {
+    set_error("op_core: bad arguments");
+    return OP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == OP_FP64)
+    return core<double>(p, ld, tau, C, S, KU, KW, (double *)KU_t, (double *)KW_t, ws, st);
+  return core<float>(p, ld, tau, C, S, KU, KW, (float *)KU_t, (float *)KW_t, ws, st);
+}
+
+op_status op_core_status(void *ws, void *stream) {
+  if (!ws) {
+    set_error("null workspace");
+    return OP_ERR_ARG;
+  }
+  int h = 0;
+  OP_CUDA(cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  OP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (h) {
+    set_error("Cholesky pivot not positive");
+    return OP_ERR_NOTSPD;
+  }
+  return OP_OK;
+}
+
+op_status op_update(int prec, long long n, int p, int ld, const void *U, const void *W,
+                    const void *KU_t, const void *KW_t, void *Unew, void *stream) {
+  OP_TRY(check_blocks(prec, p, ld, U, W));
+  if (!KU_t || !KW_t || !Unew || n < 1 || Unew == U || Unew == W) {
+    set_error("op_update: bad arguments");
+    return OP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == OP_FP64)
+    return update<double>(n, ld, (const double *)U, (const double *)W, (const double *)KU_t,
+                          (const double *)KW_t, (double *)Unew, st);
+  return update<float>(n, ld, (const float *)U, (const float *)W, (const float *)KU_t,
+                       (const float *)KW_t, (float *)Unew, st);
+}
+
+}  // extern "C"

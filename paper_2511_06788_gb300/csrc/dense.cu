@@ -1,0 +1,388 @@
+// Small dense FP64 algebra on p x p matrices (stride ld):
+//   * Steps 2-3 of §4.1: M = I + tau^2/4 (S - C C), B = M^-1 by Cholesky
+//     (M - I is positive semi-definite by Lemma 3.1, so the factorisation
+//     exists for any tau), tau/2 A = I - B + tau/2 C B, and the Step-4
+//     coefficients KU = I - tau A = 2B - I - tau C B, KW = tau B;
+//   * Cholesky-QR coefficients R^-1 for the initial orthonormalisation;
+//   * symmetric eigenvalues (cyclic Jacobi) for the reported eigenvalues.
+// All of it runs in FP64: on GB300 these kernels are FP64-pipe bound but tiny
+// next to the n x p work (O(p^3) vs O(n p^2)).
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace opevo {
+
+namespace {
+
+constexpr int kT = 16;  // tile of the small GEMM
+
+// out = alpha * A B + beta * X + gamma * I on the p x p block; zero elsewhere in
+// ld x ld.  X may be null (beta ignored).  tout (may be null) gets a T copy.
+template <typename T>
+__global__ void k_small_gemm(int p, int ld, double alpha, const double *__restrict__ A,
+                             const double *__restrict__ B, double beta,
+                             const double *__restrict__ X, double gamma, double *__restrict__ out,
+                             T *__restrict__ tout, const int *__restrict__ status) {
+  __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
+  const int i = blockIdx.y * kT + threadIdx.y, j = blockIdx.x * kT + threadIdx.x;
+  double s = 0.0;
+  for (int k0 = 0; k0 < p; k0 += kT) {
+    const int ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
+    As[threadIdx.y][threadIdx.x] = (i < p && ka < p) ? A[(long long)i * ld + ka] : 0.0;
+    Bs[threadIdx.y][threadIdx.x] = (kb < p && j < p) ? B[(long long)kb * ld + j] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kT; ++k) s = fma(As[threadIdx.y][k], Bs[k][threadIdx.x], s);
+    __syncthreads();
+  }
+  if (i >= ld || j >= ld) return;
+  double v = 0.0;
+  if (i < p && j < p) {
+    v = alpha * s + (i == j ? gamma : 0.0);
+    if (X) v += beta * X[(long long)i * ld + j];
+    if (status && *status) v = (i == j) ? 1.0 : 0.0;  // failed factorisation: identity
+  }
+  out[(long long)i * ld + j] = v;
+  if (tout) tout[(long long)i * ld + j] = (T)v;
+}
+
+// In-place right-looking Cholesky of sym(M) = (M + M^T)/2 into the lower
+// triangle of L (upper part zeroed).  One CTA.  status <- 1 on a pivot <= 0
+// or a non-finite pivot.
+__global__ void __launch_bounds__(1024) k_chol(int p, int ld, const double *__restrict__ M,
+                                               double *__restrict__ L, int *status) {
+  __shared__ double piv;
+  __shared__ int bad;
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (long long e = t; e < (long long)p * p; e += nt) {
+    const int i = (int)(e / p), j = (int)(e % p);
+    L[(long long)i * ld + j] =
+        (j <= i) ? 0.5 * (M[(long long)i * ld + j] + M[(long long)j * ld + i]) : 0.0;
+  }
+  if (t == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < p; ++k) {
+    if (t == 0) {
+      const double d = L[(long long)k * ld + k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        piv = 1.0;
+      } else {
+        piv = sqrt(d);
+        L[(long long)k * ld + k] = piv;
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double inv = 1.0 / piv;
+    for (int i = k + 1 + t; i < p; i += nt) L[(long long)i * ld + k] *= inv;
+    __syncthreads();
+    // trailing update of the lower triangle: rows i > k, columns k < j <= i
+    const int m = p - k - 1;
+    for (long long e = t; e < (long long)m * m; e += nt) {
+      const int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
+      if (j <= i) L[(long long)i * ld + j] -= L[(long long)i * ld + k] * L[(long long)j * ld + k];
+    }
+    __syncthreads();
+  }
+  if (t == 0 && bad) *status = 1;
+}
+
+// One CTA per column j.  mode 0: out[:, j] = (L L^T)^-1 e_j  (forward then
+// backward substitution).  mode 1: out[:, j] = L^-T e_j, i.e. column j of
+// R^-1 for R = L^T (backward substitution only).
+__global__ void k_tri_cols(int p, int ld, const double *__restrict__ L, int mode,
+                           double *__restrict__ out, const int *__restrict__ status) {
+  extern __shared__ double y[];  // p values
+  const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+  if (j >= ld) return;
+  if (*status || j >= p) {
+    for (int i = t; i < ld; i += nt) out[(long long)i * ld + j] = (i == j && j < p) ? 1.0 : 0.0;
+    return;
+  }
+  for (int i = t; i < p; i += nt) y[i] = (i == j) ? 1.0 : 0.0;
+  __syncthreads();
+  if (mode == 0) {
+    // forward: L z = e_j  (z_k = 0 for k < j); z overwrites y
+    for (int k = j; k < p; ++k) {
+      const double zk = y[k] / L[(long long)k * ld + k];
+      __syncthreads();
+      if (t == 0) y[k] = zk;
+      for (int i = k + 1 + t; i < p; i += nt) y[i] -= L[(long long)i * ld + k] * zk;
+      __syncthreads();
+    }
+  }
+  // backward: L^T x = y; x overwrites y
+  for (int k = p - 1; k >= 0; --k) {
+    const double xk = y[k] / L[(long long)k * ld + k];
+    __syncthreads();
+    if (t == 0) y[k] = xk;
+    for (int i = t; i < k; i += nt) y[i] -= L[(long long)k * ld + i] * xk;
+    __syncthreads();
+  }
+  for (int i = t; i < ld; i += nt) out[(long long)i * ld + j] = (i < p) ? y[i] : 0.0;
+}
+
+// KW = tau B (FP64 and T copies).
+template <typename T>
+__global__ void k_scale(int ld, double tau, const double *__restrict__ B, double *__restrict__ KW,
+                        T *__restrict__ KW_t) {
+  const long long total = (long long)ld * ld;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double v = tau * B[e];
+    KW[e] = v;
+    if (KW_t) KW_t[e] = (T)v;
+  }
+}
+
+__device__ double block_sum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += sh[i];
+  return s;  // valid in thread 0
+}
+
+__global__ void k_core_stats(int p, int ld, const double *__restrict__ C,
+                             const double *__restrict__ S, const double *__restrict__ D,
+                             double *out) {
+  __shared__ double sh[32];
+  double trs = 0.0, cc = 0.0, dd = 0.0;
+  for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x) {
+    const int i = (int)(e / p), j = (int)(e % p);
+    const long long o = (long long)i * ld + j;
+    if (S && i == j) trs += S[o];
+    if (C) cc += C[o] * C[o];
+    if (D) {
+      const double d = D[o] - (i == j ? 1.0 : 0.0);
+      dd += d * d;
+    }
+  }
+  trs = block_sum(trs, sh);
+  cc = block_sum(cc, sh);
+  dd = block_sum(dd, sh);
+  if (threadIdx.x == 0) {
+    out[0] = trs - cc;
+    out[1] = sqrt(dd);
+    out[2] = trs;
+  }
+}
+
+// ---- cyclic Jacobi eigenvalues (one CTA; round-robin pair ordering) -----------
+__global__ void __launch_bounds__(1024) k_jacobi(int p, int ld, const double *__restrict__ Ain,
+                                                 double *__restrict__ A, double *__restrict__ lam) {
+  extern __shared__ double sh[];  // cs[2 * m] rotation pairs, then scratch
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int m2 = (p + 1) / 2 * 2;  // players (a dummy when p is odd)
+  const int npair = m2 / 2;
+  double *cs = sh;                   // [npair][2]
+  int *pa = (int *)(sh + 2 * npair); // [npair]
+  int *pb = pa + npair;
+  __shared__ double off, tot;
+  for (long long e = t; e < (long long)p * p; e += nt) {
+    const int i = (int)(e / p), j = (int)(e % p);
+    A[(long long)i * p + j] = 0.5 * (Ain[(long long)i * ld + j] + Ain[(long long)j * ld + i]);
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    // convergence test: off-diagonal Frobenius norm vs total
+    if (t == 0) {
+      off = 0.0;
+      tot = 0.0;
+    }
+    __syncthreads();
+    double o = 0.0, a = 0.0;
+    for (long long e = t; e < (long long)p * p; e += nt) {
+      const int i = (int)(e / p), j = (int)(e % p);
+      const double v = A[e];
+      a += v * v;
+      if (i != j) o += v * v;
+    }
+    atomicAdd(&off, o);
+    atomicAdd(&tot, a);
+    __syncthreads();
+    if (off <= 1e-30 * tot || p < 2) break;
+    for (int r = 0; r < m2 - 1; ++r) {
+      for (int k = t; k < npair; k += nt) {
+        int x, y;
+        if (k == 0) {
+          x = r;
+          y = m2 - 1;
+        } else {
+          x = (r + k) % (m2 - 1);
+          y = (r - k + m2 - 1) % (m2 - 1);
+        }
+        const int aa = x < y ? x : y, bb = x < y ? y : x;
+        double c = 1.0, s = 0.0;
+        if (bb < p) {
+          const double apq = A[(long long)aa * p + bb];
+          if (apq != 0.0) {
+            const double th = (A[(long long)bb * p + bb] - A[(long long)aa * p + aa]) / (2.0 * apq);
+            const double tn = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(tn * tn + 1.0);
+            s = tn * c;
+          }
+        }
+        pa[k] = aa;
+        pb[k] = bb;
+        cs[2 * k] = c;
+        cs[2 * k + 1] = s;
+      }
+      __syncthreads();
+      // rows: A_a <- c A_a - s A_b ; A_b <- s A_a + c A_b
+      for (long long e = t; e < (long long)npair * p; e += nt) {
+        const int k = (int)(e / p), j = (int)(e % p);
+        const int aa = pa[k], bb = pb[k];
+        if (bb >= p) continue;
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        const double xa = A[(long long)aa * p + j], xb = A[(long long)bb * p + j];
+        A[(long long)aa * p + j] = c * xa - s * xb;
+        A[(long long)bb * p + j] = s * xa + c * xb;
+      }
+      __syncthreads();
+      // columns, same rotation
+      for (long long e = t; e < (long long)npair * p; e += nt) {
+        const int k = (int)(e / p), i = (int)(e % p);
+        const int aa = pa[k], bb = pb[k];
+        if (bb >= p) continue;
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        const double xa = A[(long long)i * p + aa], xb = A[(long long)i * p + bb];
+        A[(long long)i * p + aa] = c * xa - s * xb;
+        A[(long long)i * p + bb] = s * xa + c * xb;
+      }
+      __syncthreads();
+    }
+  }
+  // ascending diagonal: rank of each value (ties broken by index)
+  for (int i = t; i < p; i += nt) {
+    const double v = A[(long long)i * p + i];
+    int rank = 0;
+    for (int j = 0; j < p; ++j) {
+      const double w = A[(long long)j * p + j];
+      rank += (w < v) || (w == v && j < i);
+    }
+    lam[rank] = v;
+  }
+}
+
+// Residual coefficients: R = U (-Theta) + Y I with Y = H U.
+template <typename T>
+__global__ void k_resid_coeff(int p, int ld, const double *__restrict__ Th, T *__restrict__ negTh,
+                              T *__restrict__ Id) {
+  const long long total = (long long)ld * ld;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ld), j = (int)(e % ld);
+    const bool in = i < p && j < p;
+    negTh[e] = in ? (T)(-Th[e]) : T(0);
+    Id[e] = (in && i == j) ? T(1) : T(0);
+  }
+}
+
+// lambda_i = 1/mu - sigma for mu ascending (eigenvalues of <GU,U>), written ascending.
+__global__ void k_paper_lams(int p, const double *__restrict__ mu, double sigma,
+                             double *__restrict__ lam) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p; i += gridDim.x * blockDim.x)
+    lam[p - 1 - i] = 1.0 / mu[i] - sigma;
+}
+
+template <typename T>
+__global__ void k_convert(int count, const double *__restrict__ src, T *__restrict__ dst) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+    dst[e] = (T)src[e];
+}
+
+}  // namespace
+
+size_t core_workspace_bytes(int p, int ld) {
+  (void)p;
+  return 256 + 3 * (size_t)ld * ld * sizeof(double);
+}
+
+template <typename T>
+op_status core(int p, int ld, double tau, const double *C, const double *S, double *KU,
+               double *KW, T *KU_t, T *KW_t, void *ws, cudaStream_t st) {
+  int *status = (int *)ws;
+  double *M = (double *)((char *)ws + 256);
+  double *L = M + (size_t)ld * ld;
+  double *B = L + (size_t)ld * ld;
+  const dim3 tb(kT, kT), tg((ld + kT - 1) / kT, (ld + kT - 1) / kT);
+  const double q = 0.25 * tau * tau;
+  OP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  // Step 2 matrix: M = I + tau^2/4 <W,W> - tau^2/4 <W,U><W,U>
+  k_small_gemm<double><<<tg, tb, 0, st>>>(p, ld, -q, C, C, q, S, 1.0, M, (double *)nullptr,
+                                          (const int *)nullptr); count_launch();
+  k_chol<<<1, 1024, 0, st>>>(p, ld, M, L, status); count_launch();
+  k_tri_cols<<<ld, 256, p * sizeof(double), st>>>(p, ld, L, 0, B, status); count_launch();
+  // KU = 2B - I - tau C B (Step 3 folded into Step 4); KW = tau B
+  k_small_gemm<T><<<tg, tb, 0, st>>>(p, ld, -tau, C, B, 2.0, B, -1.0, KU, KU_t, status); count_launch();
+  k_scale<T><<<(ld * ld + 255) / 256, 256, 0, st>>>(ld, tau, B, KW, KW_t); count_launch();
+  OP_LAUNCH("core");
+  return OP_OK;
+}
+
+op_status cholqr_coeff(int p, int ld, const double *D, double *KU, void *ws, cudaStream_t st) {
+  int *status = (int *)ws;
+  double *L = (double *)((char *)ws + 256) + (size_t)ld * ld;
+  OP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  k_chol<<<1, 1024, 0, st>>>(p, ld, D, L, status); count_launch();
+  k_tri_cols<<<ld, 256, p * sizeof(double), st>>>(p, ld, L, 1, KU, status); count_launch();
+  OP_LAUNCH("cholqr_coeff");
+  return OP_OK;
+}
+
+op_status sym_eigvals(int p, int ld, const double *A, double *work, double *lam,
+                      cudaStream_t st) {
+  const int npair = (p + 1) / 2;
+  const size_t smem = (size_t)npair * 2 * sizeof(double) + (size_t)npair * 2 * sizeof(int) + 64;
+  k_jacobi<<<1, 1024, smem, st>>>(p, ld, A, work, lam); count_launch();
+  OP_LAUNCH("k_jacobi");
+  return OP_OK;
+}
+
+op_status launch_core_stats(int p, int ld, const double *C, const double *S, const double *D,
+                            double *out, cudaStream_t st) {
+  k_core_stats<<<1, 1024, 0, st>>>(p, ld, C, S, D, out); count_launch();
+  OP_LAUNCH("k_core_stats");
+  return OP_OK;
+}
+
+template <typename T>
+op_status launch_convert(int count, const double *src, T *dst, cudaStream_t st) {
+  k_convert<T><<<(count + 255) / 256, 256, 0, st>>>(count, src, dst); count_launch();
+  OP_LAUNCH("k_convert");
+  return OP_OK;
+}
+
+template <typename T>
+op_status launch_resid_coeff(int p, int ld, const double *Th, T *negTh, T *Id, cudaStream_t st) {
+  k_resid_coeff<T><<<(ld * ld + 255) / 256, 256, 0, st>>>(p, ld, Th, negTh, Id); count_launch();
+  OP_LAUNCH("k_resid_coeff");
+  return OP_OK;
+}
+
+op_status launch_paper_lams(int p, const double *mu, double sigma, double *lam, cudaStream_t st) {
+  k_paper_lams<<<(p + 255) / 256, 256, 0, st>>>(p, mu, sigma, lam); count_launch();
+  OP_LAUNCH("k_paper_lams");
+  return OP_OK;
+}
+
+template op_status launch_resid_coeff<float>(int, int, const double *, float *, float *,
+                                             cudaStream_t);
+template op_status launch_resid_coeff<double>(int, int, const double *, double *, double *,
+                                              cudaStream_t);
+template op_status core<float>(int, int, double, const double *, const double *, double *,
+                               double *, float *, float *, void *, cudaStream_t);
+template op_status core<double>(int, int, double, const double *, const double *, double *,
+                                double *, double *, double *, void *, cudaStream_t);
+template op_status launch_convert<float>(int, const double *, float *, cudaStream_t);
+template op_status launch_convert<double>(int, const double *, double *, cudaStream_t);
+
+}  // namespace opevo

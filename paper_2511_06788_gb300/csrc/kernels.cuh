@@ -1,0 +1,128 @@
+// Internal launchers of the opevo kernels.  Every launcher only enqueues work
+// on `st` and returns OP_OK or the launch error; buffers are device pointers.
+#pragma once
+
+#include "common.cuh"
+
+namespace opevo {
+
+// ---- optional per-kernel timing with CUDA events on the launching stream ----------
+enum ProfKind {
+  PK_CG_INIT = 0,
+  PK_CG_APPLY,
+  PK_CG_AXPY,
+  PK_CG_DIR,
+  PK_CG_FIN,
+  PK_GRAM,
+  PK_CORE,
+  PK_UPDATE,
+  PK_ENERGY,
+  PK_RESIDUAL,
+  PK_COUNT
+};
+struct Prof {
+  static constexpr int kMax = 64;
+  bool on = false;
+  bool created = false;
+  cudaEvent_t ev[2 * kMax];
+  int kind[kMax];
+  int n = 0;
+  double ms[PK_COUNT];
+  long long cnt[PK_COUNT];
+};
+const char *prof_name(int kind);
+op_status prof_enable(Prof *p, bool on);
+void prof_destroy(Prof *p);
+// begin/end bracket one launch (or a group of launches) of `kind`; no-ops when off
+void prof_begin(Prof *p, int kind, cudaStream_t st);
+void prof_end(Prof *p, cudaStream_t st);
+// accumulate the recorded pairs; the stream must have been synchronised
+void prof_harvest(Prof *p);
+
+// ---- stencil and Step-1 CG (stencil_cg.cu) --------------------------------
+// Vt: n values of V in T; the diagonal of H + sigma is Vt_i + cdiag + sigma.
+// Y = (H + sigma) X.
+template <typename T>
+op_status launch_apply(const Geom &g, const T *Vt, double sigma, const T *X, T *Y, int ld,
+                       cudaStream_t st);
+
+// out[0] = sum X .* ((H + sigma) X), out[1] = sum X .* X (FP64, device); part is
+// scratch of [max_blocks][2][ld] doubles.
+template <typename T>
+op_status launch_quad(const Geom &g, const T *Vt, double sigma, const T *X, int ld, double *part,
+                      double *out, cudaStream_t st);
+
+// out[0] = sum X .* X; part as above.
+template <typename T>
+op_status launch_sumsq(long long n, int ld, const T *X, double *part, double *out,
+                       cudaStream_t st);
+
+// Reduce part[nblk][ncomp][ld] over blocks into out[ncomp][ld] (FP64).
+op_status launch_colsum(const double *part, int nblk, int ncomp, int ld, double *out,
+                        cudaStream_t st);
+
+// CG workspace layout and the solver loop.
+struct CGWork {
+  void *R, *P, *Q;       // n x ld blocks of T
+  double *part;          // [max_blocks][2][ld]
+  double *state;         // [6][ld]: rr, target, alpha, beta, bnorm2, scratch
+  int *active;           // [ld]
+  int *nactive;          // [1] device
+  int *nactive_host;     // pinned host mirror
+  int max_blocks;
+  Prof *prof = nullptr;   // optional timing
+};
+size_t cg_workspace_bytes(long long n, int ld, int elem);
+void cg_carve(void *ws, long long n, int ld, int elem, CGWork *w);
+
+template <typename T>
+op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, int p, int ld,
+                   double rtol, int max_iter, CGWork &w, int *iters, cudaStream_t st);
+
+// Copy an n x p FP64 block into an n x ld block of T (zero padding).
+template <typename T>
+op_status launch_pad_copy(long long n, int p, int ld, const double *src, T *dst, cudaStream_t st);
+// Copy an n x ld block of T into an n x p FP64 block (drop padding).
+template <typename T>
+op_status launch_unpad_copy(long long n, int p, int ld, const T *src, double *dst,
+                            cudaStream_t st);
+
+// ---- Gram matrices (gram.cu) -------------------------------------------------
+size_t gram_workspace_bytes(long long n, int ld, int elem);
+template <typename T>
+op_status gram(long long n, int p, int ld, const T *U, const T *W, double *C, double *S,
+               double *D, void *ws, size_t ws_bytes, cudaStream_t st);
+
+// ---- dense FP64 p x p algebra (dense.cu) --------------------------------------
+size_t core_workspace_bytes(int p, int ld);
+// ws layout begins with an int status word (0 ok, 1 not SPD).
+template <typename T>
+op_status core(int p, int ld, double tau, const double *C, const double *S, double *KU,
+               double *KW, T *KU_t, T *KW_t, void *ws, cudaStream_t st);
+// Cholesky-QR coefficients: from D = U0^T U0, KU = R^-1 with R = chol(D)^T, written
+// as an ld x ld FP64 matrix (zero outside p x p). Status word as in core().
+op_status cholqr_coeff(int p, int ld, const double *D, double *KU, void *ws, cudaStream_t st);
+// Eigenvalues (ascending) of the symmetric part of the p x p matrix A (stride ld)
+// by cyclic Jacobi on the device; `work` holds 2 p*p doubles; lam receives p values.
+op_status sym_eigvals(int p, int ld, const double *A, double *work, double *lam,
+                      cudaStream_t st);
+// Scalars of the last step from C, S, D: g2 = tr S - ||C||_F^2, orth = ||D - I||_F,
+// trS = tr S; written to out[0..2].
+op_status launch_core_stats(int p, int ld, const double *C, const double *S, const double *D,
+                            double *out, cudaStream_t st);
+// Convert an ld x ld FP64 matrix to T.
+template <typename T>
+op_status launch_convert(int count, const double *src, T *dst, cudaStream_t st);
+
+// T copies of -Theta and I (p x p inside ld x ld) for R = H U - U Theta.
+template <typename T>
+op_status launch_resid_coeff(int p, int ld, const double *Th, T *negTh, T *Id, cudaStream_t st);
+// lam (ascending) = 1/mu - sigma for mu ascending.
+op_status launch_paper_lams(int p, const double *mu, double sigma, double *lam, cudaStream_t st);
+
+// ---- Step 4 (update.cu) -------------------------------------------------------
+template <typename T>
+op_status update(long long n, int ld, const T *U, const T *W, const T *KU, const T *KW, T *Unew,
+                 cudaStream_t st);
+
+}  // namespace opevo
