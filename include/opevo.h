@@ -46,7 +46,8 @@ typedef enum {
   OP_OK = 0,
   OP_ERR_ARG = -1,       /* invalid argument (null pointer, size, alignment, mode) */
   OP_ERR_CUDA = -2,      /* a CUDA runtime call failed (message has the detail)   */
-  OP_ERR_NOTSPD = -3,    /* a Cholesky pivot was not positive (Step 2 matrix or Cholesky-QR) */
+  OP_ERR_NOTSPD = -3,    /* factorisation breakdown: zero/non-finite Step-2 pivot, or a
+                            non-positive Cholesky-QR pivot                           */
   OP_ERR_DIVERGED = -4,  /* non-finite energy / residual, or energy increase beyond roundoff */
   OP_ERR_TIMEOUT = -5,   /* a bounded device wait gave up                           */
   OP_ERR_OOM = -6,       /* device allocation failed                               */
@@ -83,7 +84,8 @@ typedef struct {
   double cg_rtol;        /* Step-1 CG: relative residual per column; <= 0 selects
                             max(floor, min(1e-2, 0.1 g)) with g the relative
                             G-residual sqrt(g_residual / tr<W,W>) of the previous
-                            step, floor 1e-13 (FP64) or 1e-6 (FP32)                 */
+                            step, floor 1e-13 (FP64) or 1e-6 (FP32); inside op_solve
+                            also <= 0.1 tol (residual rule) or 0.1 sqrt(tol) (err_E) */
   int cg_max_iter;       /* Step-1 CG iteration cap per step (<= 0: 2000)           */
   int check_every;       /* op_solve: residual evaluated every this many steps (<= 0: 10) */
 } op_problem;
@@ -201,17 +203,20 @@ op_status op_gram(int prec, long long n, int p, int ld, const void *U, const voi
 size_t op_gram_workspace(int prec, long long n, int ld);
 
 /* Steps 2-3 of §4.1 in FP64: from C = <W,U>, S = <W,W> (ld x ld device, FP64) form
- * M = I + tau^2/4 (S - C C) (symmetrised), B = M^-1 by Cholesky, A from Step 3,
- * and the Step-4 coefficients KU = I - tau A = 2B - I - tau C B, KW = tau B
- * (ld x ld FP64 device, zero outside p x p).  KU_t / KW_t (may be NULL) receive the
- * same matrices in the block type of `prec`.  ws: at least op_core_workspace() bytes.
- * A non-positive Cholesky pivot is reported by the next synchronising call on the
- * same workspace via op_core_status(). */
+ * M = I + tau/2 (C - C^T) + tau^2/4 (S - C C^T), B = M^-1 (LU without pivoting; the
+ * symmetric part of M is >= I by Lemma 3.1), tau/2 A = I - B + tau/2 C^T B, and the
+ * Step-4 coefficients KU = I - tau A = 2B - I - tau C^T B, KW = tau B (ld x ld FP64
+ * device, zero outside p x p).  For the exact W = GU (C symmetric) these are the
+ * paper's Steps 2-3; for any other W they solve the midpoint scheme (4.1) exactly
+ * for the operator built from W, so Step 4 keeps <U,U>.  KU_t / KW_t (may be NULL)
+ * receive the same matrices in the block type of `prec`.  ws: at least
+ * op_core_workspace() bytes.  A zero or non-finite pivot is reported by
+ * op_core_status() on the same workspace (the coefficients are then KU = I, KW = 0). */
 op_status op_core(int prec, int p, int ld, double tau, const double *C, const double *S,
                   double *KU, double *KW, void *KU_t, void *KW_t, void *ws, size_t ws_bytes,
                   void *stream);
 size_t op_core_workspace(int p, int ld);
-/* Synchronises `stream`; returns OP_ERR_NOTSPD if the last op_core on ws failed. */
+/* Synchronises `stream`; returns OP_ERR_NOTSPD if the last op_core on ws broke down. */
 op_status op_core_status(void *ws, void *stream);
 
 /* Step 4: Unew = U KU + W KW (KU, KW: ld x ld in the block type T, device).

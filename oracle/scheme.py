@@ -37,7 +37,7 @@ __all__ = [
     "gershgorin_norm", "householder_orthonormalize", "cholesky_qr", "inner", "SourceSolver",
     "block_cg", "core_matrices", "update", "scheme_step", "energy", "residuals",
     "paper_eigenvalues", "ritz_values", "orth_error", "energy_lower_bound", "run",
-    "RunResult", "step_coefficients",
+    "RunResult", "step_coefficients", "midpoint_coefficients",
 ]
 
 
@@ -208,6 +208,30 @@ def core_matrices(W: np.ndarray, U: np.ndarray, tau: float):
     B = np.linalg.solve(M, I)
     A = (2.0 / tau) * (I - B + (tau / 2.0) * (C @ B))
     return A, B, M
+
+
+def midpoint_coefficients(W: np.ndarray, U: np.ndarray, tau: float):
+    """Exact solution of the midpoint scheme (4.1) when W is any n x p block.
+
+    (4.1) with L V = U <W, V> - W <U, V> (the operator L_U of (3.2) with GU
+    replaced by W) is solved by U^{n+1} = U - tau U A + tau W B with
+    A = <W, U^{n+1/2}>, B = <U, U^{n+1/2}> as in §4.1.  Repeating the
+    derivation of Steps 2-3 under <U, U> = I but without using the symmetry
+    of C = <W, U> (it holds only for the exact W = GU) gives
+        (I + tau/2 (C - C^T) + tau^2/4 (S - C C^T)) B = I,
+        tau/2 A = I - B + tau/2 C^T B,
+    which is Steps 2-3 when C = C^T.  Since L is skew-symmetric for every W
+    (Lemma 3.2 uses only the algebra), the step is an exact Cayley transform and
+    keeps <U, U> for any W, e.g. an inexact Step-1 solve.  Returns (A, B).
+    """
+    p = U.shape[1]
+    I = np.eye(p)
+    C = inner(W, U)
+    S = inner(W, W)
+    M = I + (tau / 2.0) * (C - C.T) + (tau * tau / 4.0) * (S - C @ C.T)
+    B = np.linalg.solve(M, I)
+    A = (2.0 / tau) * (I - B + (tau / 2.0) * (C.T @ B))
+    return A, B
 
 
 def update(U: np.ndarray, W: np.ndarray, A: np.ndarray, B: np.ndarray, tau: float) -> np.ndarray:

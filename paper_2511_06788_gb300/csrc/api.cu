@@ -102,6 +102,7 @@ struct op_ctx {
   op_stats stats;
   double E;
   double g_rel;  // last relative G-residual sqrt(g2 / trS)
+  double cg_cap; // op_solve: upper bound of the adaptive CG tolerance (from its stop rule)
   std::vector<void *> allocs;
 };
 
@@ -160,6 +161,7 @@ double cg_rtol_for(op_ctx *c) {
   const double floor = c->prec == OP_FP64 ? 1e-13 : 1e-6;
   double r = 0.1 * c->g_rel;
   if (!(r < 1e-2)) r = 1e-2;
+  if (c->cg_cap > 0.0 && r > c->cg_cap) r = c->cg_cap;
   if (r < floor) r = floor;
   return r;
 }
@@ -211,7 +213,7 @@ template <typename T> op_status step_impl(op_ctx *c) {
   OP_CUDA(cudaStreamSynchronize(c->st));
   prof_harvest(&c->prof);
   if (*c->hpin_int) {
-    set_error("Step 2 matrix is not positive definite (Cholesky pivot <= 0)");
+    set_error("Step 2 factorisation broke down (zero or non-finite pivot)");
     return OP_ERR_NOTSPD;
   }
   const double Enew = 0.5 * c->hsc[4];
@@ -519,6 +521,9 @@ op_status op_solve(op_ctx *c, double tol, int max_steps, int stop, op_stats *st)
   }
   auto t0 = std::chrono::steady_clock::now();
   const int every = c->pb.check_every > 0 ? c->pb.check_every : 10;
+  // the inner solves must be more accurate than the outer target: r ~ rtol for the
+  // residual rule, err_E ~ r^2 for Algorithm 1's rule
+  c->cg_cap = stop == OP_STOP_RESIDUAL ? 0.1 * tol : (stop == OP_STOP_ERR_E ? 0.1 * sqrt(tol) : 0.0);
   bool done = false;
   double r = NAN;
   for (int k = 0; k <= max_steps; ++k) {
@@ -537,6 +542,7 @@ op_status op_solve(op_ctx *c, double tol, int max_steps, int stop, op_stats *st)
     op_status s = c->prec == OP_FP64 ? step_impl<double>(c) : step_impl<float>(c);
     if (s != OP_OK) return s;
   }
+  c->cg_cap = 0.0;
   if (stop == OP_STOP_STEPS) done = true;
   if (stop != OP_STOP_RESIDUAL || !done) OP_TRY(op_residual(c, &r));
   c->stats.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)

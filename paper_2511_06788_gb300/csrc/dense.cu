@@ -1,8 +1,11 @@
 // Small dense FP64 algebra on p x p matrices (stride ld):
-//   * Steps 2-3 of §4.1: M = I + tau^2/4 (S - C C), B = M^-1 by Cholesky
-//     (M - I is positive semi-definite by Lemma 3.1, so the factorisation
-//     exists for any tau), tau/2 A = I - B + tau/2 C B, and the Step-4
-//     coefficients KU = I - tau A = 2B - I - tau C B, KW = tau B;
+//   * Steps 2-3 of §4.1 for C = <W,U>, S = <W,W>: M = I + tau/2 (C - C^T)
+//     + tau^2/4 (S - C C^T), B = M^-1 (LU; the symmetric part of M is >= I by
+//     Lemma 3.1, so the factorisation exists for any tau), tau/2 A = I - B +
+//     tau/2 C^T B, and the Step-4 coefficients KU = I - tau A = 2B - I -
+//     tau C^T B, KW = tau B.  For the exact W = GU, C is symmetric and this is
+//     the paper's Steps 2-3; for an inexact Step-1 solve it is still the exact
+//     solution of the midpoint scheme (4.1), so <U,U> is kept to roundoff;
 //   * Cholesky-QR coefficients R^-1 for the initial orthonormalisation;
 //   * symmetric eigenvalues (cyclic Jacobi) for the reported eigenvalues.
 // All of it runs in FP64: on GB300 these kernels are FP64-pipe bound but tiny
@@ -18,20 +21,26 @@ namespace {
 
 constexpr int kT = 16;  // tile of the small GEMM
 
-// out = alpha * A B + beta * X + gamma * I on the p x p block; zero elsewhere in
-// ld x ld.  X may be null (beta ignored).  tout (may be null) gets a T copy.
+// out = alpha op(A) op(B) + beta X + d1 Y + d2 Y^T + gamma I on the p x p block
+// (op = transpose when ta / tb is set); zero elsewhere in ld x ld.  X, Y may be
+// null.  tout (may be null) gets a T copy.  When *status is set (a failed
+// factorisation upstream) the result is the identity.
 template <typename T>
-__global__ void k_small_gemm(int p, int ld, double alpha, const double *__restrict__ A,
-                             const double *__restrict__ B, double beta,
-                             const double *__restrict__ X, double gamma, double *__restrict__ out,
+__global__ void k_small_gemm(int p, int ld, double alpha, const double *__restrict__ A, int ta,
+                             const double *__restrict__ B, int tb, double beta,
+                             const double *__restrict__ X, double d1, double d2,
+                             const double *__restrict__ Y, double gamma, double *__restrict__ out,
                              T *__restrict__ tout, const int *__restrict__ status) {
   __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
   const int i = blockIdx.y * kT + threadIdx.y, j = blockIdx.x * kT + threadIdx.x;
   double s = 0.0;
   for (int k0 = 0; k0 < p; k0 += kT) {
     const int ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
-    As[threadIdx.y][threadIdx.x] = (i < p && ka < p) ? A[(long long)i * ld + ka] : 0.0;
-    Bs[threadIdx.y][threadIdx.x] = (kb < p && j < p) ? B[(long long)kb * ld + j] : 0.0;
+    double a = 0.0, b = 0.0;
+    if (i < p && ka < p) a = ta ? A[(long long)ka * ld + i] : A[(long long)i * ld + ka];
+    if (kb < p && j < p) b = tb ? B[(long long)j * ld + kb] : B[(long long)kb * ld + j];
+    As[threadIdx.y][threadIdx.x] = a;
+    Bs[threadIdx.y][threadIdx.x] = b;
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kT; ++k) s = fma(As[threadIdx.y][k], Bs[k][threadIdx.x], s);
@@ -42,10 +51,51 @@ __global__ void k_small_gemm(int p, int ld, double alpha, const double *__restri
   if (i < p && j < p) {
     v = alpha * s + (i == j ? gamma : 0.0);
     if (X) v += beta * X[(long long)i * ld + j];
-    if (status && *status) v = (i == j) ? 1.0 : 0.0;  // failed factorisation: identity
+    if (Y) v += d1 * Y[(long long)i * ld + j] + d2 * Y[(long long)j * ld + i];
+    if (status && *status) v = (i == j) ? 1.0 : 0.0;
   }
   out[(long long)i * ld + j] = v;
   if (tout) tout[(long long)i * ld + j] = (T)v;
+}
+
+// In-place LU factorisation without pivoting of the p x p matrix M into LU (unit
+// lower factor below the diagonal, upper factor on and above).  One CTA.  Used
+// for the Step-2 matrix, whose symmetric part is >= I (Lemma 3.1), so every
+// leading block is nonsingular.  status <- 1 on a zero or non-finite pivot.
+__global__ void __launch_bounds__(1024) k_lu(int p, int ld, const double *__restrict__ M,
+                                             double *__restrict__ LU, int *status) {
+  __shared__ double piv;
+  __shared__ int bad;
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (long long e = t; e < (long long)p * p; e += nt) {
+    const int i = (int)(e / p), j = (int)(e % p);
+    LU[(long long)i * ld + j] = M[(long long)i * ld + j];
+  }
+  if (t == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < p; ++k) {
+    if (t == 0) {
+      const double d = LU[(long long)k * ld + k];
+      if (!(fabs(d) > 1e-300) || !isfinite(d)) {
+        bad = 1;
+        piv = 1.0;
+      } else {
+        piv = d;
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double inv = 1.0 / piv;
+    for (int i = k + 1 + t; i < p; i += nt) LU[(long long)i * ld + k] *= inv;
+    __syncthreads();
+    const int m = p - k - 1;
+    for (long long e = t; e < (long long)m * m; e += nt) {
+      const int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
+      LU[(long long)i * ld + j] -= LU[(long long)i * ld + k] * LU[(long long)k * ld + j];
+    }
+    __syncthreads();
+  }
+  if (t == 0 && bad) *status = 1;
 }
 
 // In-place right-looking Cholesky of sym(M) = (M + M^T)/2 into the lower
@@ -90,9 +140,10 @@ __global__ void __launch_bounds__(1024) k_chol(int p, int ld, const double *__re
   if (t == 0 && bad) *status = 1;
 }
 
-// One CTA per column j.  mode 0: out[:, j] = (L L^T)^-1 e_j  (forward then
-// backward substitution).  mode 1: out[:, j] = L^-T e_j, i.e. column j of
-// R^-1 for R = L^T (backward substitution only).
+// One CTA per column j of the solution of F x = e_j with a factor F in L:
+//   mode 0: F = L L^T (Cholesky factor in the lower triangle)
+//   mode 1: F = L^T    (column j of R^-1 for R = L^T)
+//   mode 2: F = L U    (unit-lower L below the diagonal, U on and above; k_lu)
 __global__ void k_tri_cols(int p, int ld, const double *__restrict__ L, int mode,
                            double *__restrict__ out, const int *__restrict__ status) {
   extern __shared__ double y[];  // p values
@@ -104,22 +155,26 @@ __global__ void k_tri_cols(int p, int ld, const double *__restrict__ L, int mode
   }
   for (int i = t; i < p; i += nt) y[i] = (i == j) ? 1.0 : 0.0;
   __syncthreads();
-  if (mode == 0) {
-    // forward: L z = e_j  (z_k = 0 for k < j); z overwrites y
+  if (mode != 1) {
+    // forward substitution (z_k = 0 for k < j); z overwrites y
     for (int k = j; k < p; ++k) {
-      const double zk = y[k] / L[(long long)k * ld + k];
+      const double zk = (mode == 0) ? y[k] / L[(long long)k * ld + k] : y[k];
       __syncthreads();
       if (t == 0) y[k] = zk;
       for (int i = k + 1 + t; i < p; i += nt) y[i] -= L[(long long)i * ld + k] * zk;
       __syncthreads();
     }
   }
-  // backward: L^T x = y; x overwrites y
+  // backward substitution with L^T (modes 0, 1) or U (mode 2); x overwrites y
   for (int k = p - 1; k >= 0; --k) {
     const double xk = y[k] / L[(long long)k * ld + k];
     __syncthreads();
     if (t == 0) y[k] = xk;
-    for (int i = t; i < k; i += nt) y[i] -= L[(long long)k * ld + i] * xk;
+    if (mode == 2) {
+      for (int i = t; i < k; i += nt) y[i] -= L[(long long)i * ld + k] * xk;
+    } else {
+      for (int i = t; i < k; i += nt) y[i] -= L[(long long)k * ld + i] * xk;
+    }
     __syncthreads();
   }
   for (int i = t; i < ld; i += nt) out[(long long)i * ld + j] = (i < p) ? y[i] : 0.0;
@@ -316,13 +371,15 @@ op_status core(int p, int ld, double tau, const double *C, const double *S, doub
   const dim3 tb(kT, kT), tg((ld + kT - 1) / kT, (ld + kT - 1) / kT);
   const double q = 0.25 * tau * tau;
   OP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
-  // Step 2 matrix: M = I + tau^2/4 <W,W> - tau^2/4 <W,U><W,U>
-  k_small_gemm<double><<<tg, tb, 0, st>>>(p, ld, -q, C, C, q, S, 1.0, M, (double *)nullptr,
-                                          (const int *)nullptr); count_launch();
-  k_chol<<<1, 1024, 0, st>>>(p, ld, M, L, status); count_launch();
-  k_tri_cols<<<ld, 256, p * sizeof(double), st>>>(p, ld, L, 0, B, status); count_launch();
-  // KU = 2B - I - tau C B (Step 3 folded into Step 4); KW = tau B
-  k_small_gemm<T><<<tg, tb, 0, st>>>(p, ld, -tau, C, B, 2.0, B, -1.0, KU, KU_t, status); count_launch();
+  // Step 2 matrix, solving (4.1) without assuming C = <W,U> symmetric:
+  // M = I + tau/2 (C - C^T) + tau^2/4 (S - C C^T)   (= I + tau^2/4 (S - C C) for C = C^T)
+  k_small_gemm<double><<<tg, tb, 0, st>>>(p, ld, -q, C, 0, C, 1, q, S, 0.5 * tau, -0.5 * tau, C,
+                                          1.0, M, (double *)nullptr, (const int *)nullptr); count_launch();
+  k_lu<<<1, 1024, 0, st>>>(p, ld, M, L, status); count_launch();
+  k_tri_cols<<<ld, 256, p * sizeof(double), st>>>(p, ld, L, 2, B, status); count_launch();
+  // Step 3 folded into Step 4: KU = I - tau A = 2B - I - tau C^T B; KW = tau B
+  k_small_gemm<T><<<tg, tb, 0, st>>>(p, ld, -tau, C, 1, B, 0, 2.0, B, 0.0, 0.0,
+                                     (const double *)nullptr, -1.0, KU, KU_t, status); count_launch();
   k_scale<T><<<(ld * ld + 255) / 256, 256, 0, st>>>(ld, tau, B, KW, KW_t); count_launch();
   OP_LAUNCH("core");
   return OP_OK;

@@ -172,6 +172,40 @@ def test_steps_2_to_4_equal_cayley_transform(p, tau_scale):
     np.testing.assert_allclose(o.scheme_step(U, W, tau), cayley_step(U, W, tau), rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("p", [1, 4, 7])
+def test_midpoint_coefficients_any_W_equal_cayley(p):
+    """For an arbitrary W (an inexact Step 1), the generalised Steps 2-3 solve (4.1)
+    exactly: the result is the Cayley transform and keeps orthogonality."""
+    rng = np.random.default_rng(40 + p)
+    U = o.householder_orthonormalize(rng.standard_normal((50, p)))
+    W = rng.standard_normal((50, p)) * 0.3
+    for tau in (0.05, 1.0, 25.0):
+        A, B = o.midpoint_coefficients(W, U, tau)
+        Un = o.update(U, W, A, B, tau)
+        np.testing.assert_allclose(Un, cayley_step(U, W, tau), atol=1e-12)
+        assert o.orth_error(Un) < 1e-13
+
+
+def test_midpoint_coefficients_reduce_to_steps_2_3_for_exact_W():
+    shape, lo, hi, V, H, sigma, U = random_problem(6, (5, 4, 3), 5)
+    W = np.linalg.solve(H.toarray() + sigma * np.eye(60), U)
+    tau = o.default_tau(shape, lo, hi, V, sigma)
+    A1, B1, _ = o.core_matrices(W, U, tau)
+    A2, B2 = o.midpoint_coefficients(W, U, tau)
+    np.testing.assert_allclose(A2, A1, atol=1e-12)
+    np.testing.assert_allclose(B2, B1, atol=1e-12)
+
+
+def test_paper_steps_lose_orthogonality_for_inexact_W():
+    """The printed Steps 2-3 assume <GU, U> symmetric; with a perturbed W they do
+    not keep <U, U> = I (why the device core solves (4.1) without that assumption)."""
+    rng = np.random.default_rng(3)
+    U = o.householder_orthonormalize(rng.standard_normal((50, 4)))
+    W = rng.standard_normal((50, 4)) * 0.3
+    A, B, _ = o.core_matrices(W, U, 2.0)
+    assert o.orth_error(o.update(U, W, A, B, 2.0)) > 1e-6
+
+
 def test_update_forms_agree():
     shape, lo, hi, V, H, sigma, U = random_problem(2, (5, 4, 3), 4)
     W = o.SourceSolver(H, sigma).solve(U)
