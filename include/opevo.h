@@ -196,15 +196,24 @@ size_t op_cg_workspace(const op_problem *pb, int ld);
 
 /* Inner matrices of [U W] (§2.1): C = <W,U> (C_ij = w_i . u_j), S = <W,W>, D = <U,U>,
  * each ld x ld FP64 row-major on the device (entries with i or j >= p are zero).
- * Any of C, S, D may be NULL to skip it.  Partial sums over grid-point chunks are
- * accumulated in FP64.  ws: device scratch of at least op_gram_workspace() bytes. */
+ * Any of C, S, D may be NULL to skip it.  OP_FP64: FP64 FMA, chunk partials in FP64.
+ * OP_FP32: tcgen05 tensor-core MMAs (TF32 inputs split hi + lo, three MMAs per
+ * product, FP32 accumulation per chunk of grid points, chunk partials summed in FP64).
+ * ws: device scratch of at least op_gram_workspace() bytes; its first int is set when a
+ * bounded device wait gave up (check with op_ws_status). */
 op_status op_gram(int prec, long long n, int p, int ld, const void *U, const void *W,
                   double *C, double *S, double *D, void *ws, size_t ws_bytes, void *stream);
 size_t op_gram_workspace(int prec, long long n, int ld);
 
+/* Synchronises `stream`; OP_ERR_TIMEOUT if the last op_gram / op_update on ws reported a
+ * bounded device wait that gave up, else OP_OK. */
+op_status op_ws_status(void *ws, void *stream);
+
 /* Steps 2-3 of §4.1 in FP64: from C = <W,U>, S = <W,W> (ld x ld device, FP64) form
- * M = I + tau/2 (C - C^T) + tau^2/4 (S - C C^T), B = M^-1 (LU without pivoting; the
- * symmetric part of M is >= I by Lemma 3.1), tau/2 A = I - B + tau/2 C^T B, and the
+ * M = I + tau/2 (C - C^T) + tau^2/4 (S - C C^T), B = M^-1 (p <= 128: FP32 Gauss-Jordan
+ * refined by FP64 Newton-Schulz steps, two for OP_FP64 and one for OP_FP32; larger p:
+ * FP64 LU; no pivoting is needed because the symmetric part of M is >= I by
+ * Lemma 3.1), tau/2 A = I - B + tau/2 C^T B, and the
  * Step-4 coefficients KU = I - tau A = 2B - I - tau C^T B, KW = tau B (ld x ld FP64
  * device, zero outside p x p).  For the exact W = GU (C symmetric) these are the
  * paper's Steps 2-3; for any other W they solve the midpoint scheme (4.1) exactly
@@ -220,9 +229,13 @@ size_t op_core_workspace(int p, int ld);
 op_status op_core_status(void *ws, void *stream);
 
 /* Step 4: Unew = U KU + W KW (KU, KW: ld x ld in the block type T, device).
- * Unew must not alias U or W. */
+ * OP_FP64: FP64 FMA.  OP_FP32: tcgen05 tensor-core MMAs with the 3xTF32 split (as in
+ * op_gram).  Unew must not alias U or W.  ws: device scratch of at least
+ * op_update_workspace() bytes (first int: timeout flag, see op_ws_status). */
 op_status op_update(int prec, long long n, int p, int ld, const void *U, const void *W,
-                    const void *KU_t, const void *KW_t, void *Unew, void *stream);
+                    const void *KU_t, const void *KW_t, void *Unew, void *ws, size_t ws_bytes,
+                    void *stream);
+size_t op_update_workspace(int prec, int ld);
 
 #ifdef __cplusplus
 }

@@ -90,7 +90,9 @@ def lib():
         "op_core": (i32, [i32, i32, i32, f64, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
         "op_core_workspace": (sz, [i32, i32]),
         "op_core_status": (i32, [vp, vp]),
-        "op_update": (i32, [i32, C.c_longlong, i32, i32, vp, vp, vp, vp, vp, vp]),
+        "op_update": (i32, [i32, C.c_longlong, i32, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
+        "op_update_workspace": (sz, [i32, i32]),
+        "op_ws_status": (i32, [vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -292,8 +294,10 @@ def gram(U, W, p, want=("C", "S", "D"), stream=None):
            for k in ("C", "S", "D")}
     nbytes = lib().op_gram_workspace(prec, n, ld)
     ws = torch.empty(nbytes, dtype=torch.uint8, device=U.device)
+    st = _stream_ptr(stream)
     check(lib().op_gram(prec, n, p, ld, _tptr(U), _tptr(W), _tptr(out["C"]), _tptr(out["S"]),
-                        _tptr(out["D"]), _tptr(ws), nbytes, _stream_ptr(stream)))
+                        _tptr(out["D"]), _tptr(ws), nbytes, st))
+    check(lib().op_ws_status(_tptr(ws), st))
     return out["C"], out["S"], out["D"]
 
 
@@ -322,6 +326,10 @@ def update(U, W, KU_t, KW_t, p, out=None, stream=None):
     prec = _prec_of(U)
     if out is None:
         out = torch.empty_like(U)
+    nbytes = lib().op_update_workspace(prec, ld)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=U.device)
+    st = _stream_ptr(stream)
     check(lib().op_update(prec, n, p, ld, _tptr(U), _tptr(W), _tptr(KU_t), _tptr(KW_t),
-                          _tptr(out), _stream_ptr(stream)))
+                          _tptr(out), _tptr(ws), nbytes, st))
+    check(lib().op_ws_status(_tptr(ws), st))
     return out

@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <chrono>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -91,6 +92,8 @@ struct op_ctx {
   // p x p (ld x ld) FP64 matrices
   double *C, *S, *D, *KU, *KW, *Th, *eig_work, *lam_d;
   void *KU_t, *KW_t;
+  float *KT_hi, *KT_lo;  // FP32 blocks: [KU; KW]^T split for the tensor-core update
+  int *dev_err;          // set by a tensor-core kernel whose bounded wait gave up
   void *cg_ws, *gram_ws, *core_ws;
   size_t gram_bytes;
   CGWork cgw;
@@ -179,6 +182,16 @@ template <typename T> op_status energy_impl(op_ctx *c) {
   return OP_OK;
 }
 
+// Inner matrices: FP32 blocks on the tensor cores, FP64 blocks on the FP64 pipe.
+template <typename T>
+op_status gram_any(op_ctx *c, const T *U, const T *W, double *C, double *S, double *D) {
+  if constexpr (std::is_same<T, float>::value)
+    return gram_tc(c->n, c->p, c->ld, U, W, C, S, D, c->gram_ws, c->gram_bytes, c->dev_err,
+                   c->st);
+  else
+    return gram<T>(c->n, c->p, c->ld, U, W, C, S, D, c->gram_ws, c->gram_bytes, c->st);
+}
+
 template <typename T> op_status step_impl(op_ctx *c) {
   int iters = 0;
   // Step 1: W = (H + sigma)^-1 U, warm-started from the previous W
@@ -186,8 +199,7 @@ template <typename T> op_status step_impl(op_ctx *c) {
                      cg_rtol_for(c), cg_max_iter(c), c->cgw, &iters, c->st));
   // inner matrices <W,U>, <W,W>, <U,U>
   prof_begin(&c->prof, PK_GRAM, c->st);
-  OP_TRY(gram<T>(c->n, c->p, c->ld, (const T *)c->U, (const T *)c->W, c->C, c->S, c->D,
-                 c->gram_ws, c->gram_bytes, c->st));
+  OP_TRY(gram_any<T>(c, (const T *)c->U, (const T *)c->W, c->C, c->S, c->D));
   prof_end(&c->prof, c->st);
   // Steps 2-3 (FP64) and the Step-4 coefficients
   prof_begin(&c->prof, PK_CORE, c->st);
@@ -197,8 +209,14 @@ template <typename T> op_status step_impl(op_ctx *c) {
   prof_end(&c->prof, c->st);
   // Step 4
   prof_begin(&c->prof, PK_UPDATE, c->st);
-  OP_TRY(update<T>(c->n, c->ld, (const T *)c->U, (const T *)c->W, (const T *)c->KU_t,
-                   (const T *)c->KW_t, (T *)c->U2, c->st));
+  if constexpr (std::is_same<T, float>::value) {
+    OP_TRY(launch_make_kt(c->ld, c->KU, c->KW, c->KT_hi, c->KT_lo, c->st));
+    OP_TRY(update_tc(c->n, c->ld, (const float *)c->U, (const float *)c->W, c->KT_hi, c->KT_lo,
+                     (float *)c->U2, c->dev_err, c->st));
+  } else {
+    OP_TRY(update<T>(c->n, c->ld, (const T *)c->U, (const T *)c->W, (const T *)c->KU_t,
+                     (const T *)c->KW_t, (T *)c->U2, c->st));
+  }
   prof_end(&c->prof, c->st);
   void *tmp = c->U;
   c->U = c->U2;
@@ -210,8 +228,13 @@ template <typename T> op_status step_impl(op_ctx *c) {
   prof_end(&c->prof, c->st);
   OP_CUDA(cudaMemcpyAsync(c->hsc, c->dsc, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   OP_CUDA(cudaMemcpyAsync(c->hpin_int, c->core_ws, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  OP_CUDA(cudaMemcpyAsync(c->hpin_int + 1, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   OP_CUDA(cudaStreamSynchronize(c->st));
   prof_harvest(&c->prof);
+  if (c->hpin_int[1]) {
+    set_error("a tensor-core kernel timed out waiting for its MMAs (bounded mbarrier wait)");
+    return OP_ERR_TIMEOUT;
+  }
   if (*c->hpin_int) {
     set_error("Step 2 factorisation broke down (zero or non-finite pivot)");
     return OP_ERR_NOTSPD;
@@ -238,8 +261,7 @@ template <typename T> op_status residual_impl(op_ctx *c, double *r) {
   T *Y = (T *)c->cgw.Q, *Z = (T *)c->cgw.R;
   prof_begin(&c->prof, PK_RESIDUAL, c->st);
   OP_TRY(launch_apply<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, Y, c->ld, c->st));
-  OP_TRY(gram<T>(c->n, c->p, c->ld, (const T *)c->U, Y, c->Th, nullptr, nullptr, c->gram_ws,
-                 c->gram_bytes, c->st));
+  OP_TRY(gram_any<T>(c, (const T *)c->U, Y, c->Th, nullptr, nullptr));
   OP_TRY(launch_resid_coeff<T>(c->p, c->ld, c->Th, (T *)c->KU_t, (T *)c->KW_t, c->st));
   OP_TRY(update<T>(c->n, c->ld, (const T *)c->U, Y, (const T *)c->KU_t, (const T *)c->KW_t, Z,
                    c->st));
@@ -257,16 +279,14 @@ template <typename T> op_status eig_impl(op_ctx *c, double *lam, int kind) {
   if (kind == OP_EIG_RITZ) {
     T *Y = (T *)c->cgw.Q;
     OP_TRY(launch_apply<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, Y, c->ld, c->st));
-    OP_TRY(gram<T>(c->n, c->p, c->ld, (const T *)c->U, Y, c->Th, nullptr, nullptr, c->gram_ws,
-                   c->gram_bytes, c->st));
+    OP_TRY(gram_any<T>(c, (const T *)c->U, Y, c->Th, nullptr, nullptr));
     OP_TRY(sym_eigvals(c->p, c->ld, c->Th, c->eig_work, c->lam_d, c->st));
   } else {
     int iters = 0;
     const double tight = c->prec == OP_FP64 ? 1e-13 : 1e-6;
     OP_TRY(cg_solve<T>(c->g, (const T *)c->Vt, c->sigma, (const T *)c->U, (T *)c->W, c->p, c->ld,
                        tight, 20000, c->cgw, &iters, c->st));
-    OP_TRY(gram<T>(c->n, c->p, c->ld, (const T *)c->U, (const T *)c->W, c->Th, nullptr, nullptr,
-                   c->gram_ws, c->gram_bytes, c->st));
+    OP_TRY(gram_any<T>(c, (const T *)c->U, (const T *)c->W, c->Th, nullptr, nullptr));
     OP_TRY(sym_eigvals(c->p, c->ld, c->Th, c->eig_work, c->eig_work + (size_t)c->p * c->p,
                        c->st));
     OP_TRY(launch_paper_lams(c->p, c->eig_work + (size_t)c->p * c->p, c->sigma, c->lam_d, c->st));
@@ -389,15 +409,25 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
   cg_carve(c->cg_ws, n, ld, sizeof(T), &c->cgw);
   c->cgw.prof = &c->prof;
   c->gram_bytes = gram_workspace_bytes(n, ld, sizeof(T));
+  if (sizeof(T) == 4) {
+    const size_t tcb = gram_tc_workspace_bytes(n, ld);
+    if (tcb > c->gram_bytes) c->gram_bytes = tcb;
+    OP_TRY(dev_alloc(c, &p, 2 * (size_t)ld * 2 * ld * sizeof(float)));
+    c->KT_hi = (float *)p;
+    c->KT_lo = c->KT_hi + (size_t)ld * 2 * ld;
+  }
   OP_TRY(dev_alloc(c, &c->gram_ws, c->gram_bytes));
+  OP_TRY(dev_alloc(c, &p, 256));
+  c->dev_err = (int *)p;
+  OP_CUDA(cudaMemsetAsync(c->dev_err, 0, 256, c->st));
   OP_TRY(dev_alloc(c, &c->core_ws, core_workspace_bytes(c->p, ld)));
-  OP_TRY(dev_alloc(c, &p, (size_t)kNumSMs * 8 * 2 * ld * sizeof(double)));
+  OP_TRY(dev_alloc(c, &p, part_bytes(ld)));
   c->part = (double *)p;
   OP_TRY(dev_alloc(c, &p, 64 * sizeof(double)));
   c->dsc = (double *)p;
   OP_CUDA(cudaMallocHost((void **)&c->hsc, 64 * sizeof(double)));
   OP_CUDA(cudaMallocHost((void **)&c->hpin_int, 16 * sizeof(int)));
-  c->cgw.nactive_host = c->hpin_int + 4;
+  c->cgw.host_ctl = c->hpin_int + 4;
   OP_CUDA(cudaMemsetAsync(c->W, 0, blk, c->st));
   OP_CUDA(cudaMemsetAsync(c->U2, 0, blk, c->st));
 
@@ -695,8 +725,8 @@ op_status op_cg_solve(const op_problem *pb, int ld, const void *V_t, double sigm
   const int elem = pb->prec == OP_FP64 ? 8 : 4;
   CGWork w;
   cg_carve(ws, g.n, ld, elem, &w);
-  int nact = 0;
-  w.nactive_host = &nact;
+  int host_ctl[4] = {0, 0, 0, 0};
+  w.host_ctl = host_ctl;
   cudaStream_t st = (cudaStream_t)stream;
   op_status s;
   if (pb->prec == OP_FP64)
@@ -708,21 +738,45 @@ op_status op_cg_solve(const op_problem *pb, int ld, const void *V_t, double sigm
   return s;
 }
 
+// Kernel-level scratch of op_gram / op_update starts with a 256-byte header whose first
+// int is the "bounded device wait gave up" flag (read back by op_ws_status).
+static const size_t kWsHeader = 256;
+
 size_t op_gram_workspace(int prec, long long n, int ld) {
-  return gram_workspace_bytes(n, ld, prec == OP_FP64 ? 8 : 4);
+  if (prec == OP_FP32) return kWsHeader + gram_tc_workspace_bytes(n, ld);
+  return kWsHeader + gram_workspace_bytes(n, ld, 8);
 }
 
 op_status op_gram(int prec, long long n, int p, int ld, const void *U, const void *W, double *C,
                   double *S, double *D, void *ws, size_t ws_bytes, void *stream) {
   OP_TRY(check_blocks(prec, p, ld, U, W));
-  if (n < 1) {
-    set_error("n must be positive");
+  if (n < 1 || !ws || ws_bytes < kWsHeader) {
+    set_error("op_gram: n must be positive and ws hold at least op_gram_workspace() bytes");
     return OP_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  OP_CUDA(cudaMemsetAsync(ws, 0, sizeof(int), st));
+  void *part = (char *)ws + kWsHeader;
+  const size_t pbytes = ws_bytes - kWsHeader;
   if (prec == OP_FP64)
-    return gram<double>(n, p, ld, (const double *)U, (const double *)W, C, S, D, ws, ws_bytes, st);
-  return gram<float>(n, p, ld, (const float *)U, (const float *)W, C, S, D, ws, ws_bytes, st);
+    return gram<double>(n, p, ld, (const double *)U, (const double *)W, C, S, D, part, pbytes, st);
+  return gram_tc(n, p, ld, (const float *)U, (const float *)W, C, S, D, part, pbytes, (int *)ws,
+                 st);
+}
+
+op_status op_ws_status(void *ws, void *stream) {
+  if (!ws) {
+    set_error("null workspace");
+    return OP_ERR_ARG;
+  }
+  int h = 0;
+  OP_CUDA(cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  OP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (h) {
+    set_error("a bounded device wait gave up (tensor-core pipeline did not complete)");
+    return OP_ERR_TIMEOUT;
+  }
+  return OP_OK;
 }
 
 size_t op_core_workspace(int p, int ld) { return core_workspace_bytes(p, ld); }
@@ -760,19 +814,30 @@ op_status op_core_status(void *ws, void *stream) {
   return OP_OK;
 }
 
+size_t op_update_workspace(int prec, int ld) {
+  return kWsHeader + (prec == OP_FP32 ? 2 * (size_t)ld * 2 * ld * sizeof(float) : 0);
+}
+
 op_status op_update(int prec, long long n, int p, int ld, const void *U, const void *W,
-                    const void *KU_t, const void *KW_t, void *Unew, void *stream) {
+                    const void *KU_t, const void *KW_t, void *Unew, void *ws, size_t ws_bytes,
+                    void *stream) {
   OP_TRY(check_blocks(prec, p, ld, U, W));
-  if (!KU_t || !KW_t || !Unew || n < 1 || Unew == U || Unew == W) {
-    set_error("op_update: bad arguments");
+  if (!KU_t || !KW_t || !Unew || n < 1 || Unew == U || Unew == W || !ws ||
+      ws_bytes < op_update_workspace(prec, ld)) {
+    set_error("op_update: bad arguments (outputs must not alias inputs; ws >= "
+              "op_update_workspace())");
     return OP_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  OP_CUDA(cudaMemsetAsync(ws, 0, sizeof(int), st));
   if (prec == OP_FP64)
     return update<double>(n, ld, (const double *)U, (const double *)W, (const double *)KU_t,
                           (const double *)KW_t, (double *)Unew, st);
-  return update<float>(n, ld, (const float *)U, (const float *)W, (const float *)KU_t,
-                       (const float *)KW_t, (float *)Unew, st);
+  float *KT_hi = (float *)((char *)ws + kWsHeader);
+  float *KT_lo = KT_hi + (size_t)ld * 2 * ld;
+  OP_TRY(launch_make_kt_f32(ld, (const float *)KU_t, (const float *)KW_t, KT_hi, KT_lo, st));
+  return update_tc(n, ld, (const float *)U, (const float *)W, KT_hi, KT_lo, (float *)Unew,
+                   (int *)ws, st);
 }
 
 }  // extern "C"

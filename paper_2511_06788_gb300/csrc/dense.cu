@@ -12,6 +12,8 @@
 // next to the n x p work (O(p^3) vs O(n p^2)).
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -19,31 +21,39 @@ namespace opevo {
 
 namespace {
 
-constexpr int kT = 16;  // tile of the small GEMM
+constexpr int kT = 8;  // tile of the small GEMM (8 x 8 outputs per CTA: many CTAs for p ~ 100)
 
 // out = alpha op(A) op(B) + beta X + d1 Y + d2 Y^T + gamma I on the p x p block
 // (op = transpose when ta / tb is set); zero elsewhere in ld x ld.  X, Y may be
 // null.  tout (may be null) gets a T copy.  When *status is set (a failed
 // factorisation upstream) the result is the identity.
+// One CTA of kT x kT threads per kT x kT output tile; the kT-row panel of op(A)
+// and the kT-column panel of op(B) are loaded for KC values of k at a time, all
+// loads in flight together (one L2 round trip per chunk).
+constexpr int kKC = 128;
 template <typename T>
 __global__ void k_small_gemm(int p, int ld, double alpha, const double *__restrict__ A, int ta,
                              const double *__restrict__ B, int tb, double beta,
                              const double *__restrict__ X, double d1, double d2,
                              const double *__restrict__ Y, double gamma, double *__restrict__ out,
                              T *__restrict__ tout, const int *__restrict__ status) {
-  __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
-  const int i = blockIdx.y * kT + threadIdx.y, j = blockIdx.x * kT + threadIdx.x;
+  __shared__ double As[kT][kKC + 1], Bs[kKC][kT + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * kT + tx;
+  const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
+  const int i = i0 + ty, j = j0 + tx;
   double s = 0.0;
-  for (int k0 = 0; k0 < p; k0 += kT) {
-    const int ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
-    double a = 0.0, b = 0.0;
-    if (i < p && ka < p) a = ta ? A[(long long)ka * ld + i] : A[(long long)i * ld + ka];
-    if (kb < p && j < p) b = tb ? B[(long long)j * ld + kb] : B[(long long)kb * ld + j];
-    As[threadIdx.y][threadIdx.x] = a;
-    Bs[threadIdx.y][threadIdx.x] = b;
+  for (int k0 = 0; k0 < p; k0 += kKC) {
+    for (int e = t; e < kT * kKC; e += kT * kT) {
+      const int r = e / kKC, k = k0 + e % kKC, ii = i0 + r;
+      As[r][e % kKC] = (ii < p && k < p) ? (ta ? A[(long long)k * ld + ii] : A[(long long)ii * ld + k])
+                                         : 0.0;
+      const int c = e % kT, kb = k0 + e / kT, jj = j0 + c;
+      Bs[e / kT][c] = (kb < p && jj < p) ? (tb ? B[(long long)jj * ld + kb] : B[(long long)kb * ld + jj])
+                                         : 0.0;
+    }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kT; ++k) s = fma(As[threadIdx.y][k], Bs[k][threadIdx.x], s);
+    const int kn = (p - k0) < kKC ? (p - k0) : kKC;
+    for (int k = 0; k < kn; ++k) s = fma(As[ty][k], Bs[k][tx], s);
     __syncthreads();
   }
   if (i >= ld || j >= ld) return;
@@ -180,14 +190,97 @@ __global__ void k_tri_cols(int p, int ld, const double *__restrict__ L, int mode
   for (int i = t; i < ld; i += nt) out[(long long)i * ld + j] = (i < p) ? y[i] : 0.0;
 }
 
-// KW = tau B (FP64 and T copies).
+// Inverse of the p x p matrix M (stride ld, p <= 128) in FP32 by Gauss-Jordan
+// elimination without pivoting, one CTA of 32 x 32 threads.  [M | I] is padded to
+// 128 x 256 with an identity block and held in registers: thread (tx, ty) owns
+// rows ty + 32a (a < 4) and columns tx + 32b (b < 8).  Step k publishes row k
+// and column k through shared memory (double-buffered: one barrier per step) and
+// every thread updates its 32 entries.  The result seeds the FP64 Newton-Schulz
+// refinement in core(): on GB300 an FP64 factorisation on one SM costs
+// ~p^3/3 / (2 FMA/clk), while FP32 runs 64x faster.
+// status <- 1 on a zero or non-finite pivot.
+__global__ void __launch_bounds__(1024) k_gj32(int p, int ld, const double *__restrict__ M,
+                                               double *__restrict__ X, int *status) {
+  __shared__ float rowk[2][256];
+  __shared__ float colk[2][128];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float v[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = ty + 32 * a, j = tx + 32 * b;
+      float x;
+      if (j < 128) x = (i < p && j < p) ? (float)M[(long long)i * ld + j] : (i == j ? 1.f : 0.f);
+      else x = (j - 128 == i) ? 1.f : 0.f;
+      v[a][b] = x;
+    }
+  bool bad = false;
+#pragma unroll 1
+  for (int ak = 0; ak < 4; ++ak) {
+#pragma unroll 1
+    for (int rk = 0; rk < 32; ++rk) {
+      const int k = 32 * ak + rk, buf = k & 1;
+      // publish row k (owners: ty == rk) and column k (owners: tx == rk)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        if (a == ak && ty == rk) {
+#pragma unroll
+          for (int b = 0; b < 8; ++b) rowk[buf][tx + 32 * b] = v[a][b];
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (b == ak && tx == rk) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) colk[buf][ty + 32 * a] = v[a][b];
+        }
+      }
+      __syncthreads();
+      const float d = rowk[buf][k];
+      if (!(fabsf(d) > 1e-30f) || !isfinite(d)) {
+        bad = true;  // uniform: every thread reads the same pivot
+        break;
+      }
+      const float pinv = 1.f / d;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = ty + 32 * a;
+        const float f = colk[buf][i] * pinv;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const float r = rowk[buf][tx + 32 * b];
+          v[a][b] = (i == k) ? r * pinv : fmaf(-f, r, v[a][b]);
+        }
+      }
+    }
+    if (bad) break;
+  }
+  if (bad) {
+    if (tx == 0 && ty == 0) *status = 1;
+    return;
+  }
+  // right half: M^-1 (rows and columns >= p are the padding identity)
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 4; b < 8; ++b) {
+      const int i = ty + 32 * a, j = tx + 32 * b - 128;
+      if (i < ld && j < ld) X[(long long)i * ld + j] = (i < p && j < p) ? (double)v[a][b] : 0.0;
+    }
+  // entries of X beyond the 128 x 128 block (ld > 128 cannot occur here: p <= 128 gives
+  // ld <= 128)
+}
+
+// KW = tau B (FP64 and T copies); zero after a factorisation breakdown.
 template <typename T>
 __global__ void k_scale(int ld, double tau, const double *__restrict__ B, double *__restrict__ KW,
-                        T *__restrict__ KW_t) {
+                        T *__restrict__ KW_t, const int *__restrict__ status) {
   const long long total = (long long)ld * ld;
+  const bool failed = *status != 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const double v = tau * B[e];
+    const double v = failed ? 0.0 : tau * B[e];
     KW[e] = v;
     if (KW_t) KW_t[e] = (T)v;
   }
@@ -358,7 +451,7 @@ __global__ void k_convert(int count, const double *__restrict__ src, T *__restri
 
 size_t core_workspace_bytes(int p, int ld) {
   (void)p;
-  return 256 + 3 * (size_t)ld * ld * sizeof(double);
+  return 256 + 4 * (size_t)ld * ld * sizeof(double);
 }
 
 template <typename T>
@@ -368,19 +461,50 @@ op_status core(int p, int ld, double tau, const double *C, const double *S, doub
   double *M = (double *)((char *)ws + 256);
   double *L = M + (size_t)ld * ld;
   double *B = L + (size_t)ld * ld;
+  double *R = B + (size_t)ld * ld;
   const dim3 tb(kT, kT), tg((ld + kT - 1) / kT, (ld + kT - 1) / kT);
   const double q = 0.25 * tau * tau;
   OP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
   // Step 2 matrix, solving (4.1) without assuming C = <W,U> symmetric:
   // M = I + tau/2 (C - C^T) + tau^2/4 (S - C C^T)   (= I + tau^2/4 (S - C C) for C = C^T)
   k_small_gemm<double><<<tg, tb, 0, st>>>(p, ld, -q, C, 0, C, 1, q, S, 0.5 * tau, -0.5 * tau, C,
-                                          1.0, M, (double *)nullptr, (const int *)nullptr); count_launch();
-  k_lu<<<1, 1024, 0, st>>>(p, ld, M, L, status); count_launch();
-  k_tri_cols<<<ld, 256, p * sizeof(double), st>>>(p, ld, L, 2, B, status); count_launch();
+                                          1.0, M, (double *)nullptr, (const int *)nullptr);
+  count_launch();
+  if (p <= 128) {
+    // B = M^-1: FP32 Gauss-Jordan, then Newton-Schulz X <- X + X (I - M X) in FP64
+    // (each step squares the residual: 1e-7 -> 1e-14 -> roundoff)
+    k_gj32<<<1, dim3(32, 32), 0, st>>>(p, ld, M, L, status);
+    count_launch();
+    const int nref = std::is_same<T, double>::value ? 2 : 1;
+    double *X = L, *Xn = B;
+    for (int r = 0; r < nref; ++r) {
+      k_small_gemm<double><<<tg, tb, 0, st>>>(p, ld, -1.0, M, 0, X, 0, 0.0, (const double *)nullptr,
+                                              0.0, 0.0, (const double *)nullptr, 1.0, R,
+                                              (double *)nullptr, (const int *)nullptr);
+      count_launch();
+      k_small_gemm<double><<<tg, tb, 0, st>>>(p, ld, 1.0, X, 0, R, 0, 1.0, X, 0.0, 0.0,
+                                              (const double *)nullptr, 0.0, Xn, (double *)nullptr,
+                                              (const int *)nullptr);
+      count_launch();
+      double *tmp = X;
+      X = Xn;
+      Xn = tmp;
+    }
+    if (X != B)
+      OP_CUDA(cudaMemcpyAsync(B, X, (size_t)ld * ld * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    // larger cores: FP64 LU on one CTA, then the inverse by substitution
+    k_lu<<<1, 1024, 0, st>>>(p, ld, M, L, status);
+    count_launch();
+    k_tri_cols<<<ld, 256, p * sizeof(double), st>>>(p, ld, L, 2, B, status);
+    count_launch();
+  }
   // Step 3 folded into Step 4: KU = I - tau A = 2B - I - tau C^T B; KW = tau B
   k_small_gemm<T><<<tg, tb, 0, st>>>(p, ld, -tau, C, 1, B, 0, 2.0, B, 0.0, 0.0,
-                                     (const double *)nullptr, -1.0, KU, KU_t, status); count_launch();
-  k_scale<T><<<(ld * ld + 255) / 256, 256, 0, st>>>(ld, tau, B, KW, KW_t); count_launch();
+                                     (const double *)nullptr, -1.0, KU, KU_t, status);
+  count_launch();
+  k_scale<T><<<(ld * ld + 255) / 256, 256, 0, st>>>(ld, tau, B, KW, KW_t, status);
+  count_launch();
   OP_LAUNCH("core");
   return OP_OK;
 }

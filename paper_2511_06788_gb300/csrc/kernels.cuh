@@ -63,15 +63,18 @@ op_status launch_colsum(const double *part, int nblk, int ncomp, int ld, double 
 
 // CG workspace layout and the solver loop.
 struct CGWork {
-  void *R, *P, *Q;       // n x ld blocks of T
-  double *part;          // [max_blocks][2][ld]
+  void *R, *P, *Q;       // n x ld blocks of T (FP32 path: P, Q are the two direction buffers)
+  double *part;          // CTA partials [max_blocks][2][ld] + per-column sums [2][ld]
   double *state;         // [6][ld]: rr, target, alpha, beta, bnorm2, scratch
   int *active;           // [ld]
-  int *nactive;          // [1] device
-  int *nactive_host;     // pinned host mirror
+  int *ctl;              // [4] device: active counts (two parities), iterations done
+  int *host_ctl;         // >= 3 ints of host memory (pinned for the context)
   int max_blocks;
-  Prof *prof = nullptr;   // optional timing
+  int expect_iters = 0;  // iterations of the previous solve (first chunk length)
+  Prof *prof = nullptr;  // optional timing
 };
+// bytes of the CTA-partials scratch used by the reductions of a row width ld
+size_t part_bytes(int ld);
 size_t cg_workspace_bytes(long long n, int ld, int elem);
 void cg_carve(void *ws, long long n, int ld, int elem, CGWork *w);
 
@@ -92,6 +95,12 @@ size_t gram_workspace_bytes(long long n, int ld, int elem);
 template <typename T>
 op_status gram(long long n, int p, int ld, const T *U, const T *W, double *C, double *S,
                double *D, void *ws, size_t ws_bytes, cudaStream_t st);
+
+// FP32 blocks on the tensor cores (gram_tc.cu): same outputs as gram<float>; *err is set
+// (device int) when a bounded wait inside the kernel gave up.
+size_t gram_tc_workspace_bytes(long long n, int ld);
+op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, double *C, double *S,
+                  double *D, void *ws, size_t ws_bytes, int *err, cudaStream_t st);
 
 // ---- dense FP64 p x p algebra (dense.cu) --------------------------------------
 size_t core_workspace_bytes(int p, int ld);
@@ -120,9 +129,18 @@ op_status launch_resid_coeff(int p, int ld, const double *Th, T *negTh, T *Id, c
 // lam (ascending) = 1/mu - sigma for mu ascending.
 op_status launch_paper_lams(int p, const double *mu, double sigma, double *lam, cudaStream_t st);
 
-// ---- Step 4 (update.cu) -------------------------------------------------------
+// ---- Step 4 (update.cu, update_tc.cu) -------------------------------------------------
 template <typename T>
 op_status update(long long n, int ld, const T *U, const T *W, const T *KU, const T *KW, T *Unew,
                  cudaStream_t st);
+// KT = [KU - I; KW]^T split into TF32 hi / lo parts (ld x 2 ld each) from FP64 or FP32
+// KU, KW (update_tc adds U back, so it computes U KU + W KW).
+op_status launch_make_kt(int ld, const double *KU, const double *KW, float *KT_hi, float *KT_lo,
+                         cudaStream_t st);
+op_status launch_make_kt_f32(int ld, const float *KU, const float *KW, float *KT_hi,
+                             float *KT_lo, cudaStream_t st);
+// Unew = [U W] [KU; KW] on the tensor cores (FP32 blocks); *err as for gram_tc.
+op_status update_tc(long long n, int ld, const float *U, const float *W, const float *KT_hi,
+                    const float *KT_lo, float *Unew, int *err, cudaStream_t st);
 
 }  // namespace opevo

@@ -4,9 +4,19 @@
 // Layout: n x ld row-major blocks; one thread owns one 16-byte vector of one
 // grid point's row (float4 / double2), so a warp reads whole rows with
 // coalesced 16-byte loads; the six neighbours of a point are rows i +- 1,
-// i +- nx, i +- nx*ny and are served by L1/L2 (the z-planes of a block of
-// consecutive points stay resident in the 129 MB L2).
-#include <stdio.h>
+// i +- nx, i +- nx*ny and are served by L1/L2 (the planes around the points a
+// wave of CTAs works on stay resident in the 129 MB L2).
+//
+// Per-column dot products are accumulated per thread in the block type T and
+// combined across threads and CTAs in FP64 (per-element FP64 work would make
+// the FP32 kernels FP64-pipe bound on GB300).  Partial sums per CTA are
+// reduced by one warp per column in a fixed order (deterministic).
+//
+// CG control lives on the device: the finalisers compute alpha, beta and the
+// number of still-active columns; every kernel of an iteration returns at once
+// when the previous iteration left no active column, so the host can queue
+// several iterations between convergence checks.
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -16,48 +26,78 @@ namespace opevo {
 namespace {
 
 template <typename T>
-__device__ __forceinline__ void axpy_pack(Pack<T> &acc, const Pack<T> &x) {
+__device__ __forceinline__ void add_pack(Pack<T> &acc, const Pack<T> &x) {
 #pragma unroll
   for (int k = 0; k < Pack<T>::N; ++k) acc.v[k] += x.v[k];
 }
 
-// (H + sigma) x at point i, columns col .. col+N-1.
-// Vt: V in T; shift = cdiag + sigma in T, so the diagonal is Vt_i + shift.
-template <typename T>
-__device__ __forceinline__ Pack<T> stencil_at(const Geom &g, const T *__restrict__ Vt, T shift,
-                                              const T *__restrict__ X, int ld, long long i,
-                                              int col, Pack<T> *center) {
-  const long long base = i * (long long)ld + col;
-  Pack<T> xc = Pack<T>::load(X + base);
-  const int ix = (int)(i % g.nx);
+// Grid coordinates of point i.
+struct Coord {
+  int ix, iy, iz;
+};
+__device__ __forceinline__ Coord coord_of(const Geom &g, long long i) {
+  Coord c;
   const long long r = i / g.nx;
-  const int iy = (int)(r % g.ny);
-  const int iz = (int)(r / g.ny);
-  Pack<T> sx = Pack<T>::zero(), sy = Pack<T>::zero(), sz = Pack<T>::zero();
-  if (ix > 0) axpy_pack(sx, Pack<T>::load(X + base - ld));
-  if (ix < g.nx - 1) axpy_pack(sx, Pack<T>::load(X + base + ld));
-  const long long sty = (long long)g.nx * ld;
-  if (iy > 0) axpy_pack(sy, Pack<T>::load(X + base - sty));
-  if (iy < g.ny - 1) axpy_pack(sy, Pack<T>::load(X + base + sty));
-  if (g.dim == 3) {
-    const long long stz = (long long)g.nx * g.ny * ld;
-    if (iz > 0) axpy_pack(sz, Pack<T>::load(X + base - stz));
-    if (iz < g.nz - 1) axpy_pack(sz, Pack<T>::load(X + base + stz));
-  }
-  const T d = __ldg(Vt + i) + shift;
+  c.ix = (int)(i - r * g.nx);
+  c.iy = (int)(r % g.ny);
+  c.iz = (int)(r / g.ny);
+  return c;
+}
+
+// y = d x_c - cx sx - cy sy - cz sz for the neighbour sums s*.
+template <typename T>
+__device__ __forceinline__ Pack<T> combine(const Geom &g, T d, const Pack<T> &xc, const Pack<T> &sx,
+                                           const Pack<T> &sy, const Pack<T> &sz) {
   const T cx = (T)g.c[0], cy = (T)g.c[1], cz = (T)g.c[2];
   Pack<T> y;
 #pragma unroll
   for (int k = 0; k < Pack<T>::N; ++k)
     y.v[k] = d * xc.v[k] - cx * sx.v[k] - cy * sy.v[k] - cz * sz.v[k];
-  if (center) *center = xc;
   return y;
 }
 
-// Column-wise block reduction of acc[ncomp][N] (per thread) into
-// part[blockIdx.x][ncomp][ld]; the block covers vectors blockIdx.y*blockDim.x + tx.
+// (H + sigma) x at point i, columns col .. col+N-1.  Vt: V in T; shift =
+// cdiag + sigma in T, so the diagonal is Vt_i + shift.
+template <typename T>
+__device__ __forceinline__ Pack<T> stencil_at(const Geom &g, const T *__restrict__ Vt, T shift,
+                                              const T *__restrict__ X, int ld, long long i,
+                                              int col, Pack<T> *center) {
+  const long long base = i * (long long)ld + col;
+  const Coord c = coord_of(g, i);
+  Pack<T> xc = Pack<T>::load(X + base);
+  Pack<T> sx = Pack<T>::zero(), sy = Pack<T>::zero(), sz = Pack<T>::zero();
+  if (c.ix > 0) add_pack(sx, Pack<T>::load(X + base - ld));
+  if (c.ix < g.nx - 1) add_pack(sx, Pack<T>::load(X + base + ld));
+  const long long sty = (long long)g.nx * ld;
+  if (c.iy > 0) add_pack(sy, Pack<T>::load(X + base - sty));
+  if (c.iy < g.ny - 1) add_pack(sy, Pack<T>::load(X + base + sty));
+  if (g.dim == 3) {
+    const long long stz = (long long)g.nx * g.ny * ld;
+    if (c.iz > 0) add_pack(sz, Pack<T>::load(X + base - stz));
+    if (c.iz < g.nz - 1) add_pack(sz, Pack<T>::load(X + base + stz));
+  }
+  if (center) *center = xc;
+  return combine(g, __ldg(Vt + i) + shift, xc, sx, sy, sz);
+}
+
+// Value of r + b p at a row offset (p omitted on the first CG iteration).
+template <typename T, bool FIRST>
+__device__ __forceinline__ Pack<T> dir_at(const T *__restrict__ R, const T *__restrict__ Po,
+                                          const T (&b)[Pack<T>::N], long long off) {
+  Pack<T> r = Pack<T>::load(R + off);
+  if (!FIRST) {
+    const Pack<T> q = Pack<T>::load(Po + off);
+#pragma unroll
+    for (int k = 0; k < Pack<T>::N; ++k) r.v[k] += b[k] * q.v[k];
+  }
+  return r;
+}
+
+// Column-wise block reduction of the per-thread partials acc[ncomp][N] (type T)
+// into part[blockIdx.x][ncomp][ld] (FP64); the block covers the vectors
+// blockIdx.y * blockDim.x + threadIdx.x of a row.
 template <typename T, int NCOMP>
-__device__ __forceinline__ void block_colsum(double (&acc)[NCOMP][Pack<T>::N], int ld,
+__device__ __forceinline__ void block_colsum(const T (&acc)[NCOMP][Pack<T>::N], int ld,
                                              double *__restrict__ part) {
   constexpr int N = Pack<T>::N;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -69,7 +109,7 @@ __device__ __forceinline__ void block_colsum(double (&acc)[NCOMP][Pack<T>::N], i
     for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
       for (int k = 0; k < N; ++k)
-        if (col0 + tx * N + k < ld) dst[c * ld + col0 + tx * N + k] = acc[c][k];
+        if (col0 + tx * N + k < ld) dst[c * ld + col0 + tx * N + k] = (double)acc[c][k];
     return;
   }
   // blockDim.x * blockDim.y <= 256 here, so the tile fits.
@@ -78,7 +118,7 @@ __device__ __forceinline__ void block_colsum(double (&acc)[NCOMP][Pack<T>::N], i
 #pragma unroll
   for (int c = 0; c < NCOMP; ++c)
 #pragma unroll
-    for (int k = 0; k < N; ++k) red[ty * width + c * bx * N + tx * N + k] = acc[c][k];
+    for (int k = 0; k < N; ++k) red[ty * width + c * bx * N + tx * N + k] = (double)acc[c][k];
   __syncthreads();
   const int t = ty * bx + tx;
   const int nthreads = bx * blockDim.y;
@@ -90,13 +130,21 @@ __device__ __forceinline__ void block_colsum(double (&acc)[NCOMP][Pack<T>::N], i
   }
 }
 
+#define ROW_PROLOGUE(NV)                                                            \
+  constexpr int N = Pack<T>::N;                                                     \
+  const int col = (blockIdx.y * blockDim.x + threadIdx.x) * N;                      \
+  const long long i0 = (col < ld) ? blockIdx.x * (long long)blockDim.y + threadIdx.y : (NV); \
+  const long long istep = (long long)gridDim.x * blockDim.y;
+
+// ---------------------------------------------------------------------------
+// Stencil kernels
+// ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply(Geom g, const T *__restrict__ Vt, T shift,
                                                const T *__restrict__ X, T *__restrict__ Y, int ld) {
-  const int col = (blockIdx.y * blockDim.x + threadIdx.x) * Pack<T>::N;
-  if (col >= ld) return;
-  for (long long i = blockIdx.x * (long long)blockDim.y + threadIdx.y; i < g.n;
-       i += (long long)gridDim.x * blockDim.y) {
+  ROW_PROLOGUE(g.n)
+  (void)N;
+  for (long long i = i0; i < g.n; i += istep) {
     Pack<T> y = stencil_at(g, Vt, shift, X, ld, i, col, (Pack<T> *)nullptr);
     y.store(Y + i * (long long)ld + col);
   }
@@ -107,35 +155,55 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_quad(Geom g, const T *__restrict__ Vt, T shift,
                                               const T *__restrict__ X, int ld,
                                               double *__restrict__ part) {
-  constexpr int N = Pack<T>::N;
-  const int col = (blockIdx.y * blockDim.x + threadIdx.x) * N;
-  const long long i0 = (col < ld) ? blockIdx.x * (long long)blockDim.y + threadIdx.y : g.n;
-  double acc[2][N] = {};
-  for (long long i = i0; i < g.n;
-       i += (long long)gridDim.x * blockDim.y) {
+  ROW_PROLOGUE(g.n)
+  T acc[2][N] = {};
+  for (long long i = i0; i < g.n; i += istep) {
     Pack<T> xc;
     Pack<T> y = stencil_at(g, Vt, shift, X, ld, i, col, &xc);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      acc[0][k] += (double)xc.v[k] * (double)y.v[k];
-      acc[1][k] += (double)xc.v[k] * (double)xc.v[k];
+      acc[0][k] += xc.v[k] * y.v[k];
+      acc[1][k] += xc.v[k] * xc.v[k];
     }
   }
   block_colsum<T, 2>(acc, ld, part);
 }
 
-// R = U - (H+sigma) W; P = R; part[b][0] = ||R_j||^2, part[b][1] = ||U_j||^2.
+// part[b][0][j] = sum_i X_ij^2.
 template <typename T>
+__global__ void __launch_bounds__(256) k_sumsq(long long n, int ld, const T *__restrict__ X,
+                                               double *__restrict__ part) {
+  ROW_PROLOGUE(n)
+  T acc[1][N] = {};
+  for (long long i = i0; i < n; i += istep) {
+    Pack<T> x = Pack<T>::load(X + i * (long long)ld + col);
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc[0][k] += x.v[k] * x.v[k];
+  }
+  block_colsum<T, 1>(acc, ld, part);
+}
+
+// ---------------------------------------------------------------------------
+// CG kernels.  ctl[0], ctl[1]: active-column counts written by alternate
+// iterations; ctl[2]: iterations done.  Iteration k reads nact_prev =
+// ctl[(k+1)&1] (the count left by iteration k-1, or by the start-up for k = 0)
+// and its beta finaliser accumulates into ctl[k&1].
+// ---------------------------------------------------------------------------
+
+// R = U - (H+sigma) W (and P = R when WRITE_P); part[b][0] = ||R_j||^2,
+// part[b][1] = ||U_j||^2.  Resets the control words.
+template <typename T, bool WRITE_P>
 __global__ void __launch_bounds__(256) k_cg_init(Geom g, const T *__restrict__ Vt, T shift,
                                                  const T *__restrict__ U, const T *__restrict__ W,
                                                  T *__restrict__ R, T *__restrict__ P, int ld,
-                                                 double *__restrict__ part) {
-  constexpr int N = Pack<T>::N;
-  const int col = (blockIdx.y * blockDim.x + threadIdx.x) * N;
-  const long long i0 = (col < ld) ? blockIdx.x * (long long)blockDim.y + threadIdx.y : g.n;
-  double acc[2][N] = {};
-  for (long long i = i0; i < g.n;
-       i += (long long)gridDim.x * blockDim.y) {
+                                                 double *__restrict__ part, int *ctl) {
+  ROW_PROLOGUE(g.n)
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    ctl[1] = 0;
+    ctl[2] = 0;
+  }
+  T acc[2][N] = {};
+  for (long long i = i0; i < g.n; i += istep) {
     Pack<T> aw = stencil_at(g, Vt, shift, W, ld, i, col, (Pack<T> *)nullptr);
     const long long o = i * (long long)ld + col;
     Pack<T> u = Pack<T>::load(U + o);
@@ -143,30 +211,30 @@ __global__ void __launch_bounds__(256) k_cg_init(Geom g, const T *__restrict__ V
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       r.v[k] = u.v[k] - aw.v[k];
-      acc[0][k] += (double)r.v[k] * (double)r.v[k];
-      acc[1][k] += (double)u.v[k] * (double)u.v[k];
+      acc[0][k] += r.v[k] * r.v[k];
+      acc[1][k] += u.v[k] * u.v[k];
     }
     r.store(R + o);
-    r.store(P + o);
+    if (WRITE_P) r.store(P + o);
   }
   block_colsum<T, 2>(acc, ld, part);
 }
 
+// ---- three-kernel iteration (FP64: no arithmetic is recomputed) -----------------
 // Q = (H+sigma) P; part[b][0][j] = P_j . Q_j.
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_apply(Geom g, const T *__restrict__ Vt, T shift,
                                                   const T *__restrict__ P, T *__restrict__ Q,
-                                                  int ld, double *__restrict__ part) {
-  constexpr int N = Pack<T>::N;
-  const int col = (blockIdx.y * blockDim.x + threadIdx.x) * N;
-  const long long i0 = (col < ld) ? blockIdx.x * (long long)blockDim.y + threadIdx.y : g.n;
-  double acc[1][N] = {};
-  for (long long i = i0; i < g.n;
-       i += (long long)gridDim.x * blockDim.y) {
+                                                  int ld, const int *nact_prev,
+                                                  double *__restrict__ part) {
+  if (*nact_prev == 0) return;
+  ROW_PROLOGUE(g.n)
+  T acc[1][N] = {};
+  for (long long i = i0; i < g.n; i += istep) {
     Pack<T> pc;
     Pack<T> q = stencil_at(g, Vt, shift, P, ld, i, col, &pc);
 #pragma unroll
-    for (int k = 0; k < N; ++k) acc[0][k] += (double)pc.v[k] * (double)q.v[k];
+    for (int k = 0; k < N; ++k) acc[0][k] += pc.v[k] * q.v[k];
     q.store(Q + i * (long long)ld + col);
   }
   block_colsum<T, 1>(acc, ld, part);
@@ -178,16 +246,14 @@ __global__ void __launch_bounds__(256) k_cg_axpy(long long n, int ld, T *__restr
                                                  T *__restrict__ R, const T *__restrict__ P,
                                                  const T *__restrict__ Q,
                                                  const double *__restrict__ alpha,
-                                                 double *__restrict__ part) {
-  constexpr int N = Pack<T>::N;
-  const int col = (blockIdx.y * blockDim.x + threadIdx.x) * N;
-  const long long i0 = (col < ld) ? blockIdx.x * (long long)blockDim.y + threadIdx.y : n;
+                                                 const int *nact_prev, double *__restrict__ part) {
+  if (*nact_prev == 0) return;
+  ROW_PROLOGUE(n)
   T a[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) a[k] = (col < ld) ? (T)alpha[col + k] : T(0);
-  double acc[1][N] = {};
-  for (long long i = i0; i < n;
-       i += (long long)gridDim.x * blockDim.y) {
+  T acc[1][N] = {};
+  for (long long i = i0; i < n; i += istep) {
     const long long o = i * (long long)ld + col;
     Pack<T> w = Pack<T>::load_rw(W + o), r = Pack<T>::load_rw(R + o);
     Pack<T> p = Pack<T>::load(P + o), q = Pack<T>::load(Q + o);
@@ -195,7 +261,7 @@ __global__ void __launch_bounds__(256) k_cg_axpy(long long n, int ld, T *__restr
     for (int k = 0; k < N; ++k) {
       w.v[k] += a[k] * p.v[k];
       r.v[k] -= a[k] * q.v[k];
-      acc[0][k] += (double)r.v[k] * (double)r.v[k];
+      acc[0][k] += r.v[k] * r.v[k];
     }
     w.store(W + o);
     r.store(R + o);
@@ -206,40 +272,108 @@ __global__ void __launch_bounds__(256) k_cg_axpy(long long n, int ld, T *__restr
 // P = R + beta P.
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_dir(long long n, int ld, const T *__restrict__ R,
-                                                T *__restrict__ P,
-                                                const double *__restrict__ beta) {
-  constexpr int N = Pack<T>::N;
-  const int col = (blockIdx.y * blockDim.x + threadIdx.x) * N;
+                                                T *__restrict__ P, const double *__restrict__ beta,
+                                                const int *nact_prev) {
+  if (*nact_prev == 0) return;
+  ROW_PROLOGUE(n)
   if (col >= ld) return;
   T b[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) b[k] = (T)beta[col + k];
-  for (long long i = blockIdx.x * (long long)blockDim.y + threadIdx.y; i < n;
-       i += (long long)gridDim.x * blockDim.y) {
+  for (long long i = i0; i < n; i += istep) {
     const long long o = i * (long long)ld + col;
     Pack<T> r = Pack<T>::load(R + o), pp = Pack<T>::load_rw(P + o);
 #pragma unroll
-    for (int k = 0; k < Pack<T>::N; ++k) pp.v[k] = r.v[k] + b[k] * pp.v[k];
+    for (int k = 0; k < N; ++k) pp.v[k] = r.v[k] + b[k] * pp.v[k];
     pp.store(P + o);
   }
 }
 
-// ---- single-block finalisers (deterministic reduction over blocks) -------------
-__device__ __forceinline__ double sum_blocks(const double *part, int nblk, int stride, int e) {
+// ---- two-kernel iteration (FP32: the stencil is recomputed instead of storing Q) ----
+// Pn = R + beta Po (Pn = R on the first iteration); part[b][0][j] = Pn_j . (H+sigma) Pn_j.
+// Reads R and Po (with the stencil halo), writes Pn.
+template <typename T, bool FIRST>
+__global__ void __launch_bounds__(256) k_cg_p(Geom g, const T *__restrict__ Vt, T shift,
+                                              const T *__restrict__ R, const T *__restrict__ Po,
+                                              T *__restrict__ Pn, int ld,
+                                              const double *__restrict__ beta,
+                                              const int *nact_prev, double *__restrict__ part) {
+  if (*nact_prev == 0) return;
+  ROW_PROLOGUE(g.n)
+  T b[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) b[k] = (!FIRST && col < ld) ? (T)beta[col + k] : T(0);
+  T acc[1][N] = {};
+  const long long sty = (long long)g.nx * ld, stz = (long long)g.nx * g.ny * ld;
+  for (long long i = i0; i < g.n; i += istep) {
+    const long long base = i * (long long)ld + col;
+    const Coord c = coord_of(g, i);
+    const Pack<T> pc = dir_at<T, FIRST>(R, Po, b, base);
+    Pack<T> sx = Pack<T>::zero(), sy = Pack<T>::zero(), sz = Pack<T>::zero();
+    if (c.ix > 0) add_pack(sx, dir_at<T, FIRST>(R, Po, b, base - ld));
+    if (c.ix < g.nx - 1) add_pack(sx, dir_at<T, FIRST>(R, Po, b, base + ld));
+    if (c.iy > 0) add_pack(sy, dir_at<T, FIRST>(R, Po, b, base - sty));
+    if (c.iy < g.ny - 1) add_pack(sy, dir_at<T, FIRST>(R, Po, b, base + sty));
+    if (g.dim == 3) {
+      if (c.iz > 0) add_pack(sz, dir_at<T, FIRST>(R, Po, b, base - stz));
+      if (c.iz < g.nz - 1) add_pack(sz, dir_at<T, FIRST>(R, Po, b, base + stz));
+    }
+    const Pack<T> q = combine(g, __ldg(Vt + i) + shift, pc, sx, sy, sz);
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc[0][k] += pc.v[k] * q.v[k];
+    pc.store(Pn + base);
+  }
+  block_colsum<T, 1>(acc, ld, part);
+}
+
+// q = (H+sigma) Pn (recomputed); W += alpha Pn; R -= alpha q; part[b][0][j] = ||R_j||^2.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_wr(Geom g, const T *__restrict__ Vt, T shift,
+                                               T *__restrict__ W, T *__restrict__ R,
+                                               const T *__restrict__ Pn, int ld,
+                                               const double *__restrict__ alpha,
+                                               const int *nact_prev, double *__restrict__ part) {
+  if (*nact_prev == 0) return;
+  ROW_PROLOGUE(g.n)
+  T a[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) a[k] = (col < ld) ? (T)alpha[col + k] : T(0);
+  T acc[1][N] = {};
+  for (long long i = i0; i < g.n; i += istep) {
+    Pack<T> pc;
+    const Pack<T> q = stencil_at(g, Vt, shift, Pn, ld, i, col, &pc);
+    const long long o = i * (long long)ld + col;
+    Pack<T> w = Pack<T>::load_rw(W + o), r = Pack<T>::load_rw(R + o);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      w.v[k] += a[k] * pc.v[k];
+      r.v[k] -= a[k] * q.v[k];
+      acc[0][k] += r.v[k] * r.v[k];
+    }
+    w.store(W + o);
+    r.store(R + o);
+  }
+  block_colsum<T, 1>(acc, ld, part);
+}
+
+// ---- finalisers: one warp per column, lanes stride over the CTA partials ----------
+__device__ __forceinline__ double warp_sum_blocks(const double *part, int nblk, int stride, int e) {
+  const int lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(long long)b * stride + e];
+  for (int b = lane; b < nblk; b += 32) s += part[(long long)b * stride + e];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
 
-// state rows: 0 rr, 1 target, 2 alpha, 3 beta, 4 bnorm2
+// state rows: 0 rr, 1 target, 2 alpha, 3 beta, 4 ||b||^2
 __global__ void k_cg_fin_init(const double *part, int nblk, int ld, int p, double rtol2,
-                              double *state, int *active, int *nactive) {
-  __shared__ int cnt;
-  if (threadIdx.x == 0) cnt = 0;
-  __syncthreads();
-  for (int j = threadIdx.x; j < ld; j += blockDim.x) {
-    const double rr = sum_blocks(part, nblk, 2 * ld, j);
-    const double bb = sum_blocks(part, nblk, 2 * ld, ld + j);
+                              double *state, int *active, int *ctl) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= ld) return;
+  const double rr = warp_sum_blocks(part, nblk, 2 * ld, j);
+  const double bb = warp_sum_blocks(part, nblk, 2 * ld, ld + j);
+  if ((threadIdx.x & 31) == 0) {
     state[0 * ld + j] = rr;
     state[1 * ld + j] = rtol2 * bb;
     state[2 * ld + j] = 0.0;
@@ -247,28 +381,31 @@ __global__ void k_cg_fin_init(const double *part, int nblk, int ld, int p, doubl
     state[4 * ld + j] = bb;
     const int a = (j < p) && (rr > rtol2 * bb) && (bb > 0.0);
     active[j] = a;
-    if (a) atomicAdd(&cnt, 1);
+    if (a) atomicAdd(&ctl[1], 1);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) *nactive = cnt;
 }
 
 __global__ void k_cg_fin_alpha(const double *part, int nblk, int ld, double *state,
-                               const int *active) {
-  for (int j = threadIdx.x; j < ld; j += blockDim.x) {
-    const double pq = sum_blocks(part, nblk, ld, j);
+                               const int *active, const int *nact_prev, int *nact_next) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *nact_next = 0;
+  if (*nact_prev == 0) return;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= ld) return;
+  const double pq = warp_sum_blocks(part, nblk, ld, j);
+  if ((threadIdx.x & 31) == 0) {
     const double rr = state[j];
     state[2 * ld + j] = (active[j] && pq > 0.0) ? rr / pq : 0.0;
   }
 }
 
 __global__ void k_cg_fin_beta(const double *part, int nblk, int ld, double *state, int *active,
-                              int *nactive) {
-  __shared__ int cnt;
-  if (threadIdx.x == 0) cnt = 0;
-  __syncthreads();
-  for (int j = threadIdx.x; j < ld; j += blockDim.x) {
-    const double rrn = sum_blocks(part, nblk, ld, j);
+                              const int *nact_prev, int *nact_next, int *iters) {
+  if (*nact_prev == 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *iters += 1;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= ld) return;
+  const double rrn = warp_sum_blocks(part, nblk, ld, j);
+  if ((threadIdx.x & 31) == 0) {
     const double rr = state[j];
     int a = active[j];
     state[3 * ld + j] = (a && rr > 0.0) ? rrn / rr : 0.0;
@@ -277,41 +414,26 @@ __global__ void k_cg_fin_beta(const double *part, int nblk, int ld, double *stat
       a = rrn > state[ld + j];
       active[j] = a;
     }
-    if (a) atomicAdd(&cnt, 1);
+    if (a) atomicAdd(nact_next, 1);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) *nactive = cnt;
 }
 
-__global__ void k_colsum(const double *part, int nblk, int width, double *out) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < width; e += gridDim.x * blockDim.x)
-    out[e] = sum_blocks(part, nblk, width, e);
+// colsum[e] = sum_b part[b][e] for e < ncomp*ld: one warp per entry, fixed order.
+__global__ void k_fin_cols(const double *__restrict__ part, int nblk, int ncomp, int ld,
+                           double *__restrict__ colsum) {
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (e >= ncomp * ld) return;
+  const double s = warp_sum_blocks(part, nblk, ncomp * ld, e);
+  if ((threadIdx.x & 31) == 0) colsum[e] = s;
 }
 
-// part[b][0][j] = sum_i X_ij^2.
-template <typename T>
-__global__ void __launch_bounds__(256) k_sumsq(long long n, int ld, const T *__restrict__ X,
-                                               double *__restrict__ part) {
-  constexpr int N = Pack<T>::N;
-  const int col = (blockIdx.y * blockDim.x + threadIdx.x) * N;
-  const long long i0 = (col < ld) ? blockIdx.x * (long long)blockDim.y + threadIdx.y : n;
-  double acc[1][N] = {};
-  for (long long i = i0; i < n; i += (long long)gridDim.x * blockDim.y) {
-    Pack<T> x = Pack<T>::load(X + i * (long long)ld + col);
-#pragma unroll
-    for (int k = 0; k < N; ++k) acc[0][k] += (double)x.v[k] * (double)x.v[k];
-  }
-  block_colsum<T, 1>(acc, ld, part);
-}
-
-// out[c] = sum_j sum_b part[b][c][j], c < ncomp (one CTA, fixed order).
-__global__ void k_fin_total(const double *__restrict__ part, int nblk, int ncomp, int ld,
+// out[c] = sum_j colsum[c][j], c < ncomp (one CTA, fixed order).
+__global__ void k_fin_total(const double *__restrict__ colsum, int ncomp, int ld,
                             double *__restrict__ out) {
   __shared__ double sh[256];
   for (int c = 0; c < ncomp; ++c) {
     double s = 0.0;
-    for (int j = threadIdx.x; j < ld; j += blockDim.x)
-      for (int b = 0; b < nblk; ++b) s += part[((long long)b * ncomp + c) * ld + j];
+    for (int j = threadIdx.x; j < ld; j += blockDim.x) s += colsum[c * ld + j];
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -347,15 +469,25 @@ __global__ void k_unpad_copy(long long n, int p, int ld, const T *__restrict__ s
   }
 }
 
+// CTAs of a row kernel: four 256-thread CTAs per SM, fewer for small n.
 int grid_blocks(long long n, int rows) {
   long long want = (n + rows - 1) / rows;
-  long long cap = (long long)kNumSMs * 8;
+  long long cap = (long long)kNumSMs * 4;
   if (want > cap) want = cap;
   if (want < 1) want = 1;
   return (int)want;
 }
 
+int warp_blocks(int warps) { return (warps * 32 + 255) / 256; }
+
+// The CTA partials buffer holds up to kNumSMs*8 x 2 x ld doubles; per-column sums follow.
+double *colsum_area(double *part, int ld) { return part + (size_t)kNumSMs * 8 * 2 * ld; }
+
 }  // namespace
+
+size_t part_bytes(int ld) {
+  return ((size_t)kNumSMs * 8 * 2 * ld + 2 * (size_t)ld) * sizeof(double);
+}
 
 // ---------------------------------------------------------------------------
 // Launchers
@@ -365,7 +497,8 @@ op_status launch_apply(const Geom &g, const T *Vt, double sigma, const T *X, T *
                        cudaStream_t st) {
   RowShape s = row_shape(ld, Pack<T>::N);
   k_apply<T><<<dim3(grid_blocks(g.n, s.rows), s.gy), s.block, 0, st>>>(
-      g, Vt, (T)(g.cdiag + sigma), X, Y, ld); count_launch();
+      g, Vt, (T)(g.cdiag + sigma), X, Y, ld);
+  count_launch();
   OP_LAUNCH("k_apply");
   return OP_OK;
 }
@@ -375,8 +508,12 @@ op_status launch_quad(const Geom &g, const T *Vt, double sigma, const T *X, int 
                       double *out, cudaStream_t st) {
   RowShape s = row_shape(ld, Pack<T>::N);
   const int nb = grid_blocks(g.n, s.rows);
-  k_quad<T><<<dim3(nb, s.gy), s.block, 0, st>>>(g, Vt, (T)(g.cdiag + sigma), X, ld, part); count_launch();
-  k_fin_total<<<1, 256, 0, st>>>(part, nb, 2, ld, out); count_launch();
+  k_quad<T><<<dim3(nb, s.gy), s.block, 0, st>>>(g, Vt, (T)(g.cdiag + sigma), X, ld, part);
+  count_launch();
+  k_fin_cols<<<warp_blocks(2 * ld), 256, 0, st>>>(part, nb, 2, ld, colsum_area(part, ld));
+  count_launch();
+  k_fin_total<<<1, 256, 0, st>>>(colsum_area(part, ld), 2, ld, out);
+  count_launch();
   OP_LAUNCH("k_quad");
   return OP_OK;
 }
@@ -386,26 +523,21 @@ op_status launch_sumsq(long long n, int ld, const T *X, double *part, double *ou
                        cudaStream_t st) {
   RowShape s = row_shape(ld, Pack<T>::N);
   const int nb = grid_blocks(n, s.rows);
-  k_sumsq<T><<<dim3(nb, s.gy), s.block, 0, st>>>(n, ld, X, part); count_launch();
-  k_fin_total<<<1, 256, 0, st>>>(part, nb, 1, ld, out); count_launch();
+  k_sumsq<T><<<dim3(nb, s.gy), s.block, 0, st>>>(n, ld, X, part);
+  count_launch();
+  k_fin_cols<<<warp_blocks(ld), 256, 0, st>>>(part, nb, 1, ld, colsum_area(part, ld));
+  count_launch();
+  k_fin_total<<<1, 256, 0, st>>>(colsum_area(part, ld), 1, ld, out);
+  count_launch();
   OP_LAUNCH("k_sumsq");
-  return OP_OK;
-}
-
-op_status launch_colsum(const double *part, int nblk, int ncomp, int ld, double *out,
-                        cudaStream_t st) {
-  const int width = ncomp * ld;
-  k_colsum<<<(width + 255) / 256, 256, 0, st>>>(part, nblk, width, out); count_launch();
-  OP_LAUNCH("k_colsum");
   return OP_OK;
 }
 
 size_t cg_workspace_bytes(long long n, int ld, int elem) {
   size_t blk = (size_t)n * ld * elem;
   blk = (blk + 255) / 256 * 256;
-  size_t part = (size_t)kNumSMs * 8 * 2 * ld * sizeof(double);
-  size_t state = (size_t)6 * ld * sizeof(double) + (size_t)ld * sizeof(int) + 256;
-  return 3 * blk + part + state + 1024;
+  size_t state = (size_t)6 * ld * sizeof(double) + ((size_t)ld * sizeof(int) + 255) / 256 * 256;
+  return 3 * blk + (part_bytes(ld) + 255) / 256 * 256 + state + 1024;
 }
 
 void cg_carve(void *ws, long long n, int ld, int elem, CGWork *w) {
@@ -420,63 +552,113 @@ void cg_carve(void *ws, long long n, int ld, int elem, CGWork *w) {
   p += blk;
   w->max_blocks = kNumSMs * 8;
   w->part = (double *)p;
-  p += (size_t)w->max_blocks * 2 * ld * sizeof(double);
+  p += (part_bytes(ld) + 255) / 256 * 256;
   w->state = (double *)p;
   p += (size_t)6 * ld * sizeof(double);
   w->active = (int *)p;
   p += ((size_t)ld * sizeof(int) + 255) / 256 * 256;
-  w->nactive = (int *)p;
+  w->ctl = (int *)p;
 }
 
 template <typename T>
 op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, int p, int ld,
                    double rtol, int max_iter, CGWork &w, int *iters, cudaStream_t st) {
+  constexpr bool kFused = std::is_same<T, float>::value;
   RowShape s = row_shape(ld, Pack<T>::N);
   const int nb = grid_blocks(g.n, s.rows);
-  const int fin_threads = ld < 1024 ? ld : 1024;
+  const dim3 grid(nb, s.gy);
+  const int fb = warp_blocks(ld);
   T *R = (T *)w.R, *P = (T *)w.P, *Q = (T *)w.Q;
   double *alpha = w.state + 2 * ld, *beta = w.state + 3 * ld;
+  int *ctl = w.ctl;
   const T sg = (T)(g.cdiag + sigma);
 
   prof_begin(w.prof, PK_CG_INIT, st);
-  k_cg_init<T><<<dim3(nb, s.gy), s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part); count_launch();
-  k_cg_fin_init<<<1, fin_threads, 0, st>>>(w.part, nb, ld, p, rtol * rtol, w.state, w.active,
-                                           w.nactive); count_launch();
+  if (kFused)
+    k_cg_init<T, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+  else
+    k_cg_init<T, true><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+  count_launch();
+  k_cg_fin_init<<<fb, 256, 0, st>>>(w.part, nb, ld, p, rtol * rtol, w.state, w.active, ctl);
+  count_launch();
   prof_end(w.prof, st);
   OP_LAUNCH("k_cg_init");
-  OP_CUDA(cudaMemcpyAsync(w.nactive_host, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
-  OP_CUDA(cudaStreamSynchronize(st));
-  prof_harvest(w.prof);
-  int it = 0;
-  while (*w.nactive_host > 0 && it < max_iter) {
-    prof_begin(w.prof, PK_CG_APPLY, st);
-    k_cg_apply<T><<<dim3(nb, s.gy), s.block, 0, st>>>(g, Vt, sg, P, Q, ld, w.part); count_launch();
-    prof_end(w.prof, st);
-    prof_begin(w.prof, PK_CG_FIN, st);
-    k_cg_fin_alpha<<<1, fin_threads, 0, st>>>(w.part, nb, ld, w.state, w.active); count_launch();
-    prof_end(w.prof, st);
-    prof_begin(w.prof, PK_CG_AXPY, st);
-    k_cg_axpy<T><<<dim3(nb, s.gy), s.block, 0, st>>>(g.n, ld, W, R, P, Q, alpha, w.part); count_launch();
-    prof_end(w.prof, st);
-    prof_begin(w.prof, PK_CG_FIN, st);
-    k_cg_fin_beta<<<1, fin_threads, 0, st>>>(w.part, nb, ld, w.state, w.active, w.nactive); count_launch();
-    prof_end(w.prof, st);
-    prof_begin(w.prof, PK_CG_DIR, st);
-    k_cg_dir<T><<<dim3(nb, s.gy), s.block, 0, st>>>(g.n, ld, R, P, beta); count_launch();
-    prof_end(w.prof, st);
+
+  // Queue iterations in chunks (the first one as long as the previous solve), then
+  // read the active count back; kernels queued past convergence return at once.
+  int launched = 0, done = 0;
+  int chunk = w.expect_iters > 1 ? w.expect_iters : 2;
+  while (launched < max_iter) {
+    const int upto = (launched + chunk < max_iter) ? launched + chunk : max_iter;
+    for (int k = launched; k < upto; ++k) {
+      const int *nprev = ctl + ((k + 1) & 1);
+      int *nnext = ctl + (k & 1);
+      if (kFused) {
+        T *Po = (k & 1) ? Q : P, *Pn = (k & 1) ? P : Q;
+        prof_begin(w.prof, PK_CG_APPLY, st);
+        if (k == 0)
+          k_cg_p<T, true><<<grid, s.block, 0, st>>>(g, Vt, sg, R, Po, Pn, ld, beta, nprev, w.part);
+        else
+          k_cg_p<T, false><<<grid, s.block, 0, st>>>(g, Vt, sg, R, Po, Pn, ld, beta, nprev, w.part);
+        count_launch();
+        prof_end(w.prof, st);
+        prof_begin(w.prof, PK_CG_FIN, st);
+        k_cg_fin_alpha<<<fb, 256, 0, st>>>(w.part, nb, ld, w.state, w.active, nprev, nnext);
+        count_launch();
+        prof_end(w.prof, st);
+        prof_begin(w.prof, PK_CG_AXPY, st);
+        k_cg_wr<T><<<grid, s.block, 0, st>>>(g, Vt, sg, W, R, Pn, ld, alpha, nprev, w.part);
+        count_launch();
+        prof_end(w.prof, st);
+        prof_begin(w.prof, PK_CG_FIN, st);
+        k_cg_fin_beta<<<fb, 256, 0, st>>>(w.part, nb, ld, w.state, w.active, nprev, nnext,
+                                           ctl + 2);
+        count_launch();
+        prof_end(w.prof, st);
+      } else {
+        prof_begin(w.prof, PK_CG_APPLY, st);
+        k_cg_apply<T><<<grid, s.block, 0, st>>>(g, Vt, sg, P, Q, ld, nprev, w.part);
+        count_launch();
+        prof_end(w.prof, st);
+        prof_begin(w.prof, PK_CG_FIN, st);
+        k_cg_fin_alpha<<<fb, 256, 0, st>>>(w.part, nb, ld, w.state, w.active, nprev, nnext);
+        count_launch();
+        prof_end(w.prof, st);
+        prof_begin(w.prof, PK_CG_AXPY, st);
+        k_cg_axpy<T><<<grid, s.block, 0, st>>>(g.n, ld, W, R, P, Q, alpha, nprev, w.part);
+        count_launch();
+        prof_end(w.prof, st);
+        prof_begin(w.prof, PK_CG_FIN, st);
+        k_cg_fin_beta<<<fb, 256, 0, st>>>(w.part, nb, ld, w.state, w.active, nprev, nnext,
+                                           ctl + 2);
+        count_launch();
+        prof_end(w.prof, st);
+        prof_begin(w.prof, PK_CG_DIR, st);
+        k_cg_dir<T><<<grid, s.block, 0, st>>>(g.n, ld, R, P, beta, nprev);
+        count_launch();
+        prof_end(w.prof, st);
+      }
+    }
     OP_LAUNCH("cg iteration");
-    ++it;
-    OP_CUDA(cudaMemcpyAsync(w.nactive_host, w.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+    launched = upto;
+    OP_CUDA(cudaMemcpyAsync(w.host_ctl, ctl, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     OP_CUDA(cudaStreamSynchronize(st));
     prof_harvest(w.prof);
+    done = w.host_ctl[2];
+    // converged: no active column after the last queued iteration (or the solve
+    // stopped inside the chunk)
+    if (w.host_ctl[(upto - 1) & 1] == 0 || done < launched) break;
+    chunk = 2;
   }
-  *iters = it;
+  *iters = done;
+  w.expect_iters = done;
   return OP_OK;
 }
 
 template <typename T>
 op_status launch_pad_copy(long long n, int p, int ld, const double *src, T *dst, cudaStream_t st) {
-  k_pad_copy<T><<<kNumSMs * 8, 256, 0, st>>>(n, p, ld, src, dst); count_launch();
+  k_pad_copy<T><<<kNumSMs * 8, 256, 0, st>>>(n, p, ld, src, dst);
+  count_launch();
   OP_LAUNCH("k_pad_copy");
   return OP_OK;
 }
@@ -484,7 +666,8 @@ op_status launch_pad_copy(long long n, int p, int ld, const double *src, T *dst,
 template <typename T>
 op_status launch_unpad_copy(long long n, int p, int ld, const T *src, double *dst,
                             cudaStream_t st) {
-  k_unpad_copy<T><<<kNumSMs * 8, 256, 0, st>>>(n, p, ld, src, dst); count_launch();
+  k_unpad_copy<T><<<kNumSMs * 8, 256, 0, st>>>(n, p, ld, src, dst);
+  count_launch();
   OP_LAUNCH("k_unpad_copy");
   return OP_OK;
 }

@@ -98,7 +98,8 @@ def test_kernel_level_argument_checks(lib):
     L = b.lib()
     # ld not a multiple of 8
     assert L.op_update(b.OP_FP64, 10, 3, 6, C.c_void_p(16), C.c_void_p(32), C.c_void_p(48),
-                       C.c_void_p(64), C.c_void_p(80), C.c_void_p(0)) == b.OP_ERR_ARG
+                       C.c_void_p(64), C.c_void_p(80), C.c_void_p(96), 1 << 20,
+                       C.c_void_p(0)) == b.OP_ERR_ARG
     # misaligned pointer
     assert L.op_gram(b.OP_FP32, 10, 3, 8, C.c_void_p(17), C.c_void_p(32), None, None, None,
                      None, 0, C.c_void_p(0)) == b.OP_ERR_ARG
