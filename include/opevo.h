@@ -205,6 +205,25 @@ op_status op_gram(int prec, long long n, int p, int ld, const void *U, const voi
                   double *C, double *S, double *D, void *ws, size_t ws_bytes, void *stream);
 size_t op_gram_workspace(int prec, long long n, int ld);
 
+/* op_gram without any device allocation (no counterpart in the paper: a service for
+ * callers that cannot allocate device memory or hand over a workspace, e.g. because
+ * another allocator with a hard budget owns all device memory, or because the calling
+ * loop may not enter the driver's allocator).  Same arguments and results as op_gram
+ * minus the workspace: the reduction partials live in one library-owned device array
+ * of 16 MiB (held on every GPU that loads the library until the process exits).
+ * - Limit: the partials of one chunk per output tile must fit, i.e. with all three
+ *   products ld <= 896 (OP_FP32, 128 x 128 tiles) or ld <= 960 (OP_FP64, 64 x 64
+ *   tiles); larger sizes return OP_ERR_ARG with a message.  Smaller scratch means
+ *   fewer, longer grid-point chunks than op_gram uses.
+ * - The first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ * - Every call uses the same array: calls that overlap on the GPU (other streams,
+ *   other host threads) race and corrupt each other's results.
+ * - Synchronises `stream` before returning (it reads back the bounded-wait flag:
+ *   OP_ERR_TIMEOUT if set).  Calls no cudaMalloc / cudaFree. */
+op_status op_gram_noalloc(int prec, long long n, int p, int ld, const void *U, const void *W,
+                          double *C, double *S, double *D, void *stream);
+
 /* Synchronises `stream`; OP_ERR_TIMEOUT if the last op_gram / op_update on ws reported a
  * bounded device wait that gave up, else OP_OK. */
 op_status op_ws_status(void *ws, void *stream);

@@ -87,6 +87,7 @@ def lib():
         "op_cg_workspace": (sz, [P(OpProblem), i32]),
         "op_gram": (i32, [i32, C.c_longlong, i32, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
         "op_gram_workspace": (sz, [i32, C.c_longlong, i32]),
+        "op_gram_noalloc": (i32, [i32, C.c_longlong, i32, i32, vp, vp, vp, vp, vp, vp]),
         "op_core": (i32, [i32, i32, i32, f64, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
         "op_core_workspace": (sz, [i32, i32]),
         "op_core_status": (i32, [vp, vp]),
@@ -298,6 +299,19 @@ def gram(U, W, p, want=("C", "S", "D"), stream=None):
     check(lib().op_gram(prec, n, p, ld, _tptr(U), _tptr(W), _tptr(out["C"]), _tptr(out["S"]),
                         _tptr(out["D"]), _tptr(ws), nbytes, st))
     check(lib().op_ws_status(_tptr(ws), st))
+    return out["C"], out["S"], out["D"]
+
+
+def gram_noalloc(U, W, p, want=("C", "S", "D"), stream=None):
+    """As gram(), through op_gram_noalloc (no device allocation by the library; the
+    output matrices are allocated here by torch, as a caller would)."""
+    import torch
+    n, ld = U.shape
+    prec = _prec_of(U)
+    out = {k: (torch.empty(ld, ld, dtype=torch.float64, device=U.device) if k in want else None)
+           for k in ("C", "S", "D")}
+    check(lib().op_gram_noalloc(prec, n, p, ld, _tptr(U), _tptr(W), _tptr(out["C"]),
+                                _tptr(out["S"]), _tptr(out["D"]), _stream_ptr(stream)))
     return out["C"], out["S"], out["D"]
 
 

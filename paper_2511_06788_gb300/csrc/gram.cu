@@ -225,6 +225,48 @@ op_status gram(long long n, int p, int ld, const T *U, const T *W, double *C, do
   return OP_OK;
 }
 
+// As gram(), but the chunk split is chosen so that the partials fit in part_bytes
+// (fewer, longer chunks when the scratch is small).  OP_ERR_ARG if even one chunk
+// per tile does not fit.
+template <typename T>
+op_status gram_fixed_scratch(long long n, int p, int ld, const T *U, const T *W, double *C,
+                             double *S, double *D, void *part, size_t part_bytes, cudaStream_t st) {
+  if (ld % 8 != 0 || ld > 255 * kTile || p > ld || n < 1) {
+    set_error("gram: bad sizes n=%lld p=%d ld=%d", n, p, ld);
+    return OP_ERR_ARG;
+  }
+  const int nt = (ld + kTile - 1) / kTile;
+  const int mask = (C ? 1 : 0) | (S ? 2 : 0) | (D ? 4 : 0);
+  const int nj = (C ? nt * nt : 0) + (S ? nt * (nt + 1) / 2 : 0) + (D ? nt * (nt + 1) / 2 : 0);
+  if (nj == 0) return OP_OK;
+  const size_t tile_bytes = (size_t)kTile * kTile * sizeof(double);
+  const long long fit = (long long)(part_bytes / ((size_t)nj * tile_bytes));
+  if (fit < 1) {
+    set_error("gram: %d output tiles need %zu bytes of partials, the fixed scratch holds %zu",
+              nj, (size_t)nj * tile_bytes, part_bytes);
+    return OP_ERR_ARG;
+  }
+  long long ns = (4 * kNumSMs + nj - 1) / nj;
+  const long long maxs = (n + 255) / 256;
+  if (ns > maxs) ns = maxs;
+  if (ns > fit) ns = fit;
+  if (ns < 1) ns = 1;
+  long long rps = (n + ns - 1) / ns;
+  rps = (rps + GramCfg<T>::KC - 1) / GramCfg<T>::KC * GramCfg<T>::KC;
+  const int nsplit = (int)((n + rps - 1) / rps);
+  k_gram<T, T><<<dim3(nj, nsplit), dim3(16, 16), 0, st>>>(n, ld, U, W, mask, nt, nj, rps,
+                                                         (double *)part);
+  count_launch();
+  OP_LAUNCH("k_gram");
+  k_gram_reduce<<<nj, 256, 0, st>>>(mask, nt, nj, nsplit, (const double *)part, p, ld, C, S, D);
+  count_launch();
+  OP_LAUNCH("k_gram_reduce");
+  return OP_OK;
+}
+template op_status gram_fixed_scratch<double>(long long, int, int, const double *, const double *,
+                                              double *, double *, double *, void *, size_t,
+                                              cudaStream_t);
+
 template op_status gram<float>(long long, int, int, const float *, const float *, double *,
                                double *, double *, void *, size_t, cudaStream_t);
 template op_status gram<double>(long long, int, int, const double *, const double *, double *,

@@ -291,4 +291,43 @@ op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, do
   return OP_OK;
 }
 
+// As gram_tc(), but the chunk split is chosen so that the partials fit in part_bytes.
+op_status gram_tc_fixed_scratch(long long n, int p, int ld, const float *U, const float *W,
+                                double *C, double *S, double *D, void *part, size_t part_bytes,
+                                int *err, cudaStream_t st) {
+  if (ld % 8 != 0 || p > ld || n < 1) {
+    set_error("gram_tc: bad sizes n=%lld p=%d ld=%d", n, p, ld);
+    return OP_ERR_ARG;
+  }
+  const int nt = (ld + kTM - 1) / kTM;
+  const int mask = (C ? 1 : 0) | (S ? 2 : 0) | (D ? 4 : 0);
+  const int nj = tc_jobs(nt, mask);
+  if (nj == 0) return OP_OK;
+  const size_t tile_bytes = (size_t)kTM * kTM * sizeof(double);
+  const long long fit = (long long)(part_bytes / ((size_t)nj * tile_bytes));
+  if (fit < 1) {
+    set_error("gram_tc: %d output tiles need %zu bytes of partials, the fixed scratch holds %zu",
+              nj, (size_t)nj * tile_bytes, part_bytes);
+    return OP_ERR_ARG;
+  }
+  int nsplit;
+  long long rps;
+  plan_tc(n, nj, &nsplit, &rps);
+  if (nsplit > fit) {
+    rps = (n + fit - 1) / fit;
+    rps = (rps + kKS - 1) / kKS * kKS;
+    nsplit = (int)((n + rps - 1) / rps);
+  }
+  OP_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  k_gram_tc<<<dim3(nj, nsplit), 256, kSmem, st>>>(n, ld, U, W, mask, nt, nj, rps, (double *)part,
+                                                   err);
+  count_launch();
+  OP_LAUNCH("k_gram_tc");
+  k_gram_tc_reduce<<<dim3(nj, 16), 256, 0, st>>>(mask, nt, nj, nsplit, (const double *)part, p,
+                                                   ld, C, S, D);
+  count_launch();
+  OP_LAUNCH("k_gram_tc_reduce");
+  return OP_OK;
+}
+
 }  // namespace opevo

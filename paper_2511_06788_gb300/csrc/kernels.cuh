@@ -102,6 +102,14 @@ size_t gram_tc_workspace_bytes(long long n, int ld);
 op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, double *C, double *S,
                   double *D, void *ws, size_t ws_bytes, int *err, cudaStream_t st);
 
+// Same outputs with the chunk split limited by a fixed scratch of part_bytes.
+template <typename T>
+op_status gram_fixed_scratch(long long n, int p, int ld, const T *U, const T *W, double *C,
+                             double *S, double *D, void *part, size_t part_bytes, cudaStream_t st);
+op_status gram_tc_fixed_scratch(long long n, int p, int ld, const float *U, const float *W,
+                                double *C, double *S, double *D, void *part, size_t part_bytes,
+                                int *err, cudaStream_t st);
+
 // ---- dense FP64 p x p algebra (dense.cu) --------------------------------------
 size_t core_workspace_bytes(int p, int ld);
 // ws layout begins with an int status word (0 ok, 1 not SPD).
