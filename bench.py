@@ -204,7 +204,7 @@ def run_ours(args):
     P = syn.config_3d_wells(seed)
     U0 = syn.gaussian_block(seed, P.n, P.p)
     n, p = P.n, P.p
-    s_el = 4 if args.prec == "fp32" else 8
+    s_el = 8 if args.prec == "fp64" else 4
 
     # inputs resident in HBM before timing: V and the raw U0 on the device
     V_d = torch.from_numpy(P.V).to(dev)
@@ -292,7 +292,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp64": "f64", "mix_tf32": "f32+tf32"}[args.prec],
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "p": p, "precision": args.prec,
                        "seed_per_rank": "rank", "l2": "inputs larger than L2 (each n x p block "
                        f"{n * p * s_el / 1e6:.0f} MB, working set > 0.8 GB)",
@@ -313,7 +314,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "mix_tf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

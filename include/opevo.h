@@ -56,8 +56,11 @@ typedef enum {
 
 typedef enum {
   OP_FP64 = 0,           /* blocks, stencil, CG, Gram and update in FP64           */
-  OP_FP32 = 1            /* blocks, stencil, CG and update in FP32; Gram partial sums
-                            flushed to FP64; Step 2-3 core in FP64                 */
+  OP_FP32 = 1,           /* blocks, stencil and CG in FP32; Gram and update on the
+                            tensor cores with a TF32 hi/lo split (FP32-class accuracy),
+                            Gram chunk sums in FP64; Step 2-3 core in FP64           */
+  OP_MIX_TF32 = 2        /* as OP_FP32 but one TF32 MMA per product (operands rounded
+                            to TF32, 10-bit mantissa); context-level API only        */
 } op_prec;
 
 typedef enum {

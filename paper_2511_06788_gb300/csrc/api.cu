@@ -142,7 +142,7 @@ op_status check_problem(const op_problem *pb) {
     set_error("p must be >= 1 (got %d)", pb->p);
     return OP_ERR_ARG;
   }
-  if (pb->prec != OP_FP64 && pb->prec != OP_FP32) {
+  if (pb->prec != OP_FP64 && pb->prec != OP_FP32 && pb->prec != OP_MIX_TF32) {
     set_error("unsupported precision mode %d", pb->prec);
     return OP_ERR_ARG;
   }
@@ -187,7 +187,7 @@ template <typename T>
 op_status gram_any(op_ctx *c, const T *U, const T *W, double *C, double *S, double *D) {
   if constexpr (std::is_same<T, float>::value)
     return gram_tc(c->n, c->p, c->ld, U, W, C, S, D, c->gram_ws, c->gram_bytes, c->dev_err,
-                   c->st);
+                   c->st, c->prec == OP_MIX_TF32 ? 0 : 1);
   else
     return gram<T>(c->n, c->p, c->ld, U, W, C, S, D, c->gram_ws, c->gram_bytes, c->st);
 }
@@ -212,7 +212,7 @@ template <typename T> op_status step_impl(op_ctx *c) {
   if constexpr (std::is_same<T, float>::value) {
     OP_TRY(launch_make_kt(c->ld, c->KU, c->KW, c->KT_hi, c->KT_lo, c->st));
     OP_TRY(update_tc(c->n, c->ld, (const float *)c->U, (const float *)c->W, c->KT_hi, c->KT_lo,
-                     (float *)c->U2, c->dev_err, c->st));
+                     (float *)c->U2, c->dev_err, c->st, c->prec == OP_MIX_TF32 ? 0 : 1));
   } else {
     OP_TRY(update<T>(c->n, c->ld, (const T *)c->U, (const T *)c->W, (const T *)c->KU_t,
                      (const T *)c->KW_t, (T *)c->U2, c->st));
@@ -483,7 +483,7 @@ op_status init_common(op_ctx **out, const op_problem *pb, const double *V, const
   c->p = pb->p;
   c->ld = round_up(pb->p, 8);
   c->prec = pb->prec;
-  c->elem = pb->prec == OP_FP64 ? 8 : 4;
+  c->elem = pb->prec == OP_FP64 ? 8 : 4;  // OP_FP32 and OP_MIX_TF32 store FP32 blocks
   c->st = (cudaStream_t)stream;
   op_status s = c->prec == OP_FP64 ? init_impl<double>(c, V, U0, device)
                                    : init_impl<float>(c, V, U0, device);

@@ -2,10 +2,11 @@
 // C = W^T U, S = W^T W, D = U^T U (§2.1; the matrices of Steps 2-3 and of
 // Theorem 4.1) with tcgen05.mma kind::tf32 and FP32 accumulation in TMEM.
 //
-// FP32 accuracy from TF32 units: every operand value x is split as
+// FP32 accuracy from TF32 units (split = 1): every operand value x is split as
 // x = hi + lo (hi = tf32(x), lo = tf32(x - hi)) and each product uses four
 // MMAs, hi*hi + hi*lo + lo*hi + lo*lo (the lo*lo term would otherwise leave a
-// one-signed error of ~2^-22 in the squared norms of <U,U> and <W,W>).
+// one-signed error of ~2^-22 in the squared norms of <U,U> and <W,W>).  With
+// split = 0 (the TF32 mixed mode) one MMA per product on tf32(x) is used.
 //
 // Work split: one CTA per (output tile of 128 x 128, chunk of grid points).
 // The contraction index is the grid point (the row of the n x ld blocks), so
@@ -77,9 +78,9 @@ __device__ __forceinline__ void load_patch(const float *__restrict__ X, long lon
 }
 
 // Split the patch and store it transposed: operand row m = 4q + e gets the
-// K-chunk kq = (v[0][e], .., v[3][e]).
+// K-chunk kq = (v[0][e], .., v[3][e]).  Without `split` only tf32(x) is stored.
 __device__ __forceinline__ void store_patch(uint8_t *hi, uint8_t *lo, int q, int kq,
-                                            const float (&v)[4][4]) {
+                                            const float (&v)[4][4], bool split) {
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     float4 h, l;
@@ -89,14 +90,14 @@ __device__ __forceinline__ void store_patch(uint8_t *hi, uint8_t *lo, int q, int
     tc::split_tf32(v[3][e], h.w, l.w);
     const uint32_t off = tc::sw128_offset(4 * q + e, kq);
     *reinterpret_cast<float4 *>(hi + off) = h;
-    *reinterpret_cast<float4 *>(lo + off) = l;
+    if (split) *reinterpret_cast<float4 *>(lo + off) = l;
   }
 }
 
 __global__ void __launch_bounds__(256, 1)
     k_gram_tc(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
               int mask, int nt, int njobs, long long rows_per_split, double *__restrict__ part,
-              int *err) {
+              int *err, int split) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar[2];  // one per TMEM accumulator
   __shared__ uint32_t tmem_base_sh;
@@ -159,8 +160,8 @@ __global__ void __launch_bounds__(256, 1)
     const int st = s & 1;
     uint8_t *stage = smem + st * kStage;
     // stage st was read by the MMAs of slab s-2, which the drain of slab s-2 waited for
-    store_patch(stage, stage + kPiece, q, kq, va);
-    store_patch(stage + 2 * kPiece, stage + 3 * kPiece, q, kq, vb);
+    store_patch(stage, stage + kPiece, q, kq, va, split != 0);
+    store_patch(stage + 2 * kPiece, stage + 3 * kPiece, q, kq, vb, split != 0);
     if (s + 2 < nslab) {
       const long long r = r0 + (long long)(s + 2) * kKS + 4 * kq;
       load_patch(A, r, r1, ca + 4 * q, ld, va);
@@ -180,9 +181,11 @@ __global__ void __launch_bounds__(256, 1)
         const uint64_t bh = tc::desc_sw128(base + 2 * kPiece + kk * 32);
         const uint64_t bl = tc::desc_sw128(base + 3 * kPiece + kk * 32);
         tc::mma_tf32(d, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
-        tc::mma_tf32(d, ah, bl, kIdesc, 1u);
-        tc::mma_tf32(d, al, bh, kIdesc, 1u);
-        tc::mma_tf32(d, al, bl, kIdesc, 1u);
+        if (split) {
+          tc::mma_tf32(d, ah, bl, kIdesc, 1u);
+          tc::mma_tf32(d, al, bh, kIdesc, 1u);
+          tc::mma_tf32(d, al, bl, kIdesc, 1u);
+        }
       }
       tc::mma_commit(&mbar[st]);
     }
@@ -263,7 +266,7 @@ size_t gram_tc_workspace_bytes(long long n, int ld) {
 }
 
 op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, double *C, double *S,
-                  double *D, void *ws, size_t ws_bytes, int *err, cudaStream_t st) {
+                  double *D, void *ws, size_t ws_bytes, int *err, cudaStream_t st, int split) {
   if (ld % 8 != 0 || p > ld || n < 1) {
     set_error("gram_tc: bad sizes n=%lld p=%d ld=%d", n, p, ld);
     return OP_ERR_ARG;
@@ -282,7 +285,8 @@ op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, do
   }
   OP_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
   double *part = (double *)ws;
-  k_gram_tc<<<dim3(nj, nsplit), 256, kSmem, st>>>(n, ld, U, W, mask, nt, nj, rps, part, err);
+  k_gram_tc<<<dim3(nj, nsplit), 256, kSmem, st>>>(n, ld, U, W, mask, nt, nj, rps, part, err,
+                                                   split);
   count_launch();
   OP_LAUNCH("k_gram_tc");
   k_gram_tc_reduce<<<dim3(nj, 16), 256, 0, st>>>(mask, nt, nj, nsplit, part, p, ld, C, S, D);
@@ -320,7 +324,7 @@ op_status gram_tc_fixed_scratch(long long n, int p, int ld, const float *U, cons
   }
   OP_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
   k_gram_tc<<<dim3(nj, nsplit), 256, kSmem, st>>>(n, ld, U, W, mask, nt, nj, rps, (double *)part,
-                                                   err);
+                                                   err, 1);
   count_launch();
   OP_LAUNCH("k_gram_tc");
   k_gram_tc_reduce<<<dim3(nj, 16), 256, 0, st>>>(mask, nt, nj, nsplit, (const double *)part, p,

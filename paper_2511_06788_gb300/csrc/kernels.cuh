@@ -99,8 +99,9 @@ op_status gram(long long n, int p, int ld, const T *U, const T *W, double *C, do
 // FP32 blocks on the tensor cores (gram_tc.cu): same outputs as gram<float>; *err is set
 // (device int) when a bounded wait inside the kernel gave up.
 size_t gram_tc_workspace_bytes(long long n, int ld);
+// split = 1: four-term TF32 split (FP32-class accuracy); 0: one TF32 MMA per product.
 op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, double *C, double *S,
-                  double *D, void *ws, size_t ws_bytes, int *err, cudaStream_t st);
+                  double *D, void *ws, size_t ws_bytes, int *err, cudaStream_t st, int split = 1);
 
 // Same outputs with the chunk split limited by a fixed scratch of part_bytes.
 template <typename T>
@@ -149,6 +150,6 @@ op_status launch_make_kt_f32(int ld, const float *KU, const float *KW, float *KT
                              float *KT_lo, cudaStream_t st);
 // Unew = [U W] [KU; KW] on the tensor cores (FP32 blocks); *err as for gram_tc.
 op_status update_tc(long long n, int ld, const float *U, const float *W, const float *KT_hi,
-                    const float *KT_lo, float *Unew, int *err, cudaStream_t st);
+                    const float *KT_lo, float *Unew, int *err, cudaStream_t st, int split = 1);
 
 }  // namespace opevo

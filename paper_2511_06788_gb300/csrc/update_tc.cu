@@ -1,6 +1,7 @@
 // Step 4 of §4.1 for FP32 blocks on the 5th-generation tensor cores:
 // Unew = [U W] [KU; KW] as tcgen05.mma kind::tf32 with FP32 accumulation in
-// TMEM (3xTF32: hi*hi + hi*lo + lo*hi, FP32-class accuracy).
+// TMEM (split = 1: 3xTF32, hi*hi + hi*lo + lo*hi, FP32-class accuracy;
+// split = 0, the TF32 mixed mode: one MMA on the TF32-rounded values).
 //
 // The tensor core adds into its FP32 accumulator with truncation, so the MMAs
 // accumulate only the correction [U W] [KU - I; KW] (small once the iteration
@@ -37,7 +38,7 @@ constexpr uint32_t kIdesc = tc::idesc_tf32(kTM, kTN);
 __global__ void __launch_bounds__(256, 1)
     k_update_tc(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
                 const float *__restrict__ KT_hi, const float *__restrict__ KT_lo,
-                float *__restrict__ Unew, int *err) {
+                float *__restrict__ Unew, int *err, int split) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar[2];  // one per TMEM accumulator
   __shared__ uint32_t tmem_base_sh;
@@ -123,9 +124,11 @@ __global__ void __launch_bounds__(256, 1)
       tc::split_tf32(va[j].w, h.w, l.w);
       const uint32_t off = tc::sw128_offset(r, kq);
       *reinterpret_cast<float4 *>(stage + off) = h;
-      *reinterpret_cast<float4 *>(stage + kPieceA + off) = l;
       *reinterpret_cast<float4 *>(stage + 2 * kPieceA + off) = vh[j];
-      *reinterpret_cast<float4 *>(stage + 2 * kPieceA + kPieceB + off) = vl[j];
+      if (split) {
+        *reinterpret_cast<float4 *>(stage + kPieceA + off) = l;
+        *reinterpret_cast<float4 *>(stage + 2 * kPieceA + kPieceB + off) = vl[j];
+      }
     }
     if (s + 1 < nslab) load(s + 1);
     tc::fence_async_smem();
@@ -142,8 +145,10 @@ __global__ void __launch_bounds__(256, 1)
         const uint64_t bh = tc::desc_sw128(base + 2 * kPieceA + kk * 32);
         const uint64_t bl = tc::desc_sw128(base + 2 * kPieceA + kPieceB + kk * 32);
         tc::mma_tf32(d, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
-        tc::mma_tf32(d, ah, bl, kIdesc, 1u);
-        tc::mma_tf32(d, al, bh, kIdesc, 1u);
+        if (split) {
+          tc::mma_tf32(d, ah, bl, kIdesc, 1u);
+          tc::mma_tf32(d, al, bh, kIdesc, 1u);
+        }
       }
       tc::mma_commit(&mbar[st]);
     }
@@ -209,14 +214,14 @@ op_status launch_make_kt_f32(int ld, const float *KU, const float *KW, float *KT
 }
 
 op_status update_tc(long long n, int ld, const float *U, const float *W, const float *KT_hi,
-                    const float *KT_lo, float *Unew, int *err, cudaStream_t st) {
+                    const float *KT_lo, float *Unew, int *err, cudaStream_t st, int split) {
   if (ld % 8 != 0 || n < 1) {
     set_error("update_tc: bad sizes n=%lld ld=%d", n, ld);
     return OP_ERR_ARG;
   }
   OP_CUDA(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
   const dim3 grid((unsigned)((n + kTM - 1) / kTM), (ld + kTN - 1) / kTN);
-  k_update_tc<<<grid, 256, kSmem, st>>>(n, ld, U, W, KT_hi, KT_lo, Unew, err);
+  k_update_tc<<<grid, 256, kSmem, st>>>(n, ld, U, W, KT_hi, KT_lo, Unew, err, split);
   count_launch();
   OP_LAUNCH("k_update_tc");
   return OP_OK;
