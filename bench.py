@@ -309,6 +309,76 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """64 uneven problems (N ~ U{24..48}^3, p ~ U{16..96}, 2-12 wells), FP32, advanced by
+    one graph replay per step of batched kernels; value = sum n p steps / s."""
+    import torch
+
+    import paper_2511_06788_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    probs = syn.batch_problems(seed=rank, count=args.batch_count)
+    solvers = []
+    for i, P in enumerate(probs):
+        V_d = torch.from_numpy(P.V).to(dev)
+        U0_d = torch.from_numpy(syn.gaussian_block(1000 * rank + i, P.n, P.p)).to(dev)
+        solvers.append(pkg.Solver(P.shape, P.lo, P.hi, V_d, U0_d, P.p, prec="fp32", device=True))
+    units = sum(P.n * P.p for P in probs)
+    batch = pkg.Batch(solvers, cg_iters=args.cg_iters)
+    cache = os.environ.get("OPEVO_TILE_CACHE", os.path.join(ROOT, "_build", "batch_tiles.jsonl"))
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    tune_ms = batch.autotune(cache, steps_per_trial=2)
+    batch.step(args.warmup)
+    L = pkg.lib()
+    l0 = L.op_kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    batch.step(args.steps)  # synchronises the batch stream at the end
+    ms = (time.perf_counter() - t0) * 1e3
+    clk = clocks.stop()
+    launches = L.op_kernel_launches() - l0
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = units * args.steps * ws / (ms * 1e-3)
+    iters = [batch.stats(i)["last_cg_iters"] for i in range(len(probs))]
+    batch.close()
+    # the same problems stepped one context at a time (per-problem launches)
+    t0 = time.perf_counter()
+    for s in solvers:
+        s.step(2)
+    loop_ms = (time.perf_counter() - t0) * 1e3 / 2
+    for s in solvers:
+        s.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch{len(probs)}_uneven_24-48^3_p16-96",
+                       "problems": len(probs), "sum_np": units, "cg_iters_per_step": args.cg_iters,
+                       "timing": "host wall clock around the graph replays (one sync at the end)"},
+            "tiles": {"rows_per_item_and_gram_rows": None, "autotune_ms_per_step": tune_ms},
+            "per_problem_loop": {"value": units / (loop_ms * 1e-3), "ms_per_step": loop_ms},
+            "last_cg_iters_range": [min(iters), max(iters)], "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,11 +387,16 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "mix_tf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="3d_wells_64", choices=["3d_wells_64", "batch64"])
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--cg-iters", type=int, default=12)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -175,6 +175,50 @@ op_status op_profile_read(op_ctx *ctx, int kind, double *total_ms, long long *la
 void op_destroy(op_ctx *ctx);
 
 /* ---------------------------------------------------------------------------
+ * Batches: many independent problems (uneven n and p) advanced together.
+ * A time step of every problem is one replay of a CUDA graph of batched kernels
+ * (work lists over (problem, grid-point range), (problem, Gram chunk),
+ * (problem, update tile), one CTA per problem for the FP64 core); Step 1 runs a
+ * fixed number `cg_iters` of CG iterations per step whose kernels return at once
+ * for problems whose CG has converged.  The CG tolerance, the energy, err_E and
+ * the freeze of converged problems are computed on the device.
+ * ------------------------------------------------------------------------- */
+typedef struct op_batch op_batch;
+
+/* Group `count` contexts (each OP_FP32, p <= 128; not copied, still owned by the
+ * caller) into a batch.  The batch captures and replays its graphs on a stream of
+ * its own; `stream` and the contexts' streams are synchronised at creation, and
+ * every batch call that returns results synchronises the batch stream.  While the batch exists the
+ * contexts must not be stepped on their own (they may be read: op_get_U,
+ * op_eigenvalues, op_residual, op_get_stats).  Destroy the batch before the contexts. */
+op_status op_batch_create(op_batch **b, op_ctx *const *ctxs, int count, int cg_iters,
+                          void *stream);
+/* Work-list granularity: grid points per stencil/CG/energy item (>= 32) and per Gram
+ * chunk (>= 256, multiple of 32).  Rebuilds the graphs.  Synchronises. */
+op_status op_batch_set_tiles(op_batch *b, int rows_per_item, int gram_rows);
+op_status op_batch_get_tiles(op_batch *b, int *rows_per_item, int *gram_rows);
+/* Autotuner: time `steps_per_trial` steps for each candidate granularity (the steps
+ * advance the problems), keep the fastest and append it to the JSON-lines file
+ * `cache_path` (may be NULL) keyed by the batch's shape; a cached entry for the same
+ * shape is reused without trials.  *best_ms (may be NULL): ms per step. */
+op_status op_batch_autotune(op_batch *b, const char *cache_path, int steps_per_trial,
+                            double *best_ms);
+/* Advance every unfrozen problem by `nsteps` steps; synchronises at the end and
+ * updates each context's statistics. */
+op_status op_batch_step(op_batch *b, int nsteps);
+/* Step until every problem meets the stop rule (OP_STOP_ERR_E, evaluated on the device
+ * every step, or OP_STOP_RESIDUAL, evaluated every check_every steps) or max_steps;
+ * converged problems are frozen.  *nconverged (may be NULL) receives the count.
+ * OP_ERR_STATE if some problem did not converge. */
+op_status op_batch_solve(op_batch *b, double tol, int max_steps, int stop, int check_every,
+                         int *nconverged);
+/* Clear the freeze of every problem (e.g. to continue past a looser rule). */
+op_status op_batch_unfreeze(op_batch *b);
+/* Statistics of problem i and its freeze state (0 active, 1 converged, 2 diverged). */
+op_status op_batch_stats(op_batch *b, int i, op_stats *st, int *frozen);
+void op_batch_destroy(op_batch *b);
+
+/* ---------------------------------------------------------------------------
  * Kernel-level API: single steps of the path on caller-owned device buffers.
  * `prec` selects the element type T of the blocks: double (OP_FP64) or float
  * (OP_FP32).  Blocks are n x ld, ld >= p, ld a multiple of 8.

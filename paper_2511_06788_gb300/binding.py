@@ -82,6 +82,15 @@ def lib():
         "op_profile_name": (C.c_char_p, [i32]),
         "op_profile_read": (i32, [vp, i32, P(f64), P(C.c_longlong)]),
         "op_destroy": (None, [vp]),
+        "op_batch_create": (i32, [P(vp), P(vp), i32, i32, vp]),
+        "op_batch_set_tiles": (i32, [vp, i32, i32]),
+        "op_batch_get_tiles": (i32, [vp, P(i32), P(i32)]),
+        "op_batch_autotune": (i32, [vp, C.c_char_p, i32, P(f64)]),
+        "op_batch_step": (i32, [vp, i32]),
+        "op_batch_solve": (i32, [vp, f64, i32, i32, i32, P(i32)]),
+        "op_batch_unfreeze": (i32, [vp]),
+        "op_batch_stats": (i32, [vp, i32, P(OpStats), P(i32)]),
+        "op_batch_destroy": (None, [vp]),
         "op_apply_H": (i32, [P(OpProblem), i32, vp, f64, vp, vp, vp]),
         "op_cg_solve": (i32, [P(OpProblem), i32, vp, f64, vp, vp, f64, i32, vp, sz, P(i32), vp]),
         "op_cg_workspace": (sz, [P(OpProblem), i32]),
@@ -241,6 +250,72 @@ class Solver:
         lam = np.empty(self.p)
         check(lib().op_eigenvalues(self._ctx, _dptr(lam), int(kind)))
         return lam
+
+
+class Batch:
+    """Many FP32 Solver contexts advanced together by graph-captured batched kernels.
+
+    The solvers stay owned by the caller and must outlive the batch; while the batch
+    exists they must not be stepped individually."""
+
+    def __init__(self, solvers, cg_iters=12, stream=None):
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s._ctx.value for s in self.solvers])
+        self._b = C.c_void_p()
+        check(lib().op_batch_create(C.byref(self._b), arr, len(self.solvers), int(cg_iters),
+                                    _stream_ptr(stream)))
+
+    def close(self):
+        if self._b:
+            lib().op_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_tiles(self, rows_per_item, gram_rows):
+        check(lib().op_batch_set_tiles(self._b, int(rows_per_item), int(gram_rows)))
+
+    def tiles(self):
+        r, g = C.c_int(), C.c_int()
+        check(lib().op_batch_get_tiles(self._b, C.byref(r), C.byref(g)))
+        return r.value, g.value
+
+    def autotune(self, cache_path=None, steps_per_trial=2):
+        ms = C.c_double()
+        path = cache_path.encode() if cache_path else None
+        check(lib().op_batch_autotune(self._b, path, int(steps_per_trial), C.byref(ms)))
+        return ms.value
+
+    def step(self, nsteps=1):
+        check(lib().op_batch_step(self._b, int(nsteps)))
+
+    def solve(self, tol, max_steps, stop=OP_STOP_RESIDUAL, check_every=10, raise_on_max=True):
+        nc = C.c_int()
+        s = lib().op_batch_solve(self._b, float(tol), int(max_steps), int(stop), int(check_every),
+                                 C.byref(nc))
+        if s != OP_OK and (raise_on_max or s != OP_ERR_STATE):
+            check(s)
+        return nc.value
+
+    def unfreeze(self):
+        check(lib().op_batch_unfreeze(self._b))
+
+    def stats(self, i):
+        st, fr = OpStats(), C.c_int()
+        check(lib().op_batch_stats(self._b, int(i), C.byref(st), C.byref(fr)))
+        d = st.as_dict()
+        d["frozen"] = fr.value
+        return d
 
 
 # ----------------------------------------------------------------------------

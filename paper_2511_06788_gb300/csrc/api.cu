@@ -19,6 +19,8 @@ static thread_local char g_err[1024] = "";
 static std::atomic<long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(); }
 
 void set_error(const char *fmt, ...) {
   va_list ap;
@@ -80,34 +82,7 @@ static double spectrum_lower_bound(const op_problem *pb, double vmin) {
 
 using namespace opevo;
 
-struct op_ctx {
-  op_problem pb;
-  Geom g;
-  long long n;
-  int p, ld, prec, elem;
-  double sigma, tau, hnorm;
-  cudaStream_t st;
-  // blocks (element type T)
-  void *U, *U2, *W, *Vt;
-  // p x p (ld x ld) FP64 matrices
-  double *C, *S, *D, *KU, *KW, *Th, *eig_work, *lam_d;
-  void *KU_t, *KW_t;
-  float *KT_hi, *KT_lo;  // FP32 blocks: [KU; KW]^T split for the tensor-core update
-  int *dev_err;          // set by a tensor-core kernel whose bounded wait gave up
-  void *cg_ws, *gram_ws, *core_ws;
-  size_t gram_bytes;
-  CGWork cgw;
-  Prof prof;
-  double *part;  // [max_blocks][2][ld] for quad / sumsq
-  double *dsc;   // device scalars: 0..2 core stats, 4..5 quad, 6 sumsq
-  double *hsc;   // pinned mirror
-  int *hpin_int;
-  op_stats stats;
-  double E;
-  double g_rel;  // last relative G-residual sqrt(g2 / trS)
-  double cg_cap; // op_solve: upper bound of the adaptive CG tolerance (from its stop rule)
-  std::vector<void *> allocs;
-};
+#include "ctx.cuh"
 
 namespace {
 

@@ -49,6 +49,8 @@ op_status make_geom(const op_problem *pb, Geom *g);
 
 // Number of kernels this library has launched (process-wide).
 void count_launch();
+void count_launches(long long k);
+long long launches_so_far();
 
 // 16-byte vector of T: float4 / double2.
 template <typename T> struct V16;

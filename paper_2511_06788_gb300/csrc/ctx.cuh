@@ -1,0 +1,38 @@
+// Private definition of a solver context (shared by api.cu and batch.cu).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace opevo;
+
+struct op_ctx {
+  op_problem pb;
+  Geom g;
+  long long n;
+  int p, ld, prec, elem;
+  double sigma, tau, hnorm;
+  cudaStream_t st;
+  // blocks (element type T)
+  void *U, *U2, *W, *Vt;
+  // p x p (ld x ld) FP64 matrices
+  double *C, *S, *D, *KU, *KW, *Th, *eig_work, *lam_d;
+  void *KU_t, *KW_t;
+  float *KT_hi, *KT_lo;  // FP32 blocks: [KU; KW]^T split for the tensor-core update
+  int *dev_err;          // set by a tensor-core kernel whose bounded wait gave up
+  void *cg_ws, *gram_ws, *core_ws;
+  size_t gram_bytes;
+  CGWork cgw;
+  Prof prof;
+  double *part;  // [max_blocks][2][ld] for quad / sumsq
+  double *dsc;   // device scalars: 0..2 core stats, 4..5 quad, 6 sumsq
+  double *hsc;   // pinned mirror
+  int *hpin_int;
+  op_stats stats;
+  double E;
+  double g_rel;  // last relative G-residual sqrt(g2 / trS)
+  double cg_cap; // op_solve: upper bound of the adaptive CG tolerance (from its stop rule)
+  std::vector<void *> allocs;
+};

@@ -32,11 +32,13 @@ constexpr int kT = 8;  // tile of the small GEMM (8 x 8 outputs per CTA: many CT
 // loads in flight together (one L2 round trip per chunk).
 constexpr int kKC = 128;
 template <typename T>
-__global__ void k_small_gemm(int p, int ld, double alpha, const double *__restrict__ A, int ta,
-                             const double *__restrict__ B, int tb, double beta,
-                             const double *__restrict__ X, double d1, double d2,
-                             const double *__restrict__ Y, double gamma, double *__restrict__ out,
-                             T *__restrict__ tout, const int *__restrict__ status) {
+__device__ __forceinline__ void small_gemm_body(int p, int ld, double alpha,
+                                                const double *__restrict__ A, int ta,
+                                                const double *__restrict__ B, int tb, double beta,
+                                                const double *__restrict__ X, double d1, double d2,
+                                                const double *__restrict__ Y, double gamma,
+                                                double *__restrict__ out, T *__restrict__ tout,
+                                                const int *__restrict__ status) {
   __shared__ double As[kT][kKC + 1], Bs[kKC][kT + 1];
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * kT + tx;
   const int i0 = blockIdx.y * kT, j0 = blockIdx.x * kT;
@@ -66,6 +68,15 @@ __global__ void k_small_gemm(int p, int ld, double alpha, const double *__restri
   }
   out[(long long)i * ld + j] = v;
   if (tout) tout[(long long)i * ld + j] = (T)v;
+}
+
+template <typename T>
+__global__ void k_small_gemm(int p, int ld, double alpha, const double *__restrict__ A, int ta,
+                             const double *__restrict__ B, int tb, double beta,
+                             const double *__restrict__ X, double d1, double d2,
+                             const double *__restrict__ Y, double gamma, double *__restrict__ out,
+                             T *__restrict__ tout, const int *__restrict__ status) {
+  small_gemm_body<T>(p, ld, alpha, A, ta, B, tb, beta, X, d1, d2, Y, gamma, out, tout, status);
 }
 
 // In-place LU factorisation without pivoting of the p x p matrix M into LU (unit
@@ -199,8 +210,8 @@ __global__ void k_tri_cols(int p, int ld, const double *__restrict__ L, int mode
 // refinement in core(): on GB300 an FP64 factorisation on one SM costs
 // ~p^3/3 / (2 FMA/clk), while FP32 runs 64x faster.
 // status <- 1 on a zero or non-finite pivot.
-__global__ void __launch_bounds__(1024) k_gj32(int p, int ld, const double *__restrict__ M,
-                                               double *__restrict__ X, int *status) {
+__device__ __forceinline__ void gj32_body(int p, int ld, const double *__restrict__ M,
+                                          double *__restrict__ X, int *status) {
   __shared__ float rowk[2][256];
   __shared__ float colk[2][128];
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -270,6 +281,11 @@ __global__ void __launch_bounds__(1024) k_gj32(int p, int ld, const double *__re
     }
   // entries of X beyond the 128 x 128 block (ld > 128 cannot occur here: p <= 128 gives
   // ld <= 128)
+}
+
+__global__ void __launch_bounds__(1024) k_gj32(int p, int ld, const double *__restrict__ M,
+                                               double *__restrict__ X, int *status) {
+  gj32_body(p, ld, M, X, status);
 }
 
 // KW = tau B (FP64 and T copies); zero after a factorisation breakdown.
@@ -449,6 +465,83 @@ __global__ void k_convert(int count, const double *__restrict__ src, T *__restri
 
 }  // namespace
 
+namespace {
+// ---- batched core (one problem per blockIdx.z / blockIdx.x) --------------------------
+enum { BC_M = 0, BC_R = 1, BC_X = 2, BC_K = 3 };
+
+// The GEMMs of the core for problem blockIdx.z:
+//   BC_M: M = I + tau/2 (C - C^T) + tau^2/4 (S - C C^T)
+//   BC_R: R = I - M X          BC_X: B = X + X R          BC_K: KU = 2B - I - tau C^T B
+__global__ void k_b_core_gemm(const BatchProb *__restrict__ Bp, int op) {
+  const BatchProb &pb = Bp[blockIdx.z];
+  if (*pb.frozen) return;
+  const int p = pb.p, ld = pb.ld;
+  if ((int)(blockIdx.y * kT) >= ld || (int)(blockIdx.x * kT) >= ld) return;
+  const double tau = pb.tau, q = 0.25 * tau * tau;
+  switch (op) {
+    case BC_M:
+      small_gemm_body<double>(p, ld, -q, pb.C, 0, pb.C, 1, q, pb.S, 0.5 * tau, -0.5 * tau, pb.C,
+                              1.0, pb.core_M, (double *)nullptr, (const int *)nullptr);
+      break;
+    case BC_R:
+      small_gemm_body<double>(p, ld, -1.0, pb.core_M, 0, pb.core_X, 0, 0.0,
+                              (const double *)nullptr, 0.0, 0.0, (const double *)nullptr, 1.0,
+                              pb.core_R, (double *)nullptr, (const int *)nullptr);
+      break;
+    case BC_X:
+      small_gemm_body<double>(p, ld, 1.0, pb.core_X, 0, pb.core_R, 0, 1.0, pb.core_X, 0.0, 0.0,
+                              (const double *)nullptr, 0.0, pb.core_B, (double *)nullptr,
+                              (const int *)nullptr);
+      break;
+    default:
+      small_gemm_body<double>(p, ld, -tau, pb.C, 1, pb.core_B, 0, 2.0, pb.core_B, 0.0, 0.0,
+                              (const double *)nullptr, -1.0, pb.KU, (double *)nullptr,
+                              pb.core_status);
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_b_gj32(const BatchProb *__restrict__ Bp) {
+  const BatchProb &pb = Bp[blockIdx.x];
+  if (*pb.frozen) return;
+  gj32_body(pb.p, pb.ld, pb.core_M, pb.core_X, pb.core_status);
+}
+
+// Per problem (blockIdx.x): status reset, core statistics into dsc[0..2], after the
+// Gram; KW = tau B after the inverse (second launch, stage 1).
+__global__ void k_b_core_misc(const BatchProb *__restrict__ Bp, int stage) {
+  const BatchProb &pb = Bp[blockIdx.x];
+  if (*pb.frozen) return;
+  const int p = pb.p, ld = pb.ld;
+  if (stage == 0) {
+    __shared__ double sh[32];
+    if (threadIdx.x == 0) *pb.core_status = 0;
+    double trs = 0.0, cc = 0.0, dd = 0.0;
+    for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x) {
+      const int i = (int)(e / p), j = (int)(e % p);
+      const long long o = (long long)i * ld + j;
+      if (i == j) trs += pb.S[o];
+      cc += pb.C[o] * pb.C[o];
+      const double d = pb.D[o] - (i == j ? 1.0 : 0.0);
+      dd += d * d;
+    }
+    trs = block_sum(trs, sh);
+    cc = block_sum(cc, sh);
+    dd = block_sum(dd, sh);
+    if (threadIdx.x == 0) {
+      pb.dsc[0] = trs - cc;
+      pb.dsc[1] = sqrt(dd);
+      pb.dsc[2] = trs;
+    }
+  } else {
+    const bool failed = *pb.core_status != 0;
+    for (long long e = threadIdx.x; e < (long long)ld * ld; e += blockDim.x)
+      pb.KW[e] = failed ? 0.0 : pb.tau * pb.core_B[e];
+  }
+}
+
+}  // namespace
+
 size_t core_workspace_bytes(int p, int ld) {
   (void)p;
   return 256 + 4 * (size_t)ld * ld * sizeof(double);
@@ -552,6 +645,26 @@ op_status launch_resid_coeff(int p, int ld, const double *Th, T *negTh, T *Id, c
 op_status launch_paper_lams(int p, const double *mu, double sigma, double *lam, cudaStream_t st) {
   k_paper_lams<<<(p + 255) / 256, 256, 0, st>>>(p, mu, sigma, lam); count_launch();
   OP_LAUNCH("k_paper_lams");
+  return OP_OK;
+}
+
+op_status launch_b_core(const BatchProb *B, int nprob, int max_ld, cudaStream_t st) {
+  const dim3 tb(kT, kT), tg((max_ld + kT - 1) / kT, (max_ld + kT - 1) / kT, nprob);
+  k_b_core_misc<<<nprob, 1024, 0, st>>>(B, 0);
+  count_launch();
+  k_b_core_gemm<<<tg, tb, 0, st>>>(B, BC_M);
+  count_launch();
+  k_b_gj32<<<nprob, dim3(32, 32), 0, st>>>(B);
+  count_launch();
+  k_b_core_gemm<<<tg, tb, 0, st>>>(B, BC_R);
+  count_launch();
+  k_b_core_gemm<<<tg, tb, 0, st>>>(B, BC_X);
+  count_launch();
+  k_b_core_gemm<<<tg, tb, 0, st>>>(B, BC_K);
+  count_launch();
+  k_b_core_misc<<<nprob, 1024, 0, st>>>(B, 1);
+  count_launch();
+  OP_LAUNCH("batched core");
   return OP_OK;
 }
 

@@ -94,23 +94,21 @@ __device__ __forceinline__ void store_patch(uint8_t *hi, uint8_t *lo, int q, int
   }
 }
 
-__global__ void __launch_bounds__(256, 1)
-    k_gram_tc(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
-              int mask, int nt, int njobs, long long rows_per_split, double *__restrict__ part,
-              int *err, int split) {
+// One CTA: output tile (ti, tj) of product `prod` over grid points [r0, r1) of the
+// n x ld blocks U, W, written as a 128 x 128 FP64 partial tile at dst.
+__device__ __forceinline__ void gram_tc_body(long long n, int ld, const float *__restrict__ U,
+                                             const float *__restrict__ W, int prod, int ti,
+                                             int tj, long long r0, long long r1,
+                                             double *__restrict__ dst_tile, int *err, int split) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar[2];  // one per TMEM accumulator
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
-  int prod, ti, tj;
-  decode_job(blockIdx.x, mask, nt, &prod, &ti, &tj);
   const float *A = (prod == PROD_D) ? U : W;
   const float *B = (prod == PROD_S) ? W : U;
   const int ca = ti * kTM, cb = tj * kTM;
-  const long long r0 = (long long)blockIdx.y * rows_per_split;
-  long long r1 = r0 + rows_per_split;
   if (r1 > n) r1 = n;
   const int nslab = r1 > r0 ? (int)((r1 - r0 + kKS - 1) / kKS) : 0;
 
@@ -211,14 +209,59 @@ __global__ void __launch_bounds__(256, 1)
   if (!ok || abort_sh) {
     if (t == 0) atomicExch(err, 1);
   } else {
-    double *dst = part + ((long long)blockIdx.y * njobs + blockIdx.x) * (kTM * kTM) +
-                  row * kTM + half * 64;
+    double *dst = dst_tile + row * kTM + half * 64;
 #pragma unroll
     for (int i = 0; i < 64; ++i) dst[i] = (double)acc[i];
   }
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 2 * kTM);
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_gram_tc(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
+              int mask, int nt, int njobs, long long rows_per_split, double *__restrict__ part,
+              int *err, int split) {
+  int prod, ti, tj;
+  decode_job(blockIdx.x, mask, nt, &prod, &ti, &tj);
+  const long long r0 = (long long)blockIdx.y * rows_per_split;
+  gram_tc_body(n, ld, U, W, prod, ti, tj, r0, r0 + rows_per_split,
+               part + ((long long)blockIdx.y * njobs + blockIdx.x) * (kTM * kTM), err, split);
+}
+
+// Batched: one CTA per GramItem (problem, job, grid-point chunk); all three products.
+__global__ void __launch_bounds__(256, 1)
+    k_b_gram_tc(const BatchProb *__restrict__ Bp, const GramItem *__restrict__ items, int parity) {
+  const GramItem it = items[blockIdx.x];
+  const BatchProb &pb = Bp[it.prob];
+  if (*pb.frozen) return;
+  const int nt = (pb.ld + kTM - 1) / kTM;
+  int prod, ti, tj;
+  decode_job(it.job, 7, nt, &prod, &ti, &tj);
+  gram_tc_body(pb.g.n, pb.ld, pb.U[parity], pb.W, prod, ti, tj, it.r0, it.r1,
+               pb.gram_part + ((long long)it.split * pb.gram_jobs + it.job) * (kTM * kTM), pb.err,
+               1);
+}
+
+// Batched reduce: grid (jobs, problems).
+__global__ void k_b_gram_tc_reduce(const BatchProb *__restrict__ Bp) {
+  const BatchProb &pb = Bp[blockIdx.y];
+  if (*pb.frozen || (int)blockIdx.x >= pb.gram_jobs) return;
+  const int ld = pb.ld, p = pb.p;
+  const int nt = (ld + kTM - 1) / kTM;
+  int prod, ti, tj;
+  decode_job(blockIdx.x, 7, nt, &prod, &ti, &tj);
+  double *out = prod == PROD_C ? pb.C : (prod == PROD_S ? pb.S : pb.D);
+  for (int e = threadIdx.x; e < kTM * kTM; e += blockDim.x) {
+    const int i = ti * kTM + e / kTM, j = tj * kTM + e % kTM;
+    if (i >= ld || j >= ld) continue;
+    double s = 0.0;
+    for (int sp = 0; sp < pb.n_gram_splits; ++sp)
+      s += pb.gram_part[((long long)sp * pb.gram_jobs + blockIdx.x) * (kTM * kTM) + e];
+    const double v = (i < p && j < p) ? s : 0.0;
+    out[(long long)i * ld + j] = v;
+    if (prod != PROD_C && ti != tj) out[(long long)j * ld + i] = v;
+  }
 }
 
 __global__ void k_gram_tc_reduce(int mask, int nt, int njobs, int nsplit,
@@ -333,5 +376,21 @@ op_status gram_tc_fixed_scratch(long long n, int p, int ld, const float *U, cons
   OP_LAUNCH("k_gram_tc_reduce");
   return OP_OK;
 }
+
+op_status launch_b_gram(const BatchProb *B, const GramItem *items, int nitems, int nprob,
+                        int parity, cudaStream_t st) {
+  OP_CUDA(cudaFuncSetAttribute(k_b_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  k_b_gram_tc<<<nitems, 256, kSmem, st>>>(B, items, parity);
+  count_launch();
+  OP_LAUNCH("k_b_gram_tc");
+  // at most 3 * 8 * 8 + ... jobs for ld <= 1024: grid x covers the largest job count
+  k_b_gram_tc_reduce<<<dim3(tc_jobs(8, 7), nprob), 256, 0, st>>>(B);
+  count_launch();
+  OP_LAUNCH("k_b_gram_tc_reduce");
+  return OP_OK;
+}
+
+size_t gram_tc_tile_bytes() { return (size_t)kTM * kTM * sizeof(double); }
+int gram_tc_jobs_all(int ld) { return tc_jobs((ld + kTM - 1) / kTM, 7); }
 
 }  // namespace opevo

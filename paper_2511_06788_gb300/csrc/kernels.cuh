@@ -39,6 +39,64 @@ void prof_end(Prof *p, cudaStream_t st);
 // accumulate the recorded pairs; the stream must have been synchronised
 void prof_harvest(Prof *p);
 
+// ---- batches of independent problems (FP32 blocks) ------------------------
+// One problem of a batch: device pointers into the problem's own context.  The
+// batched kernels read these descriptors from device memory; a work list maps
+// each CTA to (problem, piece of work).
+struct BatchProb {
+  Geom g;
+  int p, ld;
+  float shift;             // cdiag + sigma in FP32 (the CG operator's diagonal offset)
+  double tau;
+  const float *Vt;
+  float *U[2];             // U and U+ (roles alternate with the step parity)
+  float *W, *R, *P, *Q;    // Step-1 solution and CG buffers (P, Q: direction buffers)
+  double *part;            // row-kernel CTA partials [items][2][ld] + column sums [2][ld]
+  double *state;           // CG state [6][ld]
+  int *active, *ctl;       // CG control (ctl[0..1] active counts, ctl[2] iterations)
+  double *cg_rtol2;        // squared relative CG tolerance of the current step
+  double *C, *S, *D, *KU, *KW;
+  float *KT_hi, *KT_lo;
+  int *core_status;
+  double *core_M, *core_X, *core_B, *core_R;  // ld x ld each
+  double *gram_part;       // Gram chunk partials [splits][jobs][128 x 128]
+  int *err;
+  double *dsc;             // scalars: 0..2 core stats, 4..5 energy
+  int *frozen;             // non-zero: converged, every batched kernel skips it
+  int n_row_items;         // row items of this problem (CG partial rows)
+  int n_gram_splits;
+  int gram_jobs;
+};
+struct RowItem {
+  int prob, local;         // problem, index of this item among the problem's items
+  long long r0, r1;        // grid points [r0, r1)
+};
+struct GramItem {
+  int prob, job, split;
+  long long r0, r1;
+};
+struct TileItem {
+  int prob;
+  long long m0;            // first grid point of a 128-point tile
+  int n0;                  // first output column
+};
+
+// Batched launchers (grid = item count; problems by blockIdx where noted).
+op_status launch_b_cg_init(const BatchProb *B, const RowItem *items, int nitems, int parity,
+                           cudaStream_t st);
+op_status launch_b_fin_init(const BatchProb *B, int nprob, int max_ld, cudaStream_t st);
+op_status launch_b_cg_iter(const BatchProb *B, const RowItem *items, int nitems, int nprob,
+                           int max_ld, int k, cudaStream_t st);
+op_status launch_b_energy(const BatchProb *B, const RowItem *items, int nitems, int nprob,
+                          int max_ld, int parity, cudaStream_t st);
+op_status launch_b_gram(const BatchProb *B, const GramItem *items, int nitems, int nprob,
+                        int parity, cudaStream_t st);
+size_t gram_tc_tile_bytes();      // bytes of one 128 x 128 FP64 partial tile
+int gram_tc_jobs_all(int ld);     // tensor-core Gram jobs for C, S and D
+op_status launch_b_core(const BatchProb *B, int nprob, int max_ld, cudaStream_t st);
+op_status launch_b_update(const BatchProb *B, const TileItem *items, int nitems, int nprob,
+                          int max_ld, int parity, cudaStream_t st);
+
 // ---- stencil and Step-1 CG (stencil_cg.cu) --------------------------------
 // Vt: n values of V in T; the diagonal of H + sigma is Vt_i + cdiag + sigma.
 // Y = (H + sigma) X.

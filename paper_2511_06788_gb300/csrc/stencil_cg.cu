@@ -672,6 +672,311 @@ op_status launch_unpad_copy(long long n, int p, int ld, const T *src, double *ds
   return OP_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched kernels (FP32 blocks): one CTA per RowItem (problem, grid-point range).
+// A CTA of 256 threads covers nv = ld/4 float4 vectors of 256/nv points per pass.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct FlatMap {
+  int nv, rows, tx, ty;
+  bool active;
+};
+__device__ __forceinline__ FlatMap flat_map(int ld) {
+  FlatMap m;
+  m.nv = ld >> 2;
+  m.rows = 256 / m.nv;
+  m.tx = threadIdx.x % m.nv;
+  m.ty = threadIdx.x / m.nv;
+  m.active = m.ty < m.rows;
+  return m;
+}
+
+// Sum the per-thread partials acc[c][k] (column tx*4 + k) over the rows of the
+// CTA into dst[c][ld] (FP64, fixed order).
+template <int NCOMP>
+__device__ __forceinline__ void flat_colsum(const float (&acc)[NCOMP][4], const FlatMap &m, int ld,
+                                            double *__restrict__ dst) {
+  __shared__ double red[256 * NCOMP * 4];
+  const int width = NCOMP * ld;
+  if (m.active) {
+#pragma unroll
+    for (int c = 0; c < NCOMP; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[m.ty * width + c * ld + m.tx * 4 + k] = (double)acc[c][k];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < width; e += blockDim.x) {
+    double s = 0.0;
+    for (int y = 0; y < m.rows; ++y) s += red[y * width + e];
+    dst[e] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_b_cg_init(const BatchProb *__restrict__ B,
+                                                   const RowItem *__restrict__ items, int parity) {
+  const RowItem it = items[blockIdx.x];
+  const BatchProb &pb = B[it.prob];
+  if (*pb.frozen) return;
+  const int ld = pb.ld;
+  const FlatMap m = flat_map(ld);
+  if (it.local == 0 && threadIdx.x == 0) {
+    pb.ctl[1] = 0;
+    pb.ctl[2] = 0;
+  }
+  const float *U = pb.U[parity];
+  float acc[2][4] = {};
+  if (m.active) {
+    const int col = m.tx * 4;
+    for (long long i = it.r0 + m.ty; i < it.r1; i += m.rows) {
+      const Pack<float> aw = stencil_at(pb.g, pb.Vt, pb.shift, pb.W, ld, i, col, (Pack<float> *)nullptr);
+      const long long o = i * (long long)ld + col;
+      const Pack<float> u = Pack<float>::load(U + o);
+      Pack<float> r;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        r.v[k] = u.v[k] - aw.v[k];
+        acc[0][k] += r.v[k] * r.v[k];
+        acc[1][k] += u.v[k] * u.v[k];
+      }
+      r.store(pb.R + o);
+    }
+  }
+  flat_colsum<2>(acc, m, ld, pb.part + (long long)it.local * 2 * ld);
+}
+
+// Finalisers: grid (column warps, problems).
+__global__ void k_b_fin_init(const BatchProb *__restrict__ B) {
+  const BatchProb &pb = B[blockIdx.y];
+  const int ld = pb.ld;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= ld || *pb.frozen) return;
+  const double rr = warp_sum_blocks(pb.part, pb.n_row_items, 2 * ld, j);
+  const double bb = warp_sum_blocks(pb.part, pb.n_row_items, 2 * ld, ld + j);
+  if ((threadIdx.x & 31) == 0) {
+    const double rtol2 = *pb.cg_rtol2;
+    double *state = pb.state;
+    state[0 * ld + j] = rr;
+    state[1 * ld + j] = rtol2 * bb;
+    state[2 * ld + j] = 0.0;
+    state[3 * ld + j] = 0.0;
+    state[4 * ld + j] = bb;
+    const int a = (j < pb.p) && (rr > rtol2 * bb) && (bb > 0.0);
+    pb.active[j] = a;
+    if (a) atomicAdd(&pb.ctl[1], 1);
+  }
+}
+
+template <bool FIRST>
+__global__ void __launch_bounds__(256) k_b_cg_p(const BatchProb *__restrict__ B,
+                                                const RowItem *__restrict__ items, int k) {
+  const RowItem it = items[blockIdx.x];
+  const BatchProb &pb = B[it.prob];
+  if (*pb.frozen || pb.ctl[(k + 1) & 1] == 0) return;
+  const int ld = pb.ld;
+  const FlatMap m = flat_map(ld);
+  const float *R = pb.R;
+  const float *Po = (k & 1) ? pb.Q : pb.P;
+  float *Pn = (k & 1) ? pb.P : pb.Q;
+  const Geom &g = pb.g;
+  float acc[1][4] = {};
+  if (m.active) {
+    const int col = m.tx * 4;
+    float b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = FIRST ? 0.f : (float)pb.state[3 * ld + col + q];
+    const long long sty = (long long)g.nx * ld, stz = (long long)g.nx * g.ny * ld;
+    for (long long i = it.r0 + m.ty; i < it.r1; i += m.rows) {
+      const long long base = i * (long long)ld + col;
+      const Coord c = coord_of(g, i);
+      const Pack<float> pc = dir_at<float, FIRST>(R, Po, b, base);
+      Pack<float> sx = Pack<float>::zero(), sy = Pack<float>::zero(), sz = Pack<float>::zero();
+      if (c.ix > 0) add_pack(sx, dir_at<float, FIRST>(R, Po, b, base - ld));
+      if (c.ix < g.nx - 1) add_pack(sx, dir_at<float, FIRST>(R, Po, b, base + ld));
+      if (c.iy > 0) add_pack(sy, dir_at<float, FIRST>(R, Po, b, base - sty));
+      if (c.iy < g.ny - 1) add_pack(sy, dir_at<float, FIRST>(R, Po, b, base + sty));
+      if (g.dim == 3) {
+        if (c.iz > 0) add_pack(sz, dir_at<float, FIRST>(R, Po, b, base - stz));
+        if (c.iz < g.nz - 1) add_pack(sz, dir_at<float, FIRST>(R, Po, b, base + stz));
+      }
+      const Pack<float> q = combine(g, __ldg(pb.Vt + i) + pb.shift, pc, sx, sy, sz);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[0][e] += pc.v[e] * q.v[e];
+      pc.store(Pn + base);
+    }
+  }
+  flat_colsum<1>(acc, m, ld, pb.part + (long long)it.local * ld);
+}
+
+__global__ void k_b_fin_alpha(const BatchProb *__restrict__ B, int k) {
+  const BatchProb &pb = B[blockIdx.y];
+  if (blockIdx.x == 0 && threadIdx.x == 0) pb.ctl[k & 1] = 0;
+  if (*pb.frozen || pb.ctl[(k + 1) & 1] == 0) return;
+  const int ld = pb.ld;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= ld) return;
+  const double pq = warp_sum_blocks(pb.part, pb.n_row_items, ld, j);
+  if ((threadIdx.x & 31) == 0) {
+    const double rr = pb.state[j];
+    pb.state[2 * ld + j] = (pb.active[j] && pq > 0.0) ? rr / pq : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_b_cg_wr(const BatchProb *__restrict__ B,
+                                                 const RowItem *__restrict__ items, int k) {
+  const RowItem it = items[blockIdx.x];
+  const BatchProb &pb = B[it.prob];
+  if (*pb.frozen || pb.ctl[(k + 1) & 1] == 0) return;
+  const int ld = pb.ld;
+  const FlatMap m = flat_map(ld);
+  const float *Pn = (k & 1) ? pb.P : pb.Q;
+  float acc[1][4] = {};
+  if (m.active) {
+    const int col = m.tx * 4;
+    float a[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[q] = (float)pb.state[2 * ld + col + q];
+    for (long long i = it.r0 + m.ty; i < it.r1; i += m.rows) {
+      Pack<float> pc;
+      const Pack<float> q = stencil_at(pb.g, pb.Vt, pb.shift, Pn, ld, i, col, &pc);
+      const long long o = i * (long long)ld + col;
+      Pack<float> w = Pack<float>::load_rw(pb.W + o), r = Pack<float>::load_rw(pb.R + o);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        w.v[e] += a[e] * pc.v[e];
+        r.v[e] -= a[e] * q.v[e];
+        acc[0][e] += r.v[e] * r.v[e];
+      }
+      w.store(pb.W + o);
+      r.store(pb.R + o);
+    }
+  }
+  flat_colsum<1>(acc, m, ld, pb.part + (long long)it.local * ld);
+}
+
+__global__ void k_b_fin_beta(const BatchProb *__restrict__ B, int k) {
+  const BatchProb &pb = B[blockIdx.y];
+  if (*pb.frozen || pb.ctl[(k + 1) & 1] == 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) pb.ctl[2] += 1;
+  const int ld = pb.ld;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= ld) return;
+  const double rrn = warp_sum_blocks(pb.part, pb.n_row_items, ld, j);
+  if ((threadIdx.x & 31) == 0) {
+    double *state = pb.state;
+    const double rr = state[j];
+    int a = pb.active[j];
+    state[3 * ld + j] = (a && rr > 0.0) ? rrn / rr : 0.0;
+    if (a) {
+      state[j] = rrn;
+      a = rrn > state[ld + j];
+      pb.active[j] = a;
+    }
+    if (a) atomicAdd(&pb.ctl[k & 1], 1);
+  }
+}
+
+// Energy of the new U: part[item][0][j] = u_j . (H u)_j, part[item][1][j] = u_j . u_j.
+__global__ void __launch_bounds__(256) k_b_quad(const BatchProb *__restrict__ B,
+                                                const RowItem *__restrict__ items, int parity) {
+  const RowItem it = items[blockIdx.x];
+  const BatchProb &pb = B[it.prob];
+  if (*pb.frozen) return;
+  const int ld = pb.ld;
+  const FlatMap m = flat_map(ld);
+  const float *X = pb.U[parity];
+  const float shift0 = (float)pb.g.cdiag;  // unshifted H
+  float acc[2][4] = {};
+  if (m.active) {
+    const int col = m.tx * 4;
+    for (long long i = it.r0 + m.ty; i < it.r1; i += m.rows) {
+      Pack<float> xc;
+      const Pack<float> y = stencil_at(pb.g, pb.Vt, shift0, X, ld, i, col, &xc);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        acc[0][e] += xc.v[e] * y.v[e];
+        acc[1][e] += xc.v[e] * xc.v[e];
+      }
+    }
+  }
+  flat_colsum<2>(acc, m, ld, pb.part + (long long)it.local * 2 * ld);
+}
+
+// dsc[4] = sum_j sum_items part[.][0][j], dsc[5] likewise for component 1 (one CTA per problem).
+__global__ void k_b_fin_energy(const BatchProb *__restrict__ B) {
+  const BatchProb &pb = B[blockIdx.x];
+  if (*pb.frozen) return;
+  const int ld = pb.ld;
+  __shared__ double sh[2][256];
+  double s0 = 0.0, s1 = 0.0;
+  for (int j = threadIdx.x; j < ld; j += blockDim.x)
+    for (int b = 0; b < pb.n_row_items; ++b) {
+      s0 += pb.part[((long long)b * 2 + 0) * ld + j];
+      s1 += pb.part[((long long)b * 2 + 1) * ld + j];
+    }
+  sh[0][threadIdx.x] = s0;
+  sh[1][threadIdx.x] = s1;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pb.dsc[4] = sh[0][0];
+    pb.dsc[5] = sh[1][0];
+  }
+}
+
+}  // namespace
+
+op_status launch_b_cg_init(const BatchProb *B, const RowItem *items, int nitems, int parity,
+                           cudaStream_t st) {
+  k_b_cg_init<<<nitems, 256, 0, st>>>(B, items, parity);
+  count_launch();
+  OP_LAUNCH("k_b_cg_init");
+  return OP_OK;
+}
+
+op_status launch_b_fin_init(const BatchProb *B, int nprob, int max_ld, cudaStream_t st) {
+  k_b_fin_init<<<dim3(warp_blocks(max_ld), nprob), 256, 0, st>>>(B);
+  count_launch();
+  OP_LAUNCH("k_b_fin_init");
+  return OP_OK;
+}
+
+op_status launch_b_cg_iter(const BatchProb *B, const RowItem *items, int nitems, int nprob,
+                           int max_ld, int k, cudaStream_t st) {
+  const dim3 fg(warp_blocks(max_ld), nprob);
+  if (k == 0)
+    k_b_cg_p<true><<<nitems, 256, 0, st>>>(B, items, k);
+  else
+    k_b_cg_p<false><<<nitems, 256, 0, st>>>(B, items, k);
+  count_launch();
+  k_b_fin_alpha<<<fg, 256, 0, st>>>(B, k);
+  count_launch();
+  k_b_cg_wr<<<nitems, 256, 0, st>>>(B, items, k);
+  count_launch();
+  k_b_fin_beta<<<fg, 256, 0, st>>>(B, k);
+  count_launch();
+  OP_LAUNCH("batched cg iteration");
+  return OP_OK;
+}
+
+op_status launch_b_energy(const BatchProb *B, const RowItem *items, int nitems, int nprob,
+                          int max_ld, int parity, cudaStream_t st) {
+  (void)max_ld;
+  k_b_quad<<<nitems, 256, 0, st>>>(B, items, parity);
+  count_launch();
+  k_b_fin_energy<<<nprob, 256, 0, st>>>(B);
+  count_launch();
+  OP_LAUNCH("batched energy");
+  return OP_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Event profiler
 // ---------------------------------------------------------------------------

@@ -35,18 +35,19 @@ constexpr int kStages = 2;
 constexpr int kSmem = kStages * kStage + 1024;
 constexpr uint32_t kIdesc = tc::idesc_tf32(kTM, kTN);
 
-__global__ void __launch_bounds__(256, 1)
-    k_update_tc(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
-                const float *__restrict__ KT_hi, const float *__restrict__ KT_lo,
-                float *__restrict__ Unew, int *err, int split) {
+// One CTA: output tile rows [m0, m0 + 128) x columns [n0, n0 + 128) of Unew.
+__device__ __forceinline__ void update_tc_body(long long n, int ld, const float *__restrict__ U,
+                                               const float *__restrict__ W,
+                                               const float *__restrict__ KT_hi,
+                                               const float *__restrict__ KT_lo,
+                                               float *__restrict__ Unew, long long m0, int n0,
+                                               int *err, int split) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar[2];  // one per TMEM accumulator
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
-  const long long m0 = (long long)blockIdx.x * kTM;
-  const int n0 = blockIdx.y * kTN;
   const int K = 2 * ld;
   const int nslab = (K + kKS - 1) / kKS;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -177,6 +178,41 @@ __global__ void __launch_bounds__(256, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, 2 * kTN);
 }
 
+__global__ void __launch_bounds__(256, 1)
+    k_update_tc(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
+                const float *__restrict__ KT_hi, const float *__restrict__ KT_lo,
+                float *__restrict__ Unew, int *err, int split) {
+  update_tc_body(n, ld, U, W, KT_hi, KT_lo, Unew, (long long)blockIdx.x * kTM, blockIdx.y * kTN,
+                 err, split);
+}
+
+// Batched: one CTA per TileItem (problem, 128-point tile, column tile); U -> U+.
+__global__ void __launch_bounds__(256, 1)
+    k_b_update_tc(const BatchProb *__restrict__ B, const TileItem *__restrict__ items, int parity) {
+  const TileItem it = items[blockIdx.x];
+  const BatchProb &pb = B[it.prob];
+  if (*pb.frozen) return;
+  update_tc_body(pb.g.n, pb.ld, pb.U[parity], pb.W, pb.KT_hi, pb.KT_lo, pb.U[parity ^ 1], it.m0,
+                 it.n0, pb.err, 1);
+}
+
+// Batched KT = [KU - I; KW]^T split (grid: element blocks x problems).
+__global__ void k_b_make_kt(const BatchProb *__restrict__ B) {
+  const BatchProb &pb = B[blockIdx.y];
+  if (*pb.frozen) return;
+  const int ld = pb.ld, K = 2 * ld;
+  const long long total = (long long)ld * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int nn = (int)(e / K), k = (int)(e % K);
+    const double v = (k < ld) ? pb.KU[(long long)k * ld + nn] - (k == nn ? 1.0 : 0.0)
+                              : pb.KW[(long long)(k - ld) * ld + nn];
+    const float hi = tc::to_tf32((float)v);
+    pb.KT_hi[e] = hi;
+    pb.KT_lo[e] = tc::to_tf32((float)(v - (double)hi));
+  }
+}
+
 // KT = [KU - I; KW]^T (ld x 2 ld, K-major rows) split into TF32 hi / lo parts
 // (the identity is added back by the epilogue of k_update_tc).
 template <typename S>
@@ -196,6 +232,17 @@ __global__ void k_make_kt(int ld, const S *__restrict__ KU, const S *__restrict_
 }
 
 }  // namespace
+
+op_status launch_b_update(const BatchProb *B, const TileItem *items, int nitems, int nprob,
+                          int max_ld, int parity, cudaStream_t st) {
+  k_b_make_kt<<<dim3((2 * max_ld * max_ld + 255) / 256, nprob), 256, 0, st>>>(B);
+  count_launch();
+  OP_CUDA(cudaFuncSetAttribute(k_b_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  k_b_update_tc<<<nitems, 256, kSmem, st>>>(B, items, parity);
+  count_launch();
+  OP_LAUNCH("k_b_update_tc");
+  return OP_OK;
+}
 
 op_status launch_make_kt(int ld, const double *KU, const double *KW, float *KT_hi, float *KT_lo,
                          cudaStream_t st) {
