@@ -34,22 +34,52 @@ WORKLOAD = "3d_wells_64^3_p128"
 METRIC = "n*p orbital-updates/s"
 UNIT = "orbital-updates/s"
 
-# Algorithmic bytes per launch of each timed kernel group, per unit n (grid points),
-# for element size s and row width p (blocks are n x p; V is n values).
+# Algorithmic bytes per launch of each timed kernel group, for n grid points, row
+# width p and element size s (blocks are n x p; V is n values).  FP32 runs the
+# two-kernel CG iteration (direction kernel k_cg_tma / k_cg_p: read R, P_old, V,
+# write P_new, P_old absent on a solve's first iteration; update kernel k_cg_wr:
+# read P_new, W, R, V, write W, R); FP64 the three-kernel one.
 ALGO_BYTES = {
-    "cg_apply": lambda n, p, s: n * s * (2 * p + 1),   # read P, V; write Q
-    "cg_axpy": lambda n, p, s: n * s * 6 * p,          # read W, R, P, Q; write W, R
-    "cg_dir": lambda n, p, s: n * s * 3 * p,           # read R, P; write P
-    "cg_init": lambda n, p, s: n * s * (4 * p + 1),    # read U, W, V; write R, P
-    "gram": lambda n, p, s: n * s * 2 * p,             # read U, W
-    "update": lambda n, p, s: n * s * 3 * p,           # read U, W; write U+
-    "energy": lambda n, p, s: n * s * (p + 1),         # read U, V
+    "fp64": {
+        "cg_apply": lambda n, p, s: n * s * (2 * p + 1),   # k_cg_apply: read P, V; write Q
+        "cg_axpy": lambda n, p, s: n * s * 6 * p,          # k_cg_axpy: read W, R, P, Q; write W, R
+        "cg_dir": lambda n, p, s: n * s * 3 * p,           # k_cg_dir: read R, P; write P
+        "cg_init": lambda n, p, s: n * s * (4 * p + 1),    # read U, W, V; write R, P
+    },
+    "fp32": {
+        "cg_apply": lambda n, p, s: n * s * (3 * p + 1),   # k_cg_tma (not first iteration)
+        "cg_axpy": lambda n, p, s: n * s * (5 * p + 1),    # k_cg_wr
+        "cg_init": lambda n, p, s: n * s * (3 * p + 1),    # read U, W, V; write R
+    },
+    "any": {
+        "gram": lambda n, p, s: n * s * 2 * p,             # read U, W
+        "update": lambda n, p, s: n * s * 3 * p,           # read U, W; write U+
+        "energy": lambda n, p, s: n * s * (p + 1),         # read U, V
+    },
 }
+KERNEL_NAME = {("cg_apply", "fp32"): "k_cg_tma", ("cg_axpy", "fp32"): "k_cg_wr",
+               ("cg_apply", "fp64"): "k_cg_apply", ("cg_axpy", "fp64"): "k_cg_axpy",
+               ("cg_dir", "fp64"): "k_cg_dir", ("gram", "fp32"): "k_gram_tc",
+               ("update", "fp32"): "k_update_tc"}
+
+
+def algo_bytes(group, prec, n, p, s, launches, solves):
+    """Average algorithmic bytes per launch of a kernel group over the timed region."""
+    table = dict(ALGO_BYTES["any"], **ALGO_BYTES["fp64" if prec == "fp64" else "fp32"])
+    b = table[group](n, p, s)
+    if group == "cg_apply" and prec != "fp64" and launches > 0:
+        # the first iteration of each solve reads no P_old
+        b -= n * s * p * min(solves, launches) / launches
+    return b
+
 
 # DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # at this workload, keyed by kernel group and precision, valid for the kernel source
 # with the given SHA-1 prefix; null in the JSON line when the source has changed.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("cg_axpy", "fp32"): (619270656, "e77393e9f73a"),   # k_cg_wr, stencil_cg.cu
+    ("cg_apply", "fp32"): (371437056, "147e6cde8380"),  # k_cg_tma, stencil_tma.cu
+}
 
 
 def _sha(path):
@@ -57,9 +87,15 @@ def _sha(path):
         return hashlib.sha1(f.read()).hexdigest()[:12]
 
 
-def kernel_source_sha(group):
-    src = "stencil_cg.cu" if group.startswith("cg_") or group == "energy" else (
-        "gram.cu" if group == "gram" else "update.cu")
+def kernel_source_sha(group, prec):
+    if group == "cg_apply" and prec != "fp64":
+        src = "stencil_tma.cu"
+    elif group.startswith("cg_") or group == "energy":
+        src = "stencil_cg.cu"
+    elif group == "gram":
+        src = "gram.cu" if prec == "fp64" else "gram_tc.cu"
+    else:
+        src = "update.cu" if prec == "fp64" else "update_tc.cu"
     return _sha(os.path.join(ROOT, "paper_2511_06788_gb300", "csrc", src))
 
 
@@ -245,17 +281,19 @@ def run_ours(args):
 
     # roofline of the dominant kernel group (most device time in the timed region)
     hbm, _, peak_kind = load_peaks()
-    groups = {k: v for k, v in prof.items() if k in ALGO_BYTES and v[1] > 0}
+    known = set(ALGO_BYTES["any"]) | set(ALGO_BYTES["fp64" if args.prec == "fp64" else "fp32"])
+    groups = {k: v for k, v in prof.items() if k in known and v[1] > 0}
     dom = max(groups, key=lambda k: groups[k][0])
     tot_ms, cnt = groups[dom]
     avg_s = tot_ms * 1e-3 / cnt
-    algo = ALGO_BYTES[dom](n, p, s_el)
+    algo = algo_bytes(dom, args.prec, n, p, s_el, cnt, args.steps)
     achieved = algo / avg_s / 1e9
     traffic = None
     key = (dom, args.prec)
-    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_source_sha(dom):
+    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_source_sha(dom, args.prec):
         traffic = NCU_TRAFFIC[key][0]
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAME.get((dom, args.prec), dom),
+                "group": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
                 "algo_bytes_per_launch": algo, "avg_launch_ms": 1e3 * avg_s,
                 "share_of_step_time": tot_ms / ms}

@@ -2,6 +2,8 @@
 // on `st` and returns OP_OK or the launch error; buffers are device pointers.
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace opevo {
@@ -125,8 +127,9 @@ struct CGWork {
   double *part;          // CTA partials [max_blocks][2][ld] + per-column sums [2][ld]
   double *state;         // [6][ld]: rr, target, alpha, beta, bnorm2, scratch
   int *active;           // [ld]
-  int *ctl;              // [4] device: active counts (two parities), iterations done
-  int *host_ctl;         // >= 3 ints of host memory (pinned for the context)
+  int *ctl;              // [4] device: active counts (two parities), iterations done,
+                         // error flag (a bounded wait of a TMA kernel gave up)
+  int *host_ctl;         // >= 4 ints of host memory (pinned for the context)
   int max_blocks;
   int expect_iters = 0;  // iterations of the previous solve (first chunk length)
   Prof *prof = nullptr;  // optional timing
@@ -139,6 +142,29 @@ void cg_carve(void *ws, long long n, int ld, int elem, CGWork *w);
 template <typename T>
 op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, int p, int ld,
                    double rtol, int max_iter, CGWork &w, int *iters, cudaStream_t st);
+
+// FP32 CG direction kernel on 3-D grids with TMA-staged stencil planes (stencil_tma.cu).
+struct CgTmaGeom {
+  int nx, ny, nz, ld;
+  int ntx, nty, nch;   // 8 x 8 tiles in x and y; 32-column chunks
+  int slabs;           // z slabs per column (columns = nch * ntx * nty)
+  long long items;     // slabs * columns
+  float shift;         // cdiag + sigma
+  float cx, cy, cz;    // off-diagonal stencil weights
+};
+struct CgTmaPlan {
+  CgTmaGeom tg;
+  CUtensorMap halo[3];  // 10 x 10 x 32 boxes of R, P, Q
+  int grid;             // persistent CTAs (rows of the partials buffer)
+};
+// Grids and blocks the TMA kernel handles (3-D, >= 32 columns, 16-byte aligned blocks).
+bool cg_tma_eligible(const Geom &g, int ld, const void *R, const void *P, const void *Q);
+op_status cg_tma_prepare(const Geom &g, double sigma, int ld, const float *R, const float *P,
+                         const float *Q, CgTmaPlan *plan);
+// Pn = R (first) or R + beta Po, Po = P (po 0) or Q (po 1); part[grid][ld] = Pn . A Pn.
+op_status cg_tma_p(const CgTmaPlan &plan, bool first, int po, float *Pn, const float *Vt,
+                   const double *beta, const int *nact_prev, double *part, int *err,
+                   cudaStream_t st);
 
 // Copy an n x p FP64 block into an n x ld block of T (zero padding).
 template <typename T>

@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(256) k_cg_init(Geom g, const T *__restrict__ V
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
     ctl[1] = 0;
     ctl[2] = 0;
+    ctl[3] = 0;
   }
   T acc[2][N] = {};
   for (long long i = i0; i < g.n; i += istep) {
@@ -572,6 +573,19 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
   double *alpha = w.state + 2 * ld, *beta = w.state + 3 * ld;
   int *ctl = w.ctl;
   const T sg = (T)(g.cdiag + sigma);
+  // FP32 on 3-D grids: the direction update and its stencil by the TMA plane-marching
+  // kernel (its own persistent grid); the W/R update stays an L2-served row kernel,
+  // which measured faster (its many independent loads hide latency better)
+  CgTmaPlan plan;
+  bool tma = false;
+  int nb_p = nb;
+  if constexpr (kFused) {
+    tma = cg_tma_eligible(g, ld, R, P, Q);
+    if (tma) {
+      OP_TRY(cg_tma_prepare(g, sigma, ld, R, P, Q, &plan));
+      nb_p = plan.grid;
+    }
+  }
 
   prof_begin(w.prof, PK_CG_INIT, st);
   if (kFused)
@@ -596,14 +610,22 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
       if (kFused) {
         T *Po = (k & 1) ? Q : P, *Pn = (k & 1) ? P : Q;
         prof_begin(w.prof, PK_CG_APPLY, st);
-        if (k == 0)
-          k_cg_p<T, true><<<grid, s.block, 0, st>>>(g, Vt, sg, R, Po, Pn, ld, beta, nprev, w.part);
-        else
-          k_cg_p<T, false><<<grid, s.block, 0, st>>>(g, Vt, sg, R, Po, Pn, ld, beta, nprev, w.part);
-        count_launch();
+        if (tma) {
+          if constexpr (kFused)
+            OP_TRY(cg_tma_p(plan, k == 0, (k & 1) ? 1 : 0, Pn, Vt, beta, nprev, w.part, ctl + 3,
+                            st));
+        } else {
+          if (k == 0)
+            k_cg_p<T, true><<<grid, s.block, 0, st>>>(g, Vt, sg, R, Po, Pn, ld, beta, nprev,
+                                                      w.part);
+          else
+            k_cg_p<T, false><<<grid, s.block, 0, st>>>(g, Vt, sg, R, Po, Pn, ld, beta, nprev,
+                                                       w.part);
+          count_launch();
+        }
         prof_end(w.prof, st);
         prof_begin(w.prof, PK_CG_FIN, st);
-        k_cg_fin_alpha<<<fb, 256, 0, st>>>(w.part, nb, ld, w.state, w.active, nprev, nnext);
+        k_cg_fin_alpha<<<fb, 256, 0, st>>>(w.part, nb_p, ld, w.state, w.active, nprev, nnext);
         count_launch();
         prof_end(w.prof, st);
         prof_begin(w.prof, PK_CG_AXPY, st);
@@ -641,9 +663,13 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
     }
     OP_LAUNCH("cg iteration");
     launched = upto;
-    OP_CUDA(cudaMemcpyAsync(w.host_ctl, ctl, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    OP_CUDA(cudaMemcpyAsync(w.host_ctl, ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     OP_CUDA(cudaStreamSynchronize(st));
     prof_harvest(w.prof);
+    if (w.host_ctl[3]) {
+      set_error("a CG kernel gave up a bounded wait for its TMA copies");
+      return OP_ERR_TIMEOUT;
+    }
     done = w.host_ctl[2];
     // converged: no active column after the last queued iteration (or the solve
     // stopped inside the chunk)

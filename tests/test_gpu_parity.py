@@ -227,6 +227,48 @@ def test_cg_solve_matches_oracle(prec):
     assert np.all(W[:, p:] == 0)
 
 
+# 3-D grids with >= 32 columns run the TMA plane-marching CG kernels: ragged
+# x/y tiles, a ragged 32-column chunk, the thinnest z extent they accept.
+TMA_GEOMS = [((13, 9, 11), 40), ((16, 16, 16), 64), ((9, 8, 3), 33), ((20, 22, 18), 96)]
+
+
+@pytest.mark.parametrize("geom", TMA_GEOMS, ids=lambda g: "x".join(map(str, g[0])) + f"_p{g[1]}")
+def test_cg_plane_marching_iterates_match_oracle(geom):
+    """W after k CG iterations (warm start) equals the oracle's block CG after k iterations."""
+    shape, p = geom
+    lo, hi = (-4.0,) * 3, (4.0,) * 3
+    n = int(np.prod(shape))
+    V = rounded(random_potential(shape, lo, hi, 5), "fp32")
+    sigma = o.default_sigma(shape, lo, hi, V)
+    U = rounded(o.householder_orthonormalize(syn.gaussian_block(6, n, p)), "fp32")
+    W0 = rounded(0.05 * syn.gaussian_block(7, n, p), "fp32")
+    A = (o.hamiltonian(shape, lo, hi, V) + sigma * sp_identity(n)).tocsr()
+    ld = ld_of(p)
+    Vt = torch.from_numpy(V).to(DEV, torch.float32)
+    Ut = padded(U, ld, torch.float32)
+    for k in (1, 2, 5):
+        Wt = padded(W0, ld, torch.float32)
+        it = pkg.cg_solve(shape, lo, hi, Vt, sigma, Ut, Wt, p, 1e-30, max_iter=k)
+        assert it == k
+        W = Wt.double().cpu().numpy()
+        W_ref, _ = o.block_cg(A, U, W0, rtol=0.0, max_iter=k)
+        err = np.abs(W[:, :p] - W_ref).max() / np.abs(W_ref).max()
+        assert err < 2e-5, (k, err)
+        assert np.all(W[:, p:] == 0)
+    # and to convergence
+    Wt = padded(W0, ld, torch.float32)
+    it = pkg.cg_solve(shape, lo, hi, Vt, sigma, Ut, Wt, p, 1e-6)
+    W_exact = o.SourceSolver(o.hamiltonian(shape, lo, hi, V), sigma).solve(U)
+    lam_min = o.spectrum_lower_bound(shape, lo, hi, V) + sigma
+    err = np.linalg.norm(Wt.double().cpu().numpy()[:, :p] - W_exact, axis=0)
+    assert 0 < it < 5000 and np.all(err <= 30 * 1e-6 / lam_min)
+
+
+def sp_identity(n):
+    import scipy.sparse as sp
+    return sp.identity(n, format="csr")
+
+
 # ----------------------------------------------------------------------------
 # Whole-step and whole-solve parity through the context API
 # ----------------------------------------------------------------------------
