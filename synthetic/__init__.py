@@ -35,6 +35,8 @@ _STREAM_MUL = np.uint64(0xD1B54A32D192ED03)
 STREAM_U0 = 1
 STREAM_WELLS = 2
 STREAM_BATCH = 3
+STREAM_LEARN = 4
+STREAM_INIT = 5
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -193,4 +195,35 @@ def batch_problems(seed: int, count: int = 64, nmin: int = 24, nmax: int = 48,
         p = pmin + int(r[1] * (pmax - pmin + 1))
         k = wmin + int(r[2] * (wmax - wmin + 1))
         out.append(wells_3d(N, p, k, seed * 1000 + i))
+    return out
+
+
+def warm_start_problem(seed: int, N: int = 48, p: int = 64, box: float = 8.0,
+                       wells=(4, 16), depth=(1.0, 6.0), width=(0.5, 1.5)) -> Problem:
+    """Learned-warm-start workload: V = sum of U{4..16} Gaussian wells on [-box, box]^3,
+    depths U[1, 6], centres uniform in the box, no harmonic term; N^3 grid, p orbitals."""
+    u = uniform01(stream_key(seed, STREAM_LEARN), 0, 1)[0]
+    k = wells[0] + int(u * (wells[1] - wells[0] + 1))
+    shape = (N, N, N)
+    lo, hi = (-box,) * 3, (box,) * 3
+    w = draw_wells(seed, k, lo, hi, depth, width)
+    return Problem(shape, lo, hi, potential(shape, lo, hi, 0.0, w), p,
+                   f"warmstart_{N}^3_p{p}_w{k}_s{seed}", w)
+
+
+def uniform_init(seed: int, fans) -> np.ndarray:
+    """Initial parameters of a layered network as one flat FP32-ready vector.
+
+    ``fans`` lists, per layer in order, (fan_in, n_weights, n_bias).  Weights are
+    uniform on (-a, a) with a = sqrt(6 / fan_in) (variance 2 / fan_in, He et al.,
+    ICCV 2015); biases are zero.
+    """
+    total = sum(nw + nb for _, nw, nb in fans)
+    u = uniform01(stream_key(seed, STREAM_INIT), 0, total)
+    out = np.zeros(total)
+    off = 0
+    for fan_in, nw, nb in fans:
+        a = math.sqrt(6.0 / fan_in)
+        out[off:off + nw] = a * (2.0 * u[off:off + nw] - 1.0)
+        off += nw + nb
     return out
