@@ -155,6 +155,10 @@ op_status op_residual(op_ctx *ctx, double *r);
 /* Copy the current U (n x p, FP64, ld = p) into caller-owned host memory. Synchronises. */
 op_status op_get_U(op_ctx *ctx, double *U_host);
 
+/* Copy the current U into caller-owned device memory as an n x p block (ld = p) of
+ * FP64 (prec = OP_FP64) or FP32 (prec = OP_FP32).  Synchronises. */
+op_status op_get_U_device(op_ctx *ctx, void *U_dev, int prec);
+
 /* p eigenvalue estimates, ascending, into caller-owned host memory (kind: op_eig_kind).
  * OP_EIG_PAPER runs one extra Step-1 solve for the current U. Synchronises. */
 op_status op_eigenvalues(op_ctx *ctx, double *lam, int kind);

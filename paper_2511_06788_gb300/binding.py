@@ -44,6 +44,11 @@ class OpStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class OpnetConfig(C.Structure):
+    _fields_ = [("N", C.c_int), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("p", C.c_int),
+                ("width", C.c_int * 3), ("stream", C.c_void_p)]
+
+
 class OpError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -103,6 +108,17 @@ def lib():
         "op_update": (i32, [i32, C.c_longlong, i32, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
         "op_update_workspace": (sz, [i32, i32]),
         "op_ws_status": (i32, [vp, vp]),
+        "op_get_U_device": (i32, [vp, vp, i32]),
+        "opnet_create": (i32, [P(vp), P(OpnetConfig)]),
+        "opnet_param_count": (C.c_longlong, [vp]),
+        "opnet_layer": (i32, [vp, i32, P(i32), P(i32), P(i32)]),
+        "opnet_set_params": (i32, [vp, P(C.c_float), C.c_longlong]),
+        "opnet_get_params": (i32, [vp, P(C.c_float), C.c_longlong]),
+        "opnet_forward": (i32, [vp, vp, vp]),
+        "opnet_infer": (i32, [vp, vp, vp]),
+        "opnet_loss_grad": (i32, [vp, vp, vp, f64, P(f64), P(C.c_float), C.c_longlong]),
+        "opnet_train_step": (i32, [vp, vp, vp, f64, f64, f64, f64, f64, P(f64)]),
+        "opnet_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -231,6 +247,15 @@ class Solver:
         U = np.empty((self.n, self.p))
         check(lib().op_get_U(self._ctx, _dptr(U)))
         return U
+
+    def get_U_device(self, dtype=None):
+        """The current U as an n x p torch CUDA tensor (float64 or float32)."""
+        import torch
+        dtype = dtype or torch.float64
+        out = torch.empty(self.n, self.p, dtype=dtype, device="cuda")
+        check(lib().op_get_U_device(self._ctx, C.c_void_p(out.data_ptr()),
+                                    OP_FP64 if dtype == torch.float64 else OP_FP32))
+        return out
 
     def profile(self, enable=True):
         """Enable (and reset) or disable per-kernel event timing."""
@@ -422,3 +447,91 @@ def update(U, W, KU_t, KW_t, p, out=None, stream=None):
                           _tptr(out), _tptr(ws), nbytes, st))
     check(lib().op_ws_status(_tptr(ws), st))
     return out
+
+
+class Net:
+    """The learned warm start (include/opnet.h): a 3-level conv U-Net V -> Y (n x p).
+
+    V and targets are torch CUDA tensors (V: N^3 float64; Ustar: N^3 x p float32 with
+    orthonormal columns); parameters move as numpy float32 vectors."""
+
+    def __init__(self, N, lo, hi, p, widths=(24, 48, 96), stream=None):
+        cfg = OpnetConfig()
+        cfg.N = int(N)
+        for d in range(3):
+            cfg.lo[d] = float(lo[d])
+            cfg.hi[d] = float(hi[d])
+            cfg.width[d] = int(widths[d])
+        cfg.p = int(p)
+        cfg.stream = _stream_ptr(stream).value
+        self.N, self.p, self.n = int(N), int(p), int(N) ** 3
+        self._net = C.c_void_p()
+        check(lib().opnet_create(C.byref(self._net), C.byref(cfg)))
+        self.count = int(lib().opnet_param_count(self._net))
+
+    def close(self):
+        if self._net:
+            lib().opnet_destroy(self._net)
+            self._net = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def layers(self):
+        """[(taps, Cin, Cout)] of the 11 layers."""
+        out = []
+        for i in range(11):
+            t, ci, co = C.c_int(), C.c_int(), C.c_int()
+            check(lib().opnet_layer(self._net, i, C.byref(t), C.byref(ci), C.byref(co)))
+            out.append((t.value, ci.value, co.value))
+        return out
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        assert theta.size == self.count
+        check(lib().opnet_set_params(self._net, theta.ctypes.data_as(C.POINTER(C.c_float)),
+                                     self.count))
+
+    def get_params(self) -> np.ndarray:
+        theta = np.empty(self.count, dtype=np.float32)
+        check(lib().opnet_get_params(self._net, theta.ctypes.data_as(C.POINTER(C.c_float)),
+                                     self.count))
+        return theta
+
+    def forward(self, V):
+        import torch
+        Y = torch.empty(self.n, self.p, dtype=torch.float32, device=V.device)
+        check(lib().opnet_forward(self._net, C.c_void_p(V.data_ptr()), C.c_void_p(Y.data_ptr())))
+        return Y
+
+    def infer(self, V):
+        """The warm-start block (n x p float64 CUDA tensor) for Solver(..., device=True)."""
+        import torch
+        U0 = torch.empty(self.n, self.p, dtype=torch.float64, device=V.device)
+        check(lib().opnet_infer(self._net, C.c_void_p(V.data_ptr()), C.c_void_p(U0.data_ptr())))
+        return U0
+
+    def loss_grad(self, V, Ustar, gamma=0.1, grad=True):
+        loss = C.c_double()
+        g = np.empty(self.count, dtype=np.float32) if grad else None
+        check(lib().opnet_loss_grad(self._net, C.c_void_p(V.data_ptr()),
+                                    C.c_void_p(Ustar.data_ptr()), float(gamma), C.byref(loss),
+                                    g.ctypes.data_as(C.POINTER(C.c_float)) if grad else None,
+                                    self.count))
+        return loss.value, g
+
+    def train_step(self, V, Ustar, lr, gamma=0.1, beta1=0.9, beta2=0.999, eps=1e-8) -> float:
+        loss = C.c_double()
+        check(lib().opnet_train_step(self._net, C.c_void_p(V.data_ptr()),
+                                     C.c_void_p(Ustar.data_ptr()), float(gamma), float(lr),
+                                     float(beta1), float(beta2), float(eps), C.byref(loss)))
+        return loss.value

@@ -597,6 +597,17 @@ op_status op_get_U(op_ctx *c, double *U_host) {
   return OP_OK;
 }
 
+op_status op_get_U_device(op_ctx *c, void *U_dev, int prec) {
+  if (!c || !U_dev || (prec != OP_FP64 && prec != OP_FP32) || ((uintptr_t)U_dev & 15)) {
+    set_error("op_get_U_device: null or unaligned pointer, or prec not OP_FP64 / OP_FP32");
+    return OP_ERR_ARG;
+  }
+  OP_TRY(launch_unpad_to(c->n, c->p, c->ld, c->U, c->prec == OP_FP64 ? 8 : 4, U_dev,
+                         prec == OP_FP64 ? 8 : 4, c->st));
+  OP_CUDA(cudaStreamSynchronize(c->st));
+  return OP_OK;
+}
+
 op_status op_eigenvalues(op_ctx *c, double *lam, int kind) {
   if (!c || !lam || (kind != OP_EIG_RITZ && kind != OP_EIG_PAPER)) {
     set_error("op_eigenvalues: bad arguments");

@@ -166,6 +166,11 @@ op_status cg_tma_p(const CgTmaPlan &plan, bool first, int po, float *Pn, const f
                    const double *beta, const int *nact_prev, double *part, int *err,
                    cudaStream_t st);
 
+// Copy the first p columns of an n x ld block (elements of src_size bytes: 4 or 8)
+// into an n x p block of dst_size-byte elements (opnet.cu).
+op_status launch_unpad_to(long long n, int p, int ld, const void *src, int src_size, void *dst,
+                          int dst_size, cudaStream_t st);
+
 // Copy an n x p FP64 block into an n x ld block of T (zero padding).
 template <typename T>
 op_status launch_pad_copy(long long n, int p, int ld, const double *src, T *dst, cudaStream_t st);

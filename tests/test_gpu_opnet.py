@@ -1,0 +1,169 @@
+"""The learned warm start on the GPU (include/opnet.h) against the FP64 oracle.
+
+- the layer table and parameter layout equal the oracle's;
+- forward, loss and the full parameter gradient match oracle/unet.py on the same
+  FP32-rounded parameters;
+- one Adam step matches the oracle's Adam on the same gradient;
+- a network trained on blocks the scheme itself converged gives starting blocks
+  from which the scheme needs fewer steps than from random ones.
+
+Tolerances.  The network runs in FP32 with FP32 accumulation over at most
+27 x 144 products per output and FP32 sums over at most 2048 points per
+weight-gradient partial (partials summed in FP64).  Forward outputs agree to a
+few 1e-6 of their scale; gradients, which pass through up to 22 such layers,
+to 1e-4 relative per layer.
+"""
+import numpy as np
+import pytest
+
+from oracle import unet
+import synthetic as syn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2511_06788_gb300 as pkg  # noqa: E402
+
+DEV = torch.device("cuda:0")
+GAMMA = 0.1
+
+
+def setup(N, widths, p, seed=0):
+    table = unet.layer_table(*widths, p)
+    theta = syn.uniform_init(seed, unet.fans(table)).astype(np.float32).astype(np.float64)
+    P = syn.warm_start_problem(seed + 5, N=N, p=p)
+    net = pkg.Net(N, P.lo, P.hi, p, widths)
+    net.set_params(theta)
+    V = torch.from_numpy(P.V).to(DEV)
+    return net, theta, P, V
+
+
+def target(n, p, seed):
+    Q, _ = np.linalg.qr(syn.gaussian_block(seed, n, p))
+    return Q.astype(np.float32).astype(np.float64)
+
+
+def layer_slices(table):
+    off, out = 0, []
+    for _, t, ci, co in table:
+        size = t * ci * co + co
+        out.append(slice(off, off + size))
+        off += size
+    return out
+
+
+def test_layer_table_and_parameter_count_match_oracle():
+    with pkg.Net(48, (-8.0,) * 3, (8.0,) * 3, 64, (24, 48, 96)) as net:
+        table = unet.layer_table(24, 48, 96, 64)
+        assert net.layers() == [(t, ci, co) for _, t, ci, co in table]
+        assert net.count == sum(t * ci * co + co for _, t, ci, co in table) == 892720
+
+
+@pytest.mark.parametrize("N,widths,p", [(8, (6, 8, 10), 8), (16, (8, 16, 24), 16),
+                                        (12, (5, 7, 9), 8)])
+def test_forward_matches_oracle(N, widths, p):
+    net, theta, P, V = setup(N, widths, p)
+    Y = net.forward(V).double().cpu().numpy()
+    Y_ref, _ = unet.forward(theta, P.V, N, P.lo, P.hi, widths, p)
+    assert np.abs(Y - Y_ref).max() <= 5e-6 * np.abs(Y_ref).max()
+    U0 = net.infer(V).cpu().numpy()  # the FP64 warm-start block is the same Y
+    np.testing.assert_array_equal(U0, Y)
+    net.close()
+
+
+@pytest.mark.parametrize("N,widths,p", [(8, (6, 8, 10), 8), (16, (8, 16, 24), 16)])
+def test_loss_and_gradient_match_oracle(N, widths, p):
+    net, theta, P, V = setup(N, widths, p, seed=1)
+    Us = target(P.n, p, 3)
+    loss, g = net.loss_grad(V, torch.from_numpy(Us).to(DEV, torch.float32), GAMMA)
+    Y_ref, cache = unet.forward(theta, P.V, N, P.lo, P.hi, widths, p)
+    L_ref, dY = unet.subspace_loss(Y_ref, Us, GAMMA)
+    g_ref = unet.backward(cache, dY)
+    assert loss == pytest.approx(L_ref, rel=2e-5)
+    table = unet.layer_table(*widths, p)
+    for (name, *_), sl in zip(table, layer_slices(table)):
+        err = np.linalg.norm(g[sl] - g_ref[sl]) / np.linalg.norm(g_ref[sl])
+        assert err < 1e-4, (name, err)
+    net.close()
+
+
+def test_adam_step_matches_oracle_adam():
+    N, widths, p = 8, (6, 8, 10), 8
+    net, theta, P, V = setup(N, widths, p, seed=2)
+    Us = torch.from_numpy(target(P.n, p, 4)).to(DEV, torch.float32)
+    _, g = net.loss_grad(V, Us, GAMMA)
+    lr = 1e-3
+    net.train_step(V, Us, lr, GAMMA)
+    th1 = net.get_params().astype(np.float64)
+    ref, _, _ = unet.adam_step(theta, g.astype(np.float64), np.zeros_like(theta),
+                               np.zeros_like(theta), 1, lr)
+    assert np.abs(th1 - ref).max() <= 1e-6 * lr + 1e-7 * np.abs(theta).max()
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    N, widths, p = 8, (6, 8, 10), 8
+    net, theta, P, V = setup(N, widths, p, seed=3)
+    Us = torch.from_numpy(target(P.n, p, 5)).to(DEV, torch.float32)
+    losses = [net.train_step(V, Us, 3e-3, GAMMA) for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0]
+    net.close()
+
+
+def test_rejects_bad_configurations():
+    for N, p in [(10, 8), (8, 12), (0, 8), (8, 256)]:
+        with pytest.raises(pkg.OpError):
+            pkg.Net(N, (-1.0,) * 3, (1.0,) * 3, p, (4, 4, 4))
+
+
+# ----------------------------------------------------------------------------
+# What the trained network gains over random starting blocks
+# ----------------------------------------------------------------------------
+def converged_block(P, seed, tol=1e-4, cap=800):
+    """U* from the scheme itself (FP32 context; residual tol or cap steps) as FP32 CUDA."""
+    with pkg.Solver(P.shape, P.lo, P.hi, P.V, syn.gaussian_block(seed, P.n, P.p), P.p,
+                    prec="fp32") as s:
+        s.solve(tol, cap, raise_on_max=False)
+        return s.get_U_device(torch.float32)
+
+
+def start_and_steps(P, U0, device=False, tol=1e-10, cap=3000):
+    """E(U0) after orthonormalisation, and steps until Algorithm 1's relative energy
+    change drops below tol (capped)."""
+    V = torch.from_numpy(P.V).to(DEV) if device else P.V
+    with pkg.Solver(P.shape, P.lo, P.hi, V, U0, P.p, prec="fp32", device=device) as s:
+        E0 = s.stats()["energy"]
+        st = s.solve(tol, cap, pkg.OP_STOP_ERR_E, raise_on_max=False)
+        return E0, st["steps"]
+
+
+def test_trained_warm_start_beats_random_starts():
+    """Lower starting energy (the basin quantity of §3) and fewer steps to the err_E rule."""
+    N, p, widths = 16, 8, (8, 16, 24)
+    train_seeds, test_seeds = range(1000, 1024), range(5000, 5006)
+    data = []
+    for sd in train_seeds:
+        P = syn.warm_start_problem(sd, N=N, p=p)
+        data.append((torch.from_numpy(P.V).to(DEV), converged_block(P, sd)))
+    net = pkg.Net(N, (-8.0,) * 3, (8.0,) * 3, p, widths)
+    net.set_params(syn.uniform_init(7, unet.fans(unet.layer_table(*widths, p))))
+    first = last = None
+    for epoch in range(25):
+        tot = 0.0
+        for V, Us in data:
+            tot += net.train_step(V, Us, 2e-3, GAMMA)
+        first = tot if first is None else first
+        last = tot
+    assert last < 0.5 * first
+    rows = []
+    for sd in test_seeds:
+        P = syn.warm_start_problem(sd, N=N, p=p)
+        E_rand, n_rand = start_and_steps(P, syn.gaussian_block(sd, P.n, p))
+        E_net, n_net = start_and_steps(P, net.infer(torch.from_numpy(P.V).to(DEV)), device=True)
+        rows.append((E_rand, E_net, n_rand, n_net))
+    rows = np.array(rows)
+    assert np.all(rows[:, 1] < rows[:, 0]), rows          # every warm start has lower energy
+    assert rows[:, 3].mean() < rows[:, 2].mean(), rows    # and needs fewer steps on average
+    net.close()
