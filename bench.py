@@ -417,6 +417,121 @@ def run_batch(args):
     return 0
 
 
+def run_warmstart(args):
+    """Learned warm start on 48^3, p = 64 (V = 4-16 Gaussian wells, no harmonic term).
+
+    Training blocks come from the scheme itself (FP32 solves of training seeds); the
+    network is trained on the GPU by the library's own kernels; then, on held-out
+    seeds, the steps and time until Algorithm 1's relative energy change first falls
+    below 1e-4, 1e-6 and 1e-8 from the network's start (inference + Cholesky-QR +
+    plain FP32 scheme) are compared with random starts in FP32 and in plain FP64,
+    with the residual every 100 steps."""
+    import torch
+
+    import paper_2511_06788_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, p, widths, tol, cap = 48, 64, (24, 48, 96), args.ws_tol, args.ws_cap
+    box = ((-8.0,) * 3, (8.0,) * 3)
+
+    t0 = time.perf_counter()
+    data = []
+    for i in range(args.train_count):
+        sd = 100000 + 1000 * rank + i
+        P = syn.warm_start_problem(sd, N=N, p=p)
+        V = torch.from_numpy(P.V).to(dev)
+        U0 = torch.from_numpy(syn.gaussian_block(sd, P.n, p)).to(dev)
+        with pkg.Solver(P.shape, P.lo, P.hi, V, U0, p, prec="fp32", device=True) as s:
+            s.solve(1e-4, args.ws_target_cap, raise_on_max=False)
+            data.append((V, s.get_U_device(torch.float32)))
+    gen_s = time.perf_counter() - t0
+
+    net = pkg.Net(N, *box, p, widths)
+    nparams = net.count
+    net.set_params(syn.uniform_init(rank, [(t * ci, t * ci * co, co) for t, ci, co in net.layers()]))
+    t0 = time.perf_counter()
+    losses = []
+    for ep in range(args.epochs):
+        lr = args.lr * (0.5 ** (ep // max(1, args.epochs // 3)))
+        tot = sum(net.train_step(V, Us, lr, 0.1) for V, Us in data)
+        losses.append(tot / len(data))
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    del data
+
+    milestones = [1e-4, 1e-6, 1e-8]
+
+    def timed_solve(P, make_U0, prec, device):
+        """Step until err_E < 1e-8 (cap steps); record the step and the time at which
+        err_E first fell below each milestone, and the residual every 100 steps."""
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        V = torch.from_numpy(P.V).to(dev) if device else P.V
+        U0 = make_U0(V)
+        hit = {}
+        resid = []
+        with pkg.Solver(P.shape, P.lo, P.hi, V, U0, p, prec=prec, device=device) as s:
+            E0 = s.stats()["energy"]
+            k = 0
+            while k < cap and len(hit) < len(milestones):
+                st = s.step(1)
+                k += 1
+                for m in milestones:
+                    if m not in hit and 0 < st["err_E"] < m:
+                        hit[m] = (k, time.perf_counter() - t)
+                if k % 100 == 0:
+                    resid.append((k, s.residual()))
+            E = s.stats()["energy"]
+        return {"E0": E0, "E": E, "steps": k,
+                "err_E": {f"{m:g}": hit.get(m) for m in milestones}, "residual_every_100": resid}
+
+    rows = []
+    for i in range(args.eval_count):
+        sd = 900000 + 1000 * rank + i
+        P = syn.warm_start_problem(sd, N=N, p=p)
+        Ur = syn.gaussian_block(sd, P.n, p)
+        rows.append({
+            "seed": sd,
+            "fp64_random": timed_solve(P, lambda V: Ur, "fp64", False),
+            "fp32_random": timed_solve(P, lambda V: Ur, "fp32", False),
+            "fp32_learned": timed_solve(P, lambda V: net.infer(V), "fp32", True),
+        })
+    net.close()
+    modes = ("fp64_random", "fp32_random", "fp32_learned")
+
+    def mean_at(mode, m, idx):
+        v = [r[mode]["err_E"][f"{m:g}"] for r in rows]
+        if any(x is None for x in v):
+            return None
+        return float(np.mean([x[idx] for x in v]))
+
+    summary = {f"{m:g}": {mode: {"steps": mean_at(mode, m, 0), "s": mean_at(mode, m, 1)}
+                          for mode in modes} for m in milestones}
+    head = summary[f"{tol:g}"]
+
+    if rank == 0:
+        line = {
+            "metric": f"time-to-err_E {tol:g} (Algorithm 1 stop rule)",
+            "value": head["fp32_learned"]["s"], "unit": "s",
+            "n_gpus": 1, "higher_is_better": False, "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "warmstart_48^3_p64", "n": N ** 3, "p": p,
+                       "widths": list(widths), "params": nparams,
+                       "train_problems": args.train_count, "epochs": args.epochs,
+                       "eval_problems": args.eval_count, "step_cap": cap,
+                       "target_solves": f"FP32, residual 1e-4 or {args.ws_target_cap} steps",
+                       "timing": "host wall clock; learned includes inference and Cholesky-QR"},
+            "err_E_milestones": summary,
+            "E0": {mode: float(np.mean([r[mode]["E0"] for r in rows])) for mode in modes},
+            "train": {"data_gen_s": gen_s, "train_s": train_s, "loss_per_epoch": losses},
+            "rows": rows,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,7 +540,15 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "mix_tf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="3d_wells_64", choices=["3d_wells_64", "batch64"])
+    ap.add_argument("--workload", default="3d_wells_64",
+                    choices=["3d_wells_64", "batch64", "warmstart48"])
+    ap.add_argument("--train-count", type=int, default=192)
+    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--eval-count", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--ws-cap", type=int, default=3000)
+    ap.add_argument("--ws-tol", type=float, default=1e-6, choices=[1e-4, 1e-6, 1e-8])
+    ap.add_argument("--ws-target-cap", type=int, default=300)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--cg-iters", type=int, default=12)
     args = ap.parse_args()
@@ -435,6 +558,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "warmstart48":
+        return run_warmstart(args)
     return run_ours(args)
 
 

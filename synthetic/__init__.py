@@ -199,15 +199,17 @@ def batch_problems(seed: int, count: int = 64, nmin: int = 24, nmax: int = 48,
 
 
 def warm_start_problem(seed: int, N: int = 48, p: int = 64, box: float = 8.0,
-                       wells=(4, 16), depth=(1.0, 6.0), width=(0.5, 1.5)) -> Problem:
+                       wells=(4, 16), depth=(1.0, 6.0), width=(0.5, 1.5),
+                       harmonic: float = 0.0) -> Problem:
     """Learned-warm-start workload: V = sum of U{4..16} Gaussian wells on [-box, box]^3,
-    depths U[1, 6], centres uniform in the box, no harmonic term; N^3 grid, p orbitals."""
+    depths U[1, 6], centres uniform in the box (plus harmonic * |x|^2, zero by
+    default); N^3 grid, p orbitals."""
     u = uniform01(stream_key(seed, STREAM_LEARN), 0, 1)[0]
     k = wells[0] + int(u * (wells[1] - wells[0] + 1))
     shape = (N, N, N)
     lo, hi = (-box,) * 3, (box,) * 3
     w = draw_wells(seed, k, lo, hi, depth, width)
-    return Problem(shape, lo, hi, potential(shape, lo, hi, 0.0, w), p,
+    return Problem(shape, lo, hi, potential(shape, lo, hi, harmonic, w), p,
                    f"warmstart_{N}^3_p{p}_w{k}_s{seed}", w)
 
 
