@@ -170,6 +170,27 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_problem(rank):
+    """Weak scaling: every rank advances its own seeded instance of the workload."""
+    P = syn.config_3d_wells(rank)
+    return P, syn.gaussian_block(rank, P.n, P.p)
+
+
+def max_over_ranks(ms, device, ws):
+    """The job's elapsed time: the slowest rank's (all-reduce MAX; no data-path exchange)."""
+    if ws <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, steps, ws, ms):
+    """Whole-job throughput: the units all ranks processed over the job's elapsed time."""
+    return units_per_rank * steps * ws / (ms * 1e-3)
+
+
 # ----------------------------------------------------------------------------
 # The oracle arm (CPU): the FP64 oracle as it stands, on a bounded sample
 # ----------------------------------------------------------------------------
@@ -236,9 +257,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    seed = rank
-    P = syn.config_3d_wells(seed)
-    U0 = syn.gaussian_block(seed, P.n, P.p)
+    P, U0 = rank_problem(rank)
     n, p = P.n, P.p
     s_el = 8 if args.prec == "fp64" else 4
 
@@ -273,11 +292,8 @@ def run_ours(args):
     st1 = solver.stats()
     prof = solver.profile_read()
     solver.profile(False)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * p * args.steps * ws / (ms * 1e-3)
+    ms = max_over_ranks(ms, dev, ws)
+    value = job_value(n * p, args.steps, ws, ms)
 
     # roofline of the dominant kernel group (most device time in the timed region)
     hbm, _, peak_kind = load_peaks()
@@ -384,11 +400,8 @@ def run_batch(args):
     ms = (time.perf_counter() - t0) * 1e3
     clk = clocks.stop()
     launches = L.op_kernel_launches() - l0
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = units * args.steps * ws / (ms * 1e-3)
+    ms = max_over_ranks(ms, dev, ws)
+    value = job_value(units, args.steps, ws, ms)
     iters = [batch.stats(i)["last_cg_iters"] for i in range(len(probs))]
     batch.close()
     # the same problems stepped one context at a time (per-problem launches)
