@@ -545,6 +545,69 @@ def run_warmstart(args):
     return 0
 
 
+def run_ttr(args):
+    """Time to residual milestones on the 64^3 x 128 workload from the same raw U0 in
+    each precision mode, through the public API (op_init_device, then op_step in
+    chunks of --ttr-check steps with op_residual after each chunk; host wall clock).
+    Records, per mode, the step and the time at which the residual r first fell below
+    1e-3, 1e-4, 1e-5 and 1e-6 (up to --ttr-cap steps).  value = the FP32 mode's
+    time to the smallest milestone that every mode reached; the plain FP64 GPU form
+    is the reference the speedups are quoted against."""
+    import torch
+
+    import paper_2511_06788_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P, U0 = rank_problem(rank)
+    V_d = torch.from_numpy(P.V).to(dev)
+    U0_d = torch.from_numpy(U0).to(dev)
+    milestones = [1e-3, 1e-4, 1e-5, 1e-6]
+    rows, lams = {}, {}
+    for prec in args.ttr_modes.split(","):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        hit, k, r = {}, 0, float("inf")
+        with pkg.Solver(P.shape, P.lo, P.hi, V_d, U0_d, P.p, prec=prec, device=True) as s:
+            while k < args.ttr_cap and len(hit) < len(milestones):
+                s.step(args.ttr_check)
+                k += args.ttr_check
+                r = s.residual()
+                for m in milestones:
+                    if m not in hit and r < m:
+                        hit[m] = (k, time.perf_counter() - t0)
+            el = time.perf_counter() - t0
+            st = s.stats()
+            lams[prec] = s.eigenvalues()
+        rows[prec] = {"s": el, "steps": k, "residual": r, "orth": st["orth"],
+                      "cg_iters": st["cg_iters"], "ms_per_step": 1e3 * el / max(1, k),
+                      "milestones": {f"{m:g}": hit.get(m) for m in milestones}}
+    common = [m for m in milestones if all(rows[q]["milestones"][f"{m:g}"] for q in rows)]
+    best = f"{common[-1]:g}" if common else None
+    for prec in rows:
+        if "fp64" in lams and prec != "fp64":
+            rows[prec]["eig_max_rel_vs_fp64"] = float(
+                np.max(np.abs(lams[prec] - lams["fp64"]) / np.abs(lams["fp64"])))
+            if best:
+                rows[prec]["speedup_vs_fp64_at_" + best] = (
+                    rows["fp64"]["milestones"][best][1] / rows[prec]["milestones"][best][1])
+    if rank == 0:
+        head = rows.get("fp32") or next(iter(rows.values()))
+        line = {
+            "metric": f"time-to-residual {best}" if best else "time-to-residual",
+            "value": head["milestones"][best][1] if best else None, "unit": "s",
+            "n_gpus": 1, "higher_is_better": False, "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": P.n, "p": P.p, "step_cap": args.ttr_cap,
+                       "residual_every": args.ttr_check,
+                       "timing": "host wall clock from op_init_device, residual checks included"},
+            "modes": rows,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,7 +617,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="3d_wells_64",
-                    choices=["3d_wells_64", "batch64", "warmstart48"])
+                    choices=["3d_wells_64", "batch64", "warmstart48", "ttr64"])
+    ap.add_argument("--ttr-modes", default="fp32,mix_tf32,fp64")
+    ap.add_argument("--ttr-cap", type=int, default=4500)
+    ap.add_argument("--ttr-check", type=int, default=25)
     ap.add_argument("--train-count", type=int, default=192)
     ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--eval-count", type=int, default=4)
@@ -573,6 +639,8 @@ def main():
         return run_batch(args)
     if args.workload == "warmstart48":
         return run_warmstart(args)
+    if args.workload == "ttr64":
+        return run_ttr(args)
     return run_ours(args)
 
 
