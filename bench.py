@@ -583,15 +583,18 @@ def run_ttr(args):
         rows[prec] = {"s": el, "steps": k, "residual": r, "orth": st["orth"],
                       "cg_iters": st["cg_iters"], "ms_per_step": 1e3 * el / max(1, k),
                       "milestones": {f"{m:g}": hit.get(m) for m in milestones}}
-    common = [m for m in milestones if all(rows[q]["milestones"][f"{m:g}"] for q in rows)]
+    # headline: the smallest milestone both FP32 and plain FP64 reached
+    pair = [q for q in ("fp32", "fp64") if q in rows] or list(rows)
+    common = [m for m in milestones if all(rows[q]["milestones"][f"{m:g}"] for q in pair)]
     best = f"{common[-1]:g}" if common else None
     for prec in rows:
         if "fp64" in lams and prec != "fp64":
             rows[prec]["eig_max_rel_vs_fp64"] = float(
                 np.max(np.abs(lams[prec] - lams["fp64"]) / np.abs(lams["fp64"])))
-            if best:
-                rows[prec]["speedup_vs_fp64_at_" + best] = (
-                    rows["fp64"]["milestones"][best][1] / rows[prec]["milestones"][best][1])
+            rows[prec]["speedup_vs_fp64"] = {
+                m: rows["fp64"]["milestones"][m][1] / rows[prec]["milestones"][m][1]
+                for m in rows[prec]["milestones"]
+                if rows[prec]["milestones"][m] and rows["fp64"]["milestones"][m]}
     if rank == 0:
         head = rows.get("fp32") or next(iter(rows.values()))
         line = {
