@@ -271,63 +271,65 @@ template <typename T> op_status eig_impl(op_ctx *c, double *lam, int kind) {
   return OP_OK;
 }
 
-// Cholesky-QR (FP64) of the raw n x p block at U0 (device) into c->U (T).
-template <typename T> op_status orthonormalise_impl(op_ctx *c, const double *U0_dev) {
-  void *A64 = nullptr, *Q64 = nullptr, *KW64 = nullptr, *gws = nullptr;
-  const size_t blk = (size_t)c->n * c->ld * sizeof(double);
-  op_status s = OP_OK;
-  auto cleanup = [&]() {
-    for (void *p : {A64, Q64, KW64, gws}) {
-      if (!p) continue;
-      cudaFree(p);
-      for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
-        if (*it == p) {
-          c->allocs.erase(it);
-          break;
-        }
-    }
-  };
-  const size_t gbytes = gram_workspace_bytes(c->n, c->ld, 8);
-  if ((s = dev_alloc(c, &A64, blk)) || (s = dev_alloc(c, &Q64, blk)) ||
-      (s = dev_alloc(c, &KW64, (size_t)c->ld * c->ld * 8)) || (s = dev_alloc(c, &gws, gbytes))) {
-    cleanup();
-    return s;
+// Status of a Cholesky-QR pass: synchronises; OP_ERR_NOTSPD when U^T U was not
+// positive definite, OP_ERR_TIMEOUT when a tensor-core kernel gave up a wait.
+op_status cholqr_check(op_ctx *c) {
+  OP_CUDA(cudaMemcpyAsync(c->hpin_int, c->core_ws, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  OP_CUDA(cudaMemcpyAsync(c->hpin_int + 1, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost,
+                          c->st));
+  OP_CUDA(cudaStreamSynchronize(c->st));
+  if (c->hpin_int[1]) {
+    set_error("a tensor-core kernel timed out waiting for its MMAs (bounded mbarrier wait)");
+    return OP_ERR_TIMEOUT;
   }
-  cudaError_t e = cudaMemsetAsync(KW64, 0, (size_t)c->ld * c->ld * 8, c->st);
-  if (e != cudaSuccess) {
-    cleanup();
-    return cuda_status(e, "cudaMemsetAsync");
-  }
-  if ((s = launch_pad_copy<double>(c->n, c->p, c->ld, U0_dev, (double *)A64, c->st)) ||
-      (s = gram<double>(c->n, c->p, c->ld, (const double *)A64, (const double *)A64, nullptr,
-                        nullptr, c->D, gws, gbytes, c->st)) ||
-      (s = cholqr_coeff(c->p, c->ld, c->D, c->KU, c->core_ws, c->st)) ||
-      (s = update<double>(c->n, c->ld, (const double *)A64, (const double *)A64, c->KU,
-                          (const double *)KW64, (double *)Q64, c->st))) {
-    cleanup();
-    return s;
-  }
-  if (c->prec == OP_FP64) {
-    e = cudaMemcpyAsync(c->U, Q64, blk, cudaMemcpyDeviceToDevice, c->st);
-  } else {
-    // convert in chunks of at most 2^30 elements
-    const long long total = c->n * c->ld;
-    for (long long o = 0; o < total && !s; o += (1ll << 30)) {
-      const long long cnt = (total - o) < (1ll << 30) ? (total - o) : (1ll << 30);
-      s = launch_convert<T>((int)cnt, (const double *)Q64 + o, (T *)c->U + o, c->st);
-    }
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->hpin_int, c->core_ws, sizeof(int),
-                                            cudaMemcpyDeviceToHost, c->st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-  cleanup();
-  if (e != cudaSuccess) return cuda_status(e, "orthonormalise");
-  if (s) return s;
-  if (*c->hpin_int) {
+  if (c->hpin_int[0]) {
     set_error("Cholesky-QR of U0 failed: U0^T U0 is not positive definite");
     return OP_ERR_NOTSPD;
   }
   return OP_OK;
+}
+
+// Cholesky-QR of the raw n x p block at U0 (device, FP64) into c->U: with
+// D = U0^T U0 and R = chol(D)^T, U = U0 R^-1 (R's diagonal positive, so U is the Q of
+// the Householder QR with a positive diagonal of R).
+// FP64 contexts: one pass in FP64.
+// FP32 contexts: two passes on FP32 blocks with the tensor-core Gram and update
+// (the Cholesky factor and R^-1 in FP64).  The second pass removes the first pass's
+// orthogonality error, about kappa(U0)^2 times the FP32 rounding.
+template <typename T> op_status orthonormalise_impl(op_ctx *c, const double *U0_dev) {
+  if constexpr (std::is_same<T, float>::value) {
+    float *X = (float *)c->U2, *Y = (float *)c->U;
+    OP_TRY(launch_pad_copy<float>(c->n, c->p, c->ld, U0_dev, X, c->st));
+    OP_CUDA(cudaMemsetAsync(c->KW, 0, (size_t)c->ld * c->ld * sizeof(double), c->st));
+    for (int pass = 0; pass < 2; ++pass) {
+      OP_TRY(gram_tc(c->n, c->p, c->ld, X, X, nullptr, nullptr, c->D, c->gram_ws, c->gram_bytes,
+                     c->dev_err, c->st, 1));
+      OP_TRY(cholqr_coeff(c->p, c->ld, c->D, c->KU, c->core_ws, c->st));
+      OP_TRY(cholqr_check(c));
+      // X KU = X + [X X] [KU - I; 0]
+      OP_TRY(launch_make_kt(c->ld, c->KU, c->KW, c->KT_hi, c->KT_lo, c->st));
+      OP_TRY(update_tc(c->n, c->ld, X, X, c->KT_hi, c->KT_lo, Y, c->dev_err, c->st, 1));
+      float *tmp = X;
+      X = Y;
+      Y = tmp;
+    }
+    c->U = X;  // the second pass's output
+    c->U2 = Y;
+    return cholqr_check(c);
+  } else {
+    const size_t gbytes = gram_workspace_bytes(c->n, c->ld, 8);
+    double *A = (double *)c->U2, *Q = (double *)c->U;
+    OP_TRY(launch_pad_copy<double>(c->n, c->p, c->ld, U0_dev, A, c->st));
+    if (c->gram_bytes < gbytes) {
+      set_error("orthonormalise: Gram workspace too small");
+      return OP_ERR_STATE;
+    }
+    OP_TRY(gram<double>(c->n, c->p, c->ld, A, A, nullptr, nullptr, c->D, c->gram_ws,
+                        c->gram_bytes, c->st));
+    OP_TRY(cholqr_coeff(c->p, c->ld, c->D, c->KU, c->core_ws, c->st));
+    OP_TRY(update<double>(c->n, c->ld, A, nullptr, c->KU, nullptr, Q, c->st));
+    return cholqr_check(c);
+  }
 }
 
 template <typename T>
@@ -413,14 +415,17 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
                           n * sizeof(double),
                           device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
   OP_TRY(launch_convert<T>((int)n, (const double *)V64, (T *)c->Vt, c->st));
-  // raw U0 (n x p FP64) on the device
+  // raw U0 (n x p FP64) on the device (a device U0 is read in place)
   void *U0d = nullptr;
-  OP_TRY(dev_alloc(c, &U0d, (size_t)n * c->p * sizeof(double)));
-  OP_CUDA(cudaMemcpyAsync(U0d, U0, (size_t)n * c->p * sizeof(double),
-                          device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
-  op_status s = orthonormalise_impl<T>(c, (const double *)U0d);
+  if (!device) {
+    OP_TRY(dev_alloc(c, &U0d, (size_t)n * c->p * sizeof(double)));
+    OP_CUDA(cudaMemcpyAsync(U0d, U0, (size_t)n * c->p * sizeof(double), cudaMemcpyHostToDevice,
+                            c->st));
+  }
+  op_status s = orthonormalise_impl<T>(c, device ? U0 : (const double *)U0d);
   OP_CUDA(cudaStreamSynchronize(c->st));
   for (void *q : {V64, U0d}) {
+    if (!q) continue;
     cudaFree(q);
     for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
       if (*it == q) {

@@ -228,6 +228,7 @@ op_status launch_resid_coeff(int p, int ld, const double *Th, T *negTh, T *Id, c
 op_status launch_paper_lams(int p, const double *mu, double sigma, double *lam, cudaStream_t st);
 
 // ---- Step 4 (update.cu, update_tc.cu) -------------------------------------------------
+// Unew = U KU + W KW; W and KW may be nullptr (then Unew = U KU).
 template <typename T>
 op_status update(long long n, int ld, const T *U, const T *W, const T *KU, const T *KW, T *Unew,
                  cudaStream_t st);

@@ -1,5 +1,6 @@
 // Step 4 of §4.1, U^{n+1} = U^n - tau U^n A^n + tau W B^n, written as the
-// rank-2p product Unew = [U W] [KU; KW] with KU = I - tau A, KW = tau B.
+// rank-2p product Unew = [U W] [KU; KW] with KU = I - tau A, KW = tau B
+// (with W = nullptr, the rank-p product Unew = U KU).
 //
 // Each CTA computes a 64-row x 64-column tile of Unew; KC-wide slabs of the
 // n x 2p operand [U W] (16-byte loads along the row, stored k-major in shared
@@ -41,7 +42,8 @@ __global__ void __launch_bounds__(256) k_update(long long n, int ld, const T *__
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
 
-  for (int k0 = 0; k0 < 2 * ld; k0 += KC) {
+  const int K = W ? 2 * ld : ld;  // W == nullptr: Unew = U KU (no W block)
+  for (int k0 = 0; k0 < K; k0 += KC) {
 #pragma unroll
     for (int q = 0; q < (kRows * KV) / 256; ++q) {
       const int v = t + 256 * q;
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(256) k_update(long long n, int ld, const T *__
       const int kk = k0 + kv * N;
       const long long row = r0 + r;
       Pack<T> x = Pack<T>::zero();
-      if (row < n && kk < 2 * ld)
+      if (row < n && kk < K)
         x = (kk < ld) ? Pack<T>::load(U + row * ld + kk) : Pack<T>::load(W + row * ld + kk - ld);
 #pragma unroll
       for (int e = 0; e < N; ++e) As[kv * N + e][r] = x.v[e];
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(256) k_update(long long n, int ld, const T *__
       const int k = v / CV, cv = v % CV;
       const int kk = k0 + k, c = c0 + cv * N;
       Pack<T> x = Pack<T>::zero();
-      if (kk < 2 * ld && c < ld)
+      if (kk < K && c < ld)
         x = (kk < ld) ? Pack<T>::load(KU + (long long)kk * ld + c)
                       : Pack<T>::load(KW + (long long)(kk - ld) * ld + c);
       x.store(&Bs[k][cv * N]);
