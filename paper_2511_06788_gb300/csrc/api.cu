@@ -271,17 +271,11 @@ template <typename T> op_status eig_impl(op_ctx *c, double *lam, int kind) {
   return OP_OK;
 }
 
-// Status of a Cholesky-QR pass: synchronises; OP_ERR_NOTSPD when U^T U was not
-// positive definite, OP_ERR_TIMEOUT when a tensor-core kernel gave up a wait.
+// Status of the set-up's Cholesky-QR: synchronises; OP_ERR_NOTSPD when U0^T U0 was
+// not positive definite.
 op_status cholqr_check(op_ctx *c) {
   OP_CUDA(cudaMemcpyAsync(c->hpin_int, c->core_ws, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-  OP_CUDA(cudaMemcpyAsync(c->hpin_int + 1, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost,
-                          c->st));
   OP_CUDA(cudaStreamSynchronize(c->st));
-  if (c->hpin_int[1]) {
-    set_error("a tensor-core kernel timed out waiting for its MMAs (bounded mbarrier wait)");
-    return OP_ERR_TIMEOUT;
-  }
   if (c->hpin_int[0]) {
     set_error("Cholesky-QR of U0 failed: U0^T U0 is not positive definite");
     return OP_ERR_NOTSPD;
@@ -289,47 +283,68 @@ op_status cholqr_check(op_ctx *c) {
   return OP_OK;
 }
 
-// Cholesky-QR of the raw n x p block at U0 (device, FP64) into c->U: with
+// Cholesky-QR (FP64) of the raw n x p block at U0 (device, FP64) into c->U: with
 // D = U0^T U0 and R = chol(D)^T, U = U0 R^-1 (R's diagonal positive, so U is the Q of
-// the Householder QR with a positive diagonal of R).
-// FP64 contexts: one pass in FP64.
-// FP32 contexts: two passes on FP32 blocks with the tensor-core Gram and update
-// (the Cholesky factor and R^-1 in FP64).  The second pass removes the first pass's
-// orthogonality error, about kappa(U0)^2 times the FP32 rounding.
+// the Householder QR with a positive diagonal of R).  The set-up stays FP64 in every
+// mode: the midpoint scheme preserves U^T U, so the orthogonality error U0 starts
+// with stays for the whole run (an FP32 Cholesky-QR gave 1e-5 at p = 1024).
 template <typename T> op_status orthonormalise_impl(op_ctx *c, const double *U0_dev) {
-  if constexpr (std::is_same<T, float>::value) {
-    float *X = (float *)c->U2, *Y = (float *)c->U;
-    OP_TRY(launch_pad_copy<float>(c->n, c->p, c->ld, U0_dev, X, c->st));
-    OP_CUDA(cudaMemsetAsync(c->KW, 0, (size_t)c->ld * c->ld * sizeof(double), c->st));
-    for (int pass = 0; pass < 2; ++pass) {
-      OP_TRY(gram_tc(c->n, c->p, c->ld, X, X, nullptr, nullptr, c->D, c->gram_ws, c->gram_bytes,
-                     c->dev_err, c->st, 1));
-      OP_TRY(cholqr_coeff(c->p, c->ld, c->D, c->KU, c->core_ws, c->st));
-      OP_TRY(cholqr_check(c));
-      // X KU = X + [X X] [KU - I; 0]
-      OP_TRY(launch_make_kt(c->ld, c->KU, c->KW, c->KT_hi, c->KT_lo, c->st));
-      OP_TRY(update_tc(c->n, c->ld, X, X, c->KT_hi, c->KT_lo, Y, c->dev_err, c->st, 1));
-      float *tmp = X;
-      X = Y;
-      Y = tmp;
+  const size_t blk = (size_t)c->n * c->ld * sizeof(double);
+  const size_t gbytes = gram_workspace_bytes(c->n, c->ld, 8);
+  void *A64 = nullptr, *Q64 = nullptr, *gws = nullptr;
+  auto release = [&]() {
+    for (void *p : {A64, Q64, gws}) {
+      if (!p) continue;
+      cudaFree(p);
+      for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
+        if (*it == p) {
+          c->allocs.erase(it);
+          break;
+        }
     }
-    c->U = X;  // the second pass's output
-    c->U2 = Y;
-    return cholqr_check(c);
+  };
+  double *A, *Q;
+  void *ws = c->gram_ws;
+  size_t wsb = c->gram_bytes;
+  op_status s = OP_OK;
+  if constexpr (std::is_same<T, double>::value) {
+    A = (double *)c->U2;  // FP64 contexts: the context's own blocks are the scratch
+    Q = (double *)c->U;
   } else {
-    const size_t gbytes = gram_workspace_bytes(c->n, c->ld, 8);
-    double *A = (double *)c->U2, *Q = (double *)c->U;
-    OP_TRY(launch_pad_copy<double>(c->n, c->p, c->ld, U0_dev, A, c->st));
-    if (c->gram_bytes < gbytes) {
-      set_error("orthonormalise: Gram workspace too small");
-      return OP_ERR_STATE;
+    if ((s = dev_alloc(c, &A64, blk)) || (s = dev_alloc(c, &Q64, blk))) {
+      release();
+      return s;
     }
-    OP_TRY(gram<double>(c->n, c->p, c->ld, A, A, nullptr, nullptr, c->D, c->gram_ws,
-                        c->gram_bytes, c->st));
-    OP_TRY(cholqr_coeff(c->p, c->ld, c->D, c->KU, c->core_ws, c->st));
-    OP_TRY(update<double>(c->n, c->ld, A, nullptr, c->KU, nullptr, Q, c->st));
-    return cholqr_check(c);
+    A = (double *)A64;
+    Q = (double *)Q64;
   }
+  if (wsb < gbytes) {
+    if ((s = dev_alloc(c, &gws, gbytes))) {
+      release();
+      return s;
+    }
+    ws = gws;
+    wsb = gbytes;
+  }
+  if ((s = launch_pad_copy<double>(c->n, c->p, c->ld, U0_dev, A, c->st)) ||
+      (s = gram<double>(c->n, c->p, c->ld, A, A, nullptr, nullptr, c->D, ws, wsb, c->st)) ||
+      (s = cholqr_coeff(c->p, c->ld, c->D, c->KU, c->core_ws, c->st)) ||
+      (s = update<double>(c->n, c->ld, A, nullptr, c->KU, nullptr, Q, c->st))) {
+    release();
+    return s;
+  }
+  if constexpr (!std::is_same<T, double>::value) {
+    // convert in chunks of at most 2^30 elements
+    const long long total = c->n * c->ld;
+    for (long long o = 0; o < total && !s; o += (1ll << 30)) {
+      const long long cnt = (total - o) < (1ll << 30) ? (total - o) : (1ll << 30);
+      s = launch_convert<T>((int)cnt, Q + o, (T *)c->U + o, c->st);
+    }
+  }
+  if (s == OP_OK) s = cholqr_check(c);
+  else cudaStreamSynchronize(c->st);
+  release();
+  return s;
 }
 
 template <typename T>
