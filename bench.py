@@ -565,22 +565,31 @@ def run_ttr(args):
     U0_d = torch.from_numpy(U0).to(dev)
     milestones = [1e-3, 1e-4, 1e-5, 1e-6]
     rows, lams = {}, {}
-    for prec in args.ttr_modes.split(","):
+    for mode in args.ttr_modes.split(","):
+        prec, _, adapt = mode.partition("+adapt")   # e.g. "fp32+adapt100"
+        adapt = int(adapt) if adapt else 0
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         hit, k, r = {}, 0, float("inf")
-        with pkg.Solver(P.shape, P.lo, P.hi, V_d, U0_d, P.p, prec=prec, device=True) as s:
+        with pkg.Solver(P.shape, P.lo, P.hi, V_d, U0_d, P.p, prec=prec, device=True,
+                        adapt_every=adapt) as s:
             while k < args.ttr_cap and len(hit) < len(milestones):
-                s.step(args.ttr_check)
+                if adapt:
+                    # re-tuning runs inside op_solve (stop rule: steps), which ends
+                    # with a residual evaluation
+                    r = s.solve(0.0, args.ttr_check, pkg.OP_STOP_STEPS)["residual"]
+                else:
+                    s.step(args.ttr_check)
+                    r = s.residual()
                 k += args.ttr_check
-                r = s.residual()
                 for m in milestones:
                     if m not in hit and r < m:
                         hit[m] = (k, time.perf_counter() - t0)
             el = time.perf_counter() - t0
             st = s.stats()
-            lams[prec] = s.eigenvalues()
-        rows[prec] = {"s": el, "steps": k, "residual": r, "orth": st["orth"],
+            lams[mode] = s.eigenvalues()
+        rows[mode] = {"s": el, "steps": k, "residual": r, "orth": st["orth"],
+                      "sigma": st["sigma"], "tau": st["tau"],
                       "cg_iters": st["cg_iters"], "ms_per_step": 1e3 * el / max(1, k),
                       "milestones": {f"{m:g}": hit.get(m) for m in milestones}}
     # headline: the smallest milestone both FP32 and plain FP64 reached

@@ -91,6 +91,18 @@ typedef struct {
                             also <= 0.1 tol (residual rule) or 0.1 sqrt(tol) (err_E) */
   int cg_max_iter;       /* Step-1 CG iteration cap per step (<= 0: 2000)           */
   int check_every;       /* op_solve: residual evaluated every this many steps (<= 0: 10) */
+  int adapt_every;       /* op_solve: <= 0 keeps sigma and tau fixed; > 0 re-tunes them
+                            (inside op_solve, before a step whose context step count
+                            is a multiple of this) from the Ritz values lambda_1 <= ..
+                            <= lambda_p of the current U: sigma = max(sigma_0,
+                            lambda_p - 2 lambda_1) (the shift that maximises the
+                            per-step contraction (lambda_1 + sigma) / (lambda_p +
+                            sigma)^2 of the slowest directions), tau = 1.5 (L + sigma);
+                            a re-tune that is followed by an energy increase is undone
+                            and adaptation stops.  sigma_0 is the initial sigma; the
+                            residual normalisation keeps sigma_0.  Algorithm 1 allows
+                            a variable tau_n; the fixed points do not depend on sigma
+                            or tau. */
 } op_problem;
 
 /* Per-context statistics, filled by op_step / op_solve. */

@@ -31,7 +31,7 @@ class OpProblem(C.Structure):
     _fields_ = [("dim", C.c_int), ("shape", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("p", C.c_int), ("sigma", C.c_double),
                 ("tau", C.c_double), ("prec", C.c_int), ("cg_rtol", C.c_double),
-                ("cg_max_iter", C.c_int), ("check_every", C.c_int)]
+                ("cg_max_iter", C.c_int), ("check_every", C.c_int), ("adapt_every", C.c_int)]
 
 
 class OpStats(C.Structure):
@@ -138,7 +138,7 @@ def last_error() -> str:
 
 
 def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol=0.0,
-                 cg_max_iter=0, check_every=0) -> OpProblem:
+                 cg_max_iter=0, check_every=0, adapt_every=0) -> OpProblem:
     pb = OpProblem()
     dim = len(shape)
     pb.dim = dim
@@ -153,6 +153,7 @@ def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol
     pb.cg_rtol = float(cg_rtol)
     pb.cg_max_iter = int(cg_max_iter)
     pb.check_every = int(check_every)
+    pb.adapt_every = int(adapt_every)
     return pb
 
 
@@ -179,9 +180,11 @@ class Solver:
     """A solver context (op_init ... op_destroy) for one eigenproblem."""
 
     def __init__(self, shape, lo, hi, V, U0, p, *, prec="fp64", sigma=None, tau=None,
-                 cg_rtol=0.0, cg_max_iter=0, check_every=0, stream=None, device=False):
+                 cg_rtol=0.0, cg_max_iter=0, check_every=0, adapt_every=0, stream=None,
+                 device=False):
         self.pb = make_problem(shape, lo, hi, p, prec=prec, sigma=sigma, tau=tau,
-                               cg_rtol=cg_rtol, cg_max_iter=cg_max_iter, check_every=check_every)
+                               cg_rtol=cg_rtol, cg_max_iter=cg_max_iter, check_every=check_every,
+                               adapt_every=adapt_every)
         self.n = int(np.prod(shape))
         self.p = int(p)
         self._ctx = C.c_void_p()

@@ -375,6 +375,9 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
     set_error("tau must be positive (got %g) and sigma finite", c->tau);
     return OP_ERR_ARG;
   }
+  c->Lb = L;
+  c->sigma0 = c->sigma;
+  c->adapt_off = 0;
   c->hnorm = 2.0 * c->g.cdiag +
              (fabs(vmax + c->sigma) > fabs(vmin + c->sigma) ? fabs(vmax + c->sigma)
                                                             : fabs(vmin + c->sigma));
@@ -538,6 +541,29 @@ op_status op_residual(op_ctx *c, double *r) {
   return c->prec == OP_FP64 ? residual_impl<double>(c, r) : residual_impl<float>(c, r);
 }
 
+// Adaptive shift (op_problem.adapt_every): from the Ritz values lambda_1 <= .. <=
+// lambda_p of the current U, sigma = max(sigma_0, lambda_p - 2 lambda_1) and
+// tau = 1.5 (L + sigma).  With G = (H + sigma)^-1 and tau ~ 1/mu_1, the slowest
+// directions contract per step in proportion to (lambda_1 + sigma) (lambda_{p+1} -
+// lambda_p) / ((lambda_p + sigma) (lambda_{p+1} + sigma)), which is largest at
+// sigma ~ lambda_p - 2 lambda_1.  Changes below 10 % are skipped.  The previous
+// sigma and tau are returned for the energy guard.
+op_status retune_shift(op_ctx *c, double *prev_sigma, double *prev_tau) {
+  std::vector<double> lam(c->p);
+  OP_TRY(c->prec == OP_FP64 ? eig_impl<double>(c, lam.data(), OP_EIG_RITZ)
+                            : eig_impl<float>(c, lam.data(), OP_EIG_RITZ));
+  *prev_sigma = c->sigma;
+  *prev_tau = c->tau;
+  double s = lam[c->p - 1] - 2.0 * lam[0];
+  if (!(s > c->sigma0)) s = c->sigma0;
+  if (!isfinite(s) || fabs(s - c->sigma) <= 0.1 * fabs(c->sigma + c->Lb)) return OP_OK;
+  c->sigma = s;
+  c->tau = 1.5 * (c->Lb + s);
+  c->stats.sigma = c->sigma;
+  c->stats.tau = c->tau;
+  return OP_OK;
+}
+
 op_status op_solve(op_ctx *c, double tol, int max_steps, int stop, op_stats *st) {
   if (!c || max_steps < 0 || (stop != OP_STOP_RESIDUAL && stop != OP_STOP_ERR_E &&
                               stop != OP_STOP_STEPS)) {
@@ -551,6 +577,9 @@ op_status op_solve(op_ctx *c, double tol, int max_steps, int stop, op_stats *st)
   c->cg_cap = stop == OP_STOP_RESIDUAL ? 0.1 * tol : (stop == OP_STOP_ERR_E ? 0.1 * sqrt(tol) : 0.0);
   bool done = false;
   double r = NAN;
+  const int adapt = c->pb.adapt_every;
+  double prev_sigma = c->sigma, prev_tau = c->tau, E_before = 0.0;
+  bool probation = false;  // the step after a re-tune: undo it if the energy rises
   for (int k = 0; k <= max_steps; ++k) {
     if (stop == OP_STOP_ERR_E && c->stats.err_E <= tol) {
       done = true;
@@ -564,8 +593,23 @@ op_status op_solve(op_ctx *c, double tol, int max_steps, int stop, op_stats *st)
       }
     }
     if (k == max_steps) break;
+    if (adapt > 0 && !c->adapt_off && c->stats.steps > 0 && c->stats.steps % adapt == 0) {
+      OP_TRY(retune_shift(c, &prev_sigma, &prev_tau));
+      probation = c->sigma != prev_sigma;
+      E_before = c->E;
+    }
     op_status s = c->prec == OP_FP64 ? step_impl<double>(c) : step_impl<float>(c);
     if (s != OP_OK) return s;
+    if (probation) {
+      probation = false;
+      if (c->E > E_before + 1e-12 * fabs(E_before)) {  // energy rose: undo, stop adapting
+        c->sigma = prev_sigma;
+        c->tau = prev_tau;
+        c->stats.sigma = c->sigma;
+        c->stats.tau = c->tau;
+        c->adapt_off = 1;
+      }
+    }
   }
   c->cg_cap = 0.0;
   if (stop == OP_STOP_STEPS) done = true;

@@ -14,6 +14,8 @@ struct op_ctx {
   long long n;
   int p, ld, prec, elem;
   double sigma, tau, hnorm;
+  double Lb, sigma0;     // spectrum lower bound L and the initial sigma (adaptive shift)
+  int adapt_off;         // adaptation stopped (a re-tune raised the energy)
   cudaStream_t st;
   // blocks (element type T)
   void *U, *U2, *W, *Vt;
