@@ -630,7 +630,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="3d_wells_64",
                     choices=["3d_wells_64", "batch64", "warmstart48", "ttr64"])
-    ap.add_argument("--ttr-modes", default="fp32,mix_tf32,fp64")
+    ap.add_argument("--ttr-modes", default="fp32,fp32+adapt100,mix_tf32,fp64")
     ap.add_argument("--ttr-cap", type=int, default=4500)
     ap.add_argument("--ttr-check", type=int, default=25)
     ap.add_argument("--train-count", type=int, default=192)
