@@ -1,0 +1,75 @@
+"""The paper's test problem I (§5.1, Table 1) on the GPU: the FD analog of the 2D
+harmonic oscillator -1/2 Delta + 1/2 |x|^2 on (-5.5, 5.5)^2, N = 15 eigenpairs,
+sigma = 0, uniform tau, stopped when the relative energy error against the
+discrete reference drops below 1e-10 (the paper's rule).
+
+- Step counts are within 25 % of Table 1's (quadratic FEM with the same number of
+  unknowns; the oracle's CPU run of the same analog is pinned the same way).
+- Mesh independence (the scheme has no CFL limit): at tau = 1 the step count on
+  99^2, 199^2 and 399^2 grids varies by a few percent while h^2 varies 16-fold.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as o
+import synthetic as syn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2511_06788_gb300 as pkg  # noqa: E402
+from scipy.sparse.linalg import eigsh  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_test_problem_I.json")
+with open(GOLDEN) as f:
+    G = json.load(f)
+
+
+def e_ref(P):
+    H = o.hamiltonian(P.shape, P.lo, P.hi, P.V)
+    lam = np.sort(eigsh(H.tocsc(), k=P.p + 1, sigma=0, which="LM", return_eigenvectors=False))
+    return 0.5 * lam[:P.p].sum(), lam
+
+
+def steps_to_energy(P, tau, E_ref, cap):
+    with pkg.Solver(P.shape, P.lo, P.hi, P.V, syn.gaussian_block(0, P.n, P.p), P.p,
+                    prec="fp64", sigma=0.0, tau=tau) as s:
+        for k in range(1, cap + 1):
+            E = s.step(1)["energy"]
+            if (E - E_ref) / abs(E_ref) < G["stop_rel_energy_error"]:
+                return k, s.eigenvalues()
+    return None, None
+
+
+@pytest.fixture(scope="module")
+def ho199():
+    P = syn.harmonic_2d(199, G["N"], G["box"])
+    assert P.n == G["N_g"]
+    E, lam = e_ref(P)
+    return P, E, lam
+
+
+@pytest.mark.parametrize("tau", [0.1, 0.5, 1.0, 1.5])
+def test_table1_step_counts(ho199, tau):
+    P, E, lam = ho199
+    paper = G["steps"][G["tau"].index(tau)]
+    steps, ev = steps_to_energy(P, tau, E, 3 * paper)
+    print(f"tau {tau}: {steps} steps (Table 1: {paper})")
+    assert steps is not None and abs(steps - paper) <= 0.25 * paper
+    assert np.max(np.abs(ev / lam[:P.p] - 1.0)) <= G["max_err_i_all"]
+
+
+def test_step_count_is_mesh_independent():
+    counts = {}
+    for N in (99, 199, 399):
+        P = syn.harmonic_2d(N, G["N"], G["box"])
+        E, _ = e_ref(P)
+        counts[N], _ = steps_to_energy(P, 1.0, E, 1000)
+    print("tau 1.0 steps by grid:", counts)
+    assert all(c is not None for c in counts.values())
+    assert max(counts.values()) <= 1.1 * min(counts.values())
