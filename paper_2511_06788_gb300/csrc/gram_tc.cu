@@ -109,6 +109,9 @@ __device__ __forceinline__ void gram_tc_body(long long n, int ld, const float *_
   const float *A = (prod == PROD_D) ? U : W;
   const float *B = (prod == PROD_S) ? W : U;
   const int ca = ti * kTM, cb = tj * kTM;
+  // diagonal tiles of S = W^T W and D = U^T U: A and B are the same data, staged once
+  // (the B descriptors point at A's pieces; the MMAs and their order are unchanged)
+  const bool same = (A == B) && (ca == cb);
   if (r1 > n) r1 = n;
   const int nslab = r1 > r0 ? (int)((r1 - r0 + kKS - 1) / kKS) : 0;
 
@@ -159,11 +162,11 @@ __device__ __forceinline__ void gram_tc_body(long long n, int ld, const float *_
     uint8_t *stage = smem + st * kStage;
     // stage st was read by the MMAs of slab s-2, which the drain of slab s-2 waited for
     store_patch(stage, stage + kPiece, q, kq, va, split != 0);
-    store_patch(stage + 2 * kPiece, stage + 3 * kPiece, q, kq, vb, split != 0);
+    if (!same) store_patch(stage + 2 * kPiece, stage + 3 * kPiece, q, kq, vb, split != 0);
     if (s + 2 < nslab) {
       const long long r = r0 + (long long)(s + 2) * kKS + 4 * kq;
       load_patch(A, r, r1, ca + 4 * q, ld, va);
-      load_patch(B, r, r1, cb + 4 * q, ld, vb);
+      if (!same) load_patch(B, r, r1, cb + 4 * q, ld, vb);
     }
     tc::fence_async_smem();
     tc::tc_fence_before();
@@ -171,13 +174,14 @@ __device__ __forceinline__ void gram_tc_body(long long n, int ld, const float *_
     if (t == 0) {
       tc::tc_fence_after();
       const uint32_t base = tc::smem_u32(stage);
+      const uint32_t bbase = same ? base : base + 2 * kPiece;
       const uint32_t d = tmem + (uint32_t)(st * kTM);
 #pragma unroll
       for (int kk = 0; kk < kKS / 8; ++kk) {
         const uint64_t ah = tc::desc_sw128(base + kk * 32);
         const uint64_t al = tc::desc_sw128(base + kPiece + kk * 32);
-        const uint64_t bh = tc::desc_sw128(base + 2 * kPiece + kk * 32);
-        const uint64_t bl = tc::desc_sw128(base + 3 * kPiece + kk * 32);
+        const uint64_t bh = tc::desc_sw128(bbase + kk * 32);
+        const uint64_t bl = tc::desc_sw128(bbase + kPiece + kk * 32);
         tc::mma_tf32(d, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
         if (split) {
           tc::mma_tf32(d, ah, bl, kIdesc, 1u);
@@ -193,11 +197,11 @@ __device__ __forceinline__ void gram_tc_body(long long n, int ld, const float *_
   float va0[4][4], vb0[4][4], va1[4][4], vb1[4][4];
   if (nslab > 0) {
     load_patch(A, r0 + 4 * kq, r1, ca + 4 * q, ld, va0);
-    load_patch(B, r0 + 4 * kq, r1, cb + 4 * q, ld, vb0);
+    if (!same) load_patch(B, r0 + 4 * kq, r1, cb + 4 * q, ld, vb0);
   }
   if (nslab > 1) {
     load_patch(A, r0 + kKS + 4 * kq, r1, ca + 4 * q, ld, va1);
-    load_patch(B, r0 + kKS + 4 * kq, r1, cb + 4 * q, ld, vb1);
+    if (!same) load_patch(B, r0 + kKS + 4 * kq, r1, cb + 4 * q, ld, vb1);
   }
   bool ok = true;
   for (int s = 0; s < nslab && ok; s += 2) {
