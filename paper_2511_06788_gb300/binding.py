@@ -246,8 +246,10 @@ class Solver:
         check(lib().op_residual(self._ctx, C.byref(r)))
         return r.value
 
-    def get_U(self) -> np.ndarray:
-        U = np.empty((self.n, self.p))
+    def get_U(self, out=None) -> np.ndarray:
+        """U (n x p float64) in host memory; `out`, if given, is filled and returned."""
+        U = np.empty((self.n, self.p)) if out is None else out
+        assert U.shape == (self.n, self.p)
         check(lib().op_get_U(self._ctx, _dptr(U)))
         return U
 
