@@ -432,6 +432,86 @@ def run_batch(args):
     return 0
 
 
+def run_batch_ttr(args):
+    """Time to residual tol for the 64 uneven problems: the batch (graph replays of
+    batched kernels, FP32), the same problems solved one context at a time in FP32,
+    and in plain FP64 on the first --ttr-fp64-count problems (scaled to all of them,
+    stated as an extrapolation)."""
+    import torch
+
+    import paper_2511_06788_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    probs = syn.batch_problems(seed=rank, count=args.batch_count)
+    tol, cap, every = args.bttr_tol, args.bttr_cap, 50
+
+    def make(prec, subset=None):
+        out = []
+        for i, P in enumerate(probs if subset is None else probs[:subset]):
+            V_d = torch.from_numpy(P.V).to(dev)
+            U0_d = torch.from_numpy(syn.gaussian_block(1000 * rank + i, P.n, P.p)).to(dev)
+            out.append(pkg.Solver(P.shape, P.lo, P.hi, V_d, U0_d, P.p, prec=prec, device=True,
+                                  check_every=every))
+        return out
+
+    # batched
+    solvers = make("fp32")
+    batch = pkg.Batch(solvers, cg_iters=args.cg_iters)
+    cache = os.environ.get("OPEVO_TILE_CACHE", os.path.join(ROOT, "_build", "batch_tiles.jsonl"))
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    batch.autotune(cache, steps_per_trial=2)
+    batch.close()
+    for s in solvers:
+        s.close()
+    solvers = make("fp32")
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    batch = pkg.Batch(solvers, cg_iters=args.cg_iters)
+    batch.autotune(cache, steps_per_trial=2)  # a cache hit: the tuned tiles, no trials
+    nconv_b = batch.solve(tol, cap, pkg.OP_STOP_RESIDUAL, check_every=every, raise_on_max=False)
+    t_batch = time.perf_counter() - t0
+    steps_b = [batch.stats(i)["steps"] for i in range(len(probs))]
+    batch.close()
+    for s in solvers:
+        s.close()
+
+    def one_by_one(prec, subset=None):
+        solv = make(prec, subset)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        conv, steps = 0, []
+        for s in solv:
+            st = s.solve(tol, cap, raise_on_max=False)
+            conv += int(st["converged"])
+            steps.append(st["steps"])
+        el = time.perf_counter() - t
+        for s in solv:
+            s.close()
+        return el, conv, steps
+
+    t32, conv32, steps32 = one_by_one("fp32")
+    k64 = min(args.ttr_fp64_count, len(probs))
+    t64, conv64, steps64 = one_by_one("fp64", k64)
+    if rank == 0:
+        line = {
+            "metric": f"time-to-residual {tol:g} (batch of {len(probs)})", "value": t_batch,
+            "unit": "s", "n_gpus": 1, "higher_is_better": False, "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch{len(probs)}_uneven_24-48^3_p16-96", "tol": tol,
+                       "step_cap": cap, "residual_every": every,
+                       "timing": "host wall clock; contexts created before the clock starts"},
+            "batch_fp32": {"s": t_batch, "converged": nconv_b, "max_steps": max(steps_b)},
+            "one_by_one_fp32": {"s": t32, "converged": conv32, "max_steps": max(steps32)},
+            "one_by_one_fp64_subset": {"problems": k64, "s": t64, "converged": conv64,
+                                       "steps": steps64, "fp32_steps_same": steps32[:k64]},
+            "speedup_batch_vs_fp32_loop": t32 / t_batch,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_warmstart(args):
     """Learned warm start on 48^3, p = 64 (V = 4-16 Gaussian wells, no harmonic term).
 
@@ -631,7 +711,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="3d_wells_64",
-                    choices=["3d_wells_64", "batch64", "warmstart48", "ttr64"])
+                    choices=["3d_wells_64", "batch64", "warmstart48", "ttr64", "batch64-ttr"])
+    ap.add_argument("--bttr-tol", type=float, default=1e-6)
+    ap.add_argument("--bttr-cap", type=int, default=3000)
+    ap.add_argument("--ttr-fp64-count", type=int, default=8)
     ap.add_argument("--ttr-modes", default="fp32,fp32+adapt100,mix_tf32,fp64")
     ap.add_argument("--ttr-cap", type=int, default=4500)
     ap.add_argument("--ttr-check", type=int, default=25)
@@ -655,6 +738,8 @@ def main():
         return run_warmstart(args)
     if args.workload == "ttr64":
         return run_ttr(args)
+    if args.workload == "batch64-ttr":
+        return run_batch_ttr(args)
     return run_ours(args)
 
 
