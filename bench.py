@@ -491,6 +491,26 @@ def run_batch_ttr(args):
             s.close()
         return el, conv, steps
 
+    # batched, with the per-problem adaptive shift
+    t_ad, nconv_ad, steps_ad = None, None, None
+    if args.bttr_adapt > 0:
+        solvers = [pkg.Solver(P.shape, P.lo, P.hi, torch.from_numpy(P.V).to(dev),
+                              torch.from_numpy(syn.gaussian_block(1000 * rank + i, P.n,
+                                                                  P.p)).to(dev),
+                              P.p, prec="fp32", device=True, check_every=every,
+                              adapt_every=args.bttr_adapt) for i, P in enumerate(probs)]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        batch = pkg.Batch(solvers, cg_iters=args.cg_iters)
+        batch.autotune(cache, steps_per_trial=2)
+        nconv_ad = batch.solve(tol, cap, pkg.OP_STOP_RESIDUAL, check_every=every,
+                               raise_on_max=False)
+        t_ad = time.perf_counter() - t0
+        steps_ad = max(batch.stats(i)["steps"] for i in range(len(probs)))
+        batch.close()
+        for s in solvers:
+            s.close()
+
     t32, conv32, steps32 = one_by_one("fp32")
     k64 = min(args.ttr_fp64_count, len(probs))
     t64, conv64, steps64 = one_by_one("fp64", k64)
@@ -503,6 +523,9 @@ def run_batch_ttr(args):
                        "step_cap": cap, "residual_every": every,
                        "timing": "host wall clock; contexts created before the clock starts"},
             "batch_fp32": {"s": t_batch, "converged": nconv_b, "max_steps": max(steps_b)},
+            "batch_fp32_adaptive_shift": {"s": t_ad, "converged": nconv_ad,
+                                          "max_steps": steps_ad,
+                                          "adapt_every": args.bttr_adapt},
             "one_by_one_fp32": {"s": t32, "converged": conv32, "max_steps": max(steps32)},
             "one_by_one_fp64_subset": {"problems": k64, "s": t64, "converged": conv64,
                                        "steps": steps64, "fp32_steps_same": steps32[:k64]},
@@ -715,6 +738,7 @@ def main():
     ap.add_argument("--bttr-tol", type=float, default=1e-6)
     ap.add_argument("--bttr-cap", type=int, default=3000)
     ap.add_argument("--ttr-fp64-count", type=int, default=8)
+    ap.add_argument("--bttr-adapt", type=int, default=100)
     ap.add_argument("--ttr-modes", default="fp32,fp32+adapt100,mix_tf32,fp64")
     ap.add_argument("--ttr-cap", type=int, default=4500)
     ap.add_argument("--ttr-check", type=int, default=25)

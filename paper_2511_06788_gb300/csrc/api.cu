@@ -497,6 +497,29 @@ op_status init_common(op_ctx **out, const op_problem *pb, const double *V, const
 
 }  // namespace
 
+// Adaptive shift (op_problem.adapt_every): from the Ritz values lambda_1 <= .. <=
+// lambda_p of the current U, sigma = max(sigma_0, lambda_p - 2 lambda_1) and
+// tau = 1.5 (L + sigma).  With G = (H + sigma)^-1 and tau ~ 1/mu_1, the slowest
+// directions contract per step in proportion to (lambda_1 + sigma) (lambda_{p+1} -
+// lambda_p) / ((lambda_p + sigma) (lambda_{p+1} + sigma)), which is largest at
+// sigma ~ lambda_p - 2 lambda_1.  Changes below 10 % are skipped.  The previous
+// sigma and tau are returned for the energy guard.  Synchronises the context's stream.
+op_status opevo::retune_shift(op_ctx *c, double *prev_sigma, double *prev_tau) {
+  std::vector<double> lam(c->p);
+  OP_TRY(c->prec == OP_FP64 ? eig_impl<double>(c, lam.data(), OP_EIG_RITZ)
+                            : eig_impl<float>(c, lam.data(), OP_EIG_RITZ));
+  *prev_sigma = c->sigma;
+  *prev_tau = c->tau;
+  double s = lam[c->p - 1] - 2.0 * lam[0];
+  if (!(s > c->sigma0)) s = c->sigma0;
+  if (!isfinite(s) || fabs(s - c->sigma) <= 0.1 * fabs(c->sigma + c->Lb)) return OP_OK;
+  c->sigma = s;
+  c->tau = 1.5 * (c->Lb + s);
+  c->stats.sigma = c->sigma;
+  c->stats.tau = c->tau;
+  return OP_OK;
+}
+
 extern "C" {
 
 const char *op_version(void) { return "opevo 0.1 (sm_103a)"; }
@@ -539,29 +562,6 @@ op_status op_residual(op_ctx *c, double *r) {
     return OP_ERR_ARG;
   }
   return c->prec == OP_FP64 ? residual_impl<double>(c, r) : residual_impl<float>(c, r);
-}
-
-// Adaptive shift (op_problem.adapt_every): from the Ritz values lambda_1 <= .. <=
-// lambda_p of the current U, sigma = max(sigma_0, lambda_p - 2 lambda_1) and
-// tau = 1.5 (L + sigma).  With G = (H + sigma)^-1 and tau ~ 1/mu_1, the slowest
-// directions contract per step in proportion to (lambda_1 + sigma) (lambda_{p+1} -
-// lambda_p) / ((lambda_p + sigma) (lambda_{p+1} + sigma)), which is largest at
-// sigma ~ lambda_p - 2 lambda_1.  Changes below 10 % are skipped.  The previous
-// sigma and tau are returned for the energy guard.
-op_status retune_shift(op_ctx *c, double *prev_sigma, double *prev_tau) {
-  std::vector<double> lam(c->p);
-  OP_TRY(c->prec == OP_FP64 ? eig_impl<double>(c, lam.data(), OP_EIG_RITZ)
-                            : eig_impl<float>(c, lam.data(), OP_EIG_RITZ));
-  *prev_sigma = c->sigma;
-  *prev_tau = c->tau;
-  double s = lam[c->p - 1] - 2.0 * lam[0];
-  if (!(s > c->sigma0)) s = c->sigma0;
-  if (!isfinite(s) || fabs(s - c->sigma) <= 0.1 * fabs(c->sigma + c->Lb)) return OP_OK;
-  c->sigma = s;
-  c->tau = 1.5 * (c->Lb + s);
-  c->stats.sigma = c->sigma;
-  c->stats.tau = c->tau;
-  return OP_OK;
 }
 
 op_status op_solve(op_ctx *c, double tol, int max_steps, int stop, op_stats *st) {

@@ -445,7 +445,59 @@ op_status op_batch_solve(op_batch *b, double tol, int max_steps, int stop, int c
   BatchCtl ctl{stop, tol, stop == OP_STOP_RESIDUAL ? 0.1 * tol : 0.1 * sqrt(tol)};
   OP_CUDA(cudaMemcpyAsync(b->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, b->st));
   int done_steps = 0, conv = 0;
+  // adaptive shift per problem (op_problem.adapt_every of its context): re-tuned at the
+  // first check at or after each multiple of adapt_every steps; the descriptors the
+  // replayed kernels read are updated in place.  A re-tune after which the energy has
+  // risen by the next check is undone and adaptation stops for that problem.
+  struct Guard {
+    bool pending = false;
+    double E = 0.0, sigma = 0.0, tau = 0.0;
+    int next = 0;
+  };
+  std::vector<Guard> guard(b->count);
+  for (int i = 0; i < b->count; ++i) {
+    const int a = b->ctx[i]->pb.adapt_every;
+    if (a > 0) guard[i].next = (b->ctx[i]->stats.steps / a + 1) * a;
+  }
+  auto push_shift = [&](int i) -> op_status {
+    op_ctx *c = b->ctx[i];
+    const float shift = (float)(c->g.cdiag + c->sigma);
+    const double tau = c->tau;
+    OP_CUDA(cudaMemcpyAsync(&b->d_prob[i].shift, &shift, sizeof(float), cudaMemcpyHostToDevice,
+                            b->st));
+    OP_CUDA(cudaMemcpyAsync(&b->d_prob[i].tau, &tau, sizeof(double), cudaMemcpyHostToDevice,
+                            b->st));
+    return OP_OK;
+  };
   while (true) {
+    for (int i = 0; i < b->count; ++i) {
+      op_ctx *c = b->ctx[i];
+      Guard &gd = guard[i];
+      if (b->h_frozen[i] == 1 || c->pb.adapt_every <= 0) continue;
+      if (gd.pending) {
+        gd.pending = false;
+        if (c->E > gd.E + 1e-12 * fabs(gd.E)) {
+          c->sigma = gd.sigma;
+          c->tau = gd.tau;
+          c->stats.sigma = c->sigma;
+          c->stats.tau = c->tau;
+          c->adapt_off = 1;
+          OP_TRY(push_shift(i));
+        }
+      }
+      if (!c->adapt_off && c->stats.steps >= gd.next) {
+        gd.next = c->stats.steps + c->pb.adapt_every;
+        double ps = 0.0, pt = 0.0;
+        OP_TRY(retune_shift(c, &ps, &pt));
+        if (c->sigma != ps) {
+          gd.pending = true;
+          gd.E = c->E;
+          gd.sigma = ps;
+          gd.tau = pt;
+          OP_TRY(push_shift(i));
+        }
+      }
+    }
     // residual rule: evaluate the residual of every active problem on the host side
     conv = 0;
     for (int i = 0; i < b->count; ++i) {

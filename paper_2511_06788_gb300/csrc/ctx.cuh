@@ -38,3 +38,9 @@ struct op_ctx {
   double cg_cap; // op_solve: upper bound of the adaptive CG tolerance (from its stop rule)
   std::vector<void *> allocs;
 };
+
+namespace opevo {
+// Adaptive shift (op_problem.adapt_every): re-tune c->sigma and c->tau from the Ritz
+// values of the current U; the previous values are returned (api.cu).
+op_status retune_shift(op_ctx *c, double *prev_sigma, double *prev_tau);
+}  // namespace opevo

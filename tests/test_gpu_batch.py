@@ -115,3 +115,25 @@ def test_batch_rejects_fp64_contexts():
     with pytest.raises(pkg.OpError):
         pkg.Batch(solvers)
     solvers[0].close()
+
+
+def test_batch_solve_with_adaptive_shift():
+    """Per-problem shift re-tuning inside the batch: same eigenvalues, shifts moved,
+    and no more steps than with fixed shifts."""
+    probs, fixed = make(SHAPES)
+    _, adapt = make(SHAPES, adapt_every=50)
+    steps = {}
+    for name, solvers in (("fixed", fixed), ("adapt", adapt)):
+        with pkg.Batch(solvers, cg_iters=16) as b:
+            assert b.solve(1e-6, 4000, pkg.OP_STOP_RESIDUAL, check_every=10) == len(probs)
+            steps[name] = [b.stats(i)["steps"] for i in range(len(probs))]
+            sig = [b.stats(i)["sigma"] for i in range(len(probs))]
+        for s, P in zip(solvers, probs):
+            lam = np.linalg.eigvalsh(o.hamiltonian(P.shape, P.lo, P.hi, P.V).toarray())[: P.p]
+            np.testing.assert_allclose(s.eigenvalues(), lam, rtol=1e-5)
+        if name == "adapt":
+            assert any(a > f for a, f in zip(sig, [st.stats()["sigma"] for st in fixed]))
+    print("steps fixed", steps["fixed"], "adaptive", steps["adapt"])
+    assert sum(steps["adapt"]) <= sum(steps["fixed"])
+    for s in fixed + adapt:
+        s.close()
