@@ -188,6 +188,18 @@ const char *op_profile_name(int kind);  /* static storage; "" for an unknown kin
 op_status op_profile_read(op_ctx *ctx, int kind, double *total_ms, long long *launches);
 
 /* Free the context's device memory. NULL is allowed. */
+/* Checkpoint / resume.  The paper has no counterpart; the scheme is a one-step map,
+ * so a context restored from a checkpoint continues bit-identically: the state is
+ * U, the Step-1 warm start W, sigma, tau and the step statistics.
+ * op_checkpoint_size: bytes of a checkpoint of ctx (0 for NULL).
+ * op_checkpoint: writes the state into caller-owned host memory buf (len >= size).
+ * op_restore: loads a state written by op_checkpoint into a context of the same
+ *   problem size (n, p, ld) and precision (OP_ERR_ARG otherwise, or for a buffer
+ *   that is not a checkpoint).  Both synchronise the context's stream. */
+size_t op_checkpoint_size(const op_ctx *ctx);
+op_status op_checkpoint(op_ctx *ctx, void *buf, size_t len);
+op_status op_restore(op_ctx *ctx, const void *buf, size_t len);
+
 void op_destroy(op_ctx *ctx);
 
 /* ---------------------------------------------------------------------------

@@ -109,6 +109,9 @@ def lib():
         "op_update_workspace": (sz, [i32, i32]),
         "op_ws_status": (i32, [vp, vp]),
         "op_get_U_device": (i32, [vp, vp, i32]),
+        "op_checkpoint_size": (sz, [vp]),
+        "op_checkpoint": (i32, [vp, vp, sz]),
+        "op_restore": (i32, [vp, vp, sz]),
         "opnet_create": (i32, [P(vp), P(OpnetConfig)]),
         "opnet_param_count": (C.c_longlong, [vp]),
         "opnet_layer": (i32, [vp, i32, P(i32), P(i32), P(i32)]),
@@ -261,6 +264,17 @@ class Solver:
         check(lib().op_get_U_device(self._ctx, C.c_void_p(out.data_ptr()),
                                     OP_FP64 if dtype == torch.float64 else OP_FP32))
         return out
+
+    def checkpoint(self) -> np.ndarray:
+        """The context's state (U, W, sigma, tau, statistics) as a host byte array."""
+        buf = np.empty(int(lib().op_checkpoint_size(self._ctx)), dtype=np.uint8)
+        check(lib().op_checkpoint(self._ctx, buf.ctypes.data_as(C.c_void_p), buf.size))
+        return buf
+
+    def restore(self, buf: np.ndarray):
+        """Load a state written by checkpoint() of a context of the same size and precision."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(lib().op_restore(self._ctx, buf.ctypes.data_as(C.c_void_p), buf.size))
 
     def profile(self, enable=True):
         """Enable (and reset) or disable per-kernel event timing."""

@@ -624,6 +624,83 @@ op_status op_solve(op_ctx *c, double tol, int max_steps, int stop, op_stats *st)
   return OP_OK;
 }
 
+namespace {
+struct CkptHeader {
+  char magic[8];  // "OPEVOCK1"
+  long long n;
+  int p, ld, prec, elem;
+  double sigma, tau, sigma0, Lb, E, g_rel;
+  int adapt_off, expect_iters;
+  op_stats stats;
+};
+const char kCkptMagic[8] = {'O', 'P', 'E', 'V', 'O', 'C', 'K', '1'};
+}  // namespace
+
+size_t op_checkpoint_size(const op_ctx *c) {
+  if (!c) return 0;
+  return sizeof(CkptHeader) + 2 * (size_t)c->n * c->ld * c->elem;
+}
+
+op_status op_checkpoint(op_ctx *c, void *buf, size_t len) {
+  if (!c || !buf || len < op_checkpoint_size(c)) {
+    set_error("op_checkpoint: null argument or buffer smaller than op_checkpoint_size");
+    return OP_ERR_ARG;
+  }
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kCkptMagic, 8);
+  h.n = c->n;
+  h.p = c->p;
+  h.ld = c->ld;
+  h.prec = c->prec;
+  h.elem = c->elem;
+  h.sigma = c->sigma;
+  h.tau = c->tau;
+  h.sigma0 = c->sigma0;
+  h.Lb = c->Lb;
+  h.E = c->E;
+  h.g_rel = c->g_rel;
+  h.adapt_off = c->adapt_off;
+  h.expect_iters = c->cgw.expect_iters;
+  h.stats = c->stats;
+  const size_t blk = (size_t)c->n * c->ld * c->elem;
+  char *out = (char *)buf;
+  memcpy(out, &h, sizeof(h));
+  OP_CUDA(cudaMemcpyAsync(out + sizeof(h), c->U, blk, cudaMemcpyDeviceToHost, c->st));
+  OP_CUDA(cudaMemcpyAsync(out + sizeof(h) + blk, c->W, blk, cudaMemcpyDeviceToHost, c->st));
+  OP_CUDA(cudaStreamSynchronize(c->st));
+  return OP_OK;
+}
+
+op_status op_restore(op_ctx *c, const void *buf, size_t len) {
+  if (!c || !buf || len < sizeof(CkptHeader)) {
+    set_error("op_restore: null argument or buffer too small");
+    return OP_ERR_ARG;
+  }
+  CkptHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (memcmp(h.magic, kCkptMagic, 8) != 0 || h.n != c->n || h.p != c->p || h.ld != c->ld ||
+      h.prec != c->prec || h.elem != c->elem || len < op_checkpoint_size(c)) {
+    set_error("op_restore: not a checkpoint of a context with this size and precision");
+    return OP_ERR_ARG;
+  }
+  const size_t blk = (size_t)c->n * c->ld * c->elem;
+  const char *in = (const char *)buf;
+  OP_CUDA(cudaMemcpyAsync(c->U, in + sizeof(h), blk, cudaMemcpyHostToDevice, c->st));
+  OP_CUDA(cudaMemcpyAsync(c->W, in + sizeof(h) + blk, blk, cudaMemcpyHostToDevice, c->st));
+  OP_CUDA(cudaStreamSynchronize(c->st));
+  c->sigma = h.sigma;
+  c->tau = h.tau;
+  c->sigma0 = h.sigma0;
+  c->Lb = h.Lb;
+  c->E = h.E;
+  c->g_rel = h.g_rel;
+  c->adapt_off = h.adapt_off;
+  c->cgw.expect_iters = h.expect_iters;
+  c->stats = h.stats;
+  return OP_OK;
+}
+
 op_status op_energy(op_ctx *c, double *E) {
   if (!c || !E) {
     set_error("op_energy: null argument");
