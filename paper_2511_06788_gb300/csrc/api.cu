@@ -168,10 +168,15 @@ op_status gram_any(op_ctx *c, const T *U, const T *W, double *C, double *S, doub
 }
 
 template <typename T> op_status step_impl(op_ctx *c) {
+  NvtxRange step_range("opevo step");
   int iters = 0;
   // Step 1: W = (H + sigma)^-1 U, warm-started from the previous W
-  OP_TRY(cg_solve<T>(c->g, (const T *)c->Vt, c->sigma, (const T *)c->U, (T *)c->W, c->p, c->ld,
-                     cg_rtol_for(c), cg_max_iter(c), c->cgw, &iters, c->st));
+  {
+    NvtxRange r("step 1: CG");
+    OP_TRY(cg_solve<T>(c->g, (const T *)c->Vt, c->sigma, (const T *)c->U, (T *)c->W, c->p,
+                       c->ld, cg_rtol_for(c), cg_max_iter(c), c->cgw, &iters, c->st));
+  }
+  NvtxRange r_rest("Grams, core, update, energy");
   // inner matrices <W,U>, <W,W>, <U,U>
   prof_begin(&c->prof, PK_GRAM, c->st);
   OP_TRY(gram_any<T>(c, (const T *)c->U, (const T *)c->W, c->C, c->S, c->D));

@@ -422,6 +422,7 @@ op_status op_batch_get_tiles(op_batch *b, int *rows_per_item, int *gram_rows) {
 }
 
 op_status op_batch_step(op_batch *b, int nsteps) {
+  NvtxRange range("opevo batch step");
   if (!b || nsteps < 0) {
     set_error("op_batch_step: bad arguments");
     return OP_ERR_ARG;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "opevo.h"
@@ -119,6 +120,15 @@ inline RowShape row_shape(int ld, int vec) {
 }
 
 constexpr int kNumSMs = 152;
+
+// NVTX range over a host scope (the enqueue of one phase); profilers that record
+// NVTX attribute the phase's kernels to it.  Costs a few ns when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
