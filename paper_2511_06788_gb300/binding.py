@@ -265,6 +265,25 @@ class Solver:
                                     OP_FP64 if dtype == torch.float64 else OP_FP32))
         return out
 
+    def run_logged(self, nsteps, path, residual_every=10):
+        """Advance nsteps steps one at a time and append one JSON line per step to `path`:
+        the per-step series of §5 (energy, err_E, ||U^T U - I||_F, the G-residual,
+        CG iterations, wall-clock ms) plus the residual r every `residual_every` steps."""
+        import json
+        import time
+        with open(path, "a") as f:
+            for k in range(int(nsteps)):
+                t = time.perf_counter()
+                st = self.step(1)
+                row = {"step": st["steps"], "energy": st["energy"], "err_E": st["err_E"],
+                       "orth": st["orth"], "g_residual": st["g_residual"],
+                       "cg_iters": st["last_cg_iters"], "sigma": st["sigma"], "tau": st["tau"],
+                       "ms": 1e3 * (time.perf_counter() - t)}
+                if residual_every and st["steps"] % residual_every == 0:
+                    row["residual"] = self.residual()
+                f.write(json.dumps(row) + "\n")
+        return self.stats()
+
     def checkpoint(self) -> np.ndarray:
         """The context's state (U, W, sigma, tau, statistics) as a host byte array."""
         buf = np.empty(int(lib().op_checkpoint_size(self._ctx)), dtype=np.uint8)

@@ -59,3 +59,16 @@ def test_restore_rejects_other_sizes_and_formats():
         with pytest.raises(pkg.OpError):
             a.restore(ck[: ck.size // 2])  # truncated
         a.restore(ck)
+
+
+def test_run_logged_writes_the_per_step_series(tmp_path):
+    import json
+    P = syn.wells_3d(10, 8, 3, 0)
+    log = tmp_path / "run.jsonl"
+    with pkg.Solver(P.shape, P.lo, P.hi, P.V, syn.gaussian_block(0, P.n, P.p), P.p,
+                    prec="fp32") as s:
+        s.run_logged(6, str(log), residual_every=3)
+    rows = [json.loads(x) for x in log.read_text().splitlines()]
+    assert [r["step"] for r in rows] == [1, 2, 3, 4, 5, 6]
+    assert all(b["energy"] <= a["energy"] for a, b in zip(rows, rows[1:]))
+    assert "residual" in rows[2] and "residual" in rows[5] and "residual" not in rows[0]
