@@ -57,10 +57,15 @@ ALGO_BYTES = {
         "energy": lambda n, p, s: n * s * (p + 1),         # read U, V
     },
 }
+# FP64 mode: algorithmic flops per launch of the FP64-pipe-bound groups (C = W^T U in
+# full, S and D one triangle each; the update [U W] [KU; KW] is n x 2p x p)
+FP64_FLOPS = {"gram": lambda n, p: 4 * n * p * p, "update": lambda n, p: 4 * n * p * p}
+FP64_TFLOPS = 1.25  # GB300 nominal FP64 (non-tensor) rate
 KERNEL_NAME = {("cg_apply", "fp32"): "k_cg_tma", ("cg_axpy", "fp32"): "k_cg_wr",
                ("cg_apply", "fp64"): "k_cg_apply", ("cg_axpy", "fp64"): "k_cg_axpy",
                ("cg_dir", "fp64"): "k_cg_dir", ("gram", "fp32"): "k_gram_tc",
-               ("update", "fp32"): "k_update_tc"}
+               ("update", "fp32"): "k_update_tc", ("gram", "fp64"): "k_gram<double>",
+               ("update", "fp64"): "k_update<double>"}
 
 
 def algo_bytes(group, prec, n, p, s, launches, solves):
@@ -305,14 +310,28 @@ def run_ours(args):
     algo = algo_bytes(dom, args.prec, n, p, s_el, cnt, args.steps)
     achieved = algo / avg_s / 1e9
     traffic = None
-    key = (dom, args.prec)
+    # the CG, stencil and energy kernels of the TF32 mode are the FP32 mode's
+    key = (dom, "fp32" if args.prec == "mix_tf32" and dom.startswith(("cg_", "energy"))
+           else args.prec)
     if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_source_sha(dom, args.prec):
         traffic = NCU_TRAFFIC[key][0]
-    roofline = {"bound": "hbm", "kernel": KERNEL_NAME.get((dom, args.prec), dom),
-                "group": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
-                "algo_bytes_per_launch": algo, "avg_launch_ms": 1e3 * avg_s,
-                "share_of_step_time": tot_ms / ms}
+    if args.prec == "fp64" and dom in FP64_FLOPS:
+        # FP64 Gram and update run on the FP64 pipe (about 2 DFMA / clock / SM on GB300):
+        # roofline against the nominal FP64 rate, algorithmic flops per launch
+        flops = FP64_FLOPS[dom](n, p)
+        fa = flops / avg_s / 1e12
+        roofline = {"bound": "alu", "kernel": KERNEL_NAME.get((dom, args.prec), dom),
+                    "group": dom, "achieved": fa, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                    "frac": fa / FP64_TFLOPS, "traffic": None,
+                    "peak_source": "nominal GB300 FP64 rate (not measured)",
+                    "algo_flops_per_launch": flops, "avg_launch_ms": 1e3 * avg_s,
+                    "share_of_step_time": tot_ms / ms}
+    else:
+        roofline = {"bound": "hbm", "kernel": KERNEL_NAME.get((dom, args.prec), dom),
+                    "group": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_kind,
+                    "algo_bytes_per_launch": algo, "avg_launch_ms": 1e3 * avg_s,
+                    "share_of_step_time": tot_ms / ms}
     kernel_times = {k: {"ms": round(v[0], 3), "groups": v[1]} for k, v in prof.items() if v[1]}
 
     # end to end through the public API with host buffers (pinned), copies inside
