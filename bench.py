@@ -554,6 +554,61 @@ def run_batch_ttr(args):
     return 0
 
 
+def run_c3(args):
+    """The 128^3 x 1024 configuration at full size (harmonic trap plus 32 wells on
+    [-8, 8]^3): one step of each precision mode from the same raw U0 (drawn on the
+    device from a seeded torch generator: 2.1e9 Gaussians), with Step 1 to a fixed CG
+    tolerance; the FP32 and TF32 results are compared with the FP64 GPU step.  Reports
+    set-up and step times per mode."""
+    import torch
+
+    import paper_2511_06788_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P = syn.wells_3d(128, 1024, 32, seed=rank)
+    V_d = torch.from_numpy(P.V).to(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(rank)
+    U0 = torch.randn(P.n, P.p, dtype=torch.float64, device=dev, generator=gen)
+    rtol = {"fp64": 1e-10, "fp32": 1e-6, "mix_tf32": 1e-6}
+    rows, U64 = {}, None
+    for prec in ("fp64", "fp32", "mix_tf32"):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s = pkg.Solver(P.shape, P.lo, P.hi, V_d, U0, P.p, prec=prec, device=True,
+                       cg_rtol=rtol[prec])
+        t_init = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        st = s.step(1)
+        t_step = time.perf_counter() - t0
+        U = s.get_U_device(torch.float64)
+        s.close()
+        row = {"init_s": t_init, "step_s": t_step, "energy": st["energy"], "orth": st["orth"],
+               "cg_iters": st["last_cg_iters"]}
+        if prec == "fp64":
+            U64 = U
+        else:
+            row["max_dU_rel_vs_fp64"] = float((U - U64).abs().max() / U64.abs().max())
+            row["dE_rel_vs_fp64"] = abs(st["energy"] - rows["fp64"]["energy"]) / abs(
+                rows["fp64"]["energy"])
+            row["step_speedup_vs_fp64"] = rows["fp64"]["step_s"] / t_step
+        del U
+        rows[prec] = row
+        torch.cuda.empty_cache()
+    if rank == 0:
+        line = {"metric": "one step, 128^3 x 1024", "value": rows["fp32"]["step_s"], "unit": "s",
+                "n_gpus": 1, "higher_is_better": False, "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "3d_wells_128^3_p1024", "n": P.n, "p": P.p,
+                           "cg_rtol": rtol, "timing": "host wall clock of op_init_device and "
+                           "of one op_step"},
+                "modes": rows}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_warmstart(args):
     """Learned warm start on 48^3, p = 64 (V = 4-16 Gaussian wells, no harmonic term).
 
@@ -753,7 +808,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="3d_wells_64",
-                    choices=["3d_wells_64", "batch64", "warmstart48", "ttr64", "batch64-ttr"])
+                    choices=["3d_wells_64", "batch64", "warmstart48", "ttr64", "batch64-ttr",
+                             "c3"])
     ap.add_argument("--bttr-tol", type=float, default=1e-6)
     ap.add_argument("--bttr-cap", type=int, default=3000)
     ap.add_argument("--ttr-fp64-count", type=int, default=8)
@@ -783,6 +839,8 @@ def main():
         return run_ttr(args)
     if args.workload == "batch64-ttr":
         return run_batch_ttr(args)
+    if args.workload == "c3":
+        return run_c3(args)
     return run_ours(args)
 
 
