@@ -148,10 +148,16 @@ int cg_max_iter(op_ctx *c) { return c->pb.cg_max_iter > 0 ? c->pb.cg_max_iter : 
 
 template <typename T> op_status energy_impl(op_ctx *c) {
   OP_TRY(launch_quad<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, c->ld, c->part, c->dsc + 4,
-                        c->st));
+                        c->st, c->dev_err));
   OP_CUDA(cudaMemcpyAsync(c->hsc + 4, c->dsc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                           c->st));
+  OP_CUDA(cudaMemcpyAsync(c->hpin_int + 1, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost,
+                          c->st));
   OP_CUDA(cudaStreamSynchronize(c->st));
+  if (c->hpin_int[1]) {
+    set_error("a kernel gave up a bounded device wait");
+    return OP_ERR_TIMEOUT;
+  }
   c->E = 0.5 * c->hsc[4];
   c->stats.energy = c->E;
   return OP_OK;
@@ -204,7 +210,7 @@ template <typename T> op_status step_impl(op_ctx *c) {
   // E(U^{n+1}) for Algorithm 1's err_E
   prof_begin(&c->prof, PK_ENERGY, c->st);
   OP_TRY(launch_quad<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, c->ld, c->part, c->dsc + 4,
-                        c->st));
+                        c->st, c->dev_err));
   prof_end(&c->prof, c->st);
   OP_CUDA(cudaMemcpyAsync(c->hsc, c->dsc, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   OP_CUDA(cudaMemcpyAsync(c->hpin_int, c->core_ws, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -212,7 +218,7 @@ template <typename T> op_status step_impl(op_ctx *c) {
   OP_CUDA(cudaStreamSynchronize(c->st));
   prof_harvest(&c->prof);
   if (c->hpin_int[1]) {
-    set_error("a tensor-core kernel timed out waiting for its MMAs (bounded mbarrier wait)");
+    set_error("a kernel gave up a bounded device wait (tensor-core MMAs or TMA copies)");
     return OP_ERR_TIMEOUT;
   }
   if (*c->hpin_int) {

@@ -107,10 +107,11 @@ op_status launch_apply(const Geom &g, const T *Vt, double sigma, const T *X, T *
                        cudaStream_t st);
 
 // out[0] = sum X .* ((H + sigma) X), out[1] = sum X .* X (FP64, device); part is
-// scratch of [max_blocks][2][ld] doubles.
+// scratch of [max_blocks][2][ld] doubles.  With err (device int, set when a bounded
+// wait gave up), FP32 blocks on 3-D grids use the TMA plane-marching kernel.
 template <typename T>
 op_status launch_quad(const Geom &g, const T *Vt, double sigma, const T *X, int ld, double *part,
-                      double *out, cudaStream_t st);
+                      double *out, cudaStream_t st, int *err = nullptr);
 
 // out[0] = sum X .* X; part as above.
 template <typename T>
@@ -154,6 +155,7 @@ struct CgTmaGeom {
 };
 struct CgTmaPlan {
   CgTmaGeom tg;
+  Geom geom;
   CUtensorMap halo[3];  // 10 x 10 x 32 boxes of R, P, Q
   int grid;             // persistent CTAs (rows of the partials buffer)
 };
@@ -161,6 +163,14 @@ struct CgTmaPlan {
 bool cg_tma_eligible(const Geom &g, int ld, const void *R, const void *P, const void *Q);
 op_status cg_tma_prepare(const Geom &g, double sigma, int ld, const float *R, const float *P,
                          const float *Q, CgTmaPlan *plan);
+// R = U - A W (A = H + sigma of the plan); part[grid][2][ld] = (||R||^2, ||U||^2); resets
+// the CG control words ctl[1..3].
+op_status cg_tma_init(const CgTmaPlan &plan, const float *Vt, const float *U, const float *W,
+                      float *R, double *part, int *ctl, int *err, cudaStream_t st);
+// part[grid][2][ld] = (X . (H + sigma) X, X . X) for FP32 blocks on 3-D grids; *grid
+// receives the number of partial rows.
+op_status tma_quad(const Geom &g, double sigma, int ld, const float *Vt, const float *X,
+                   double *part, int *err, int *grid, cudaStream_t st);
 // Pn = R (first) or R + beta Po, Po = P (po 0) or Q (po 1); part[grid][ld] = Pn . A Pn.
 op_status cg_tma_p(const CgTmaPlan &plan, bool first, int po, float *Pn, const float *Vt,
                    const double *beta, const int *nact_prev, double *part, int *err,

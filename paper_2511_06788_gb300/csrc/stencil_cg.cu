@@ -506,11 +506,20 @@ op_status launch_apply(const Geom &g, const T *Vt, double sigma, const T *X, T *
 
 template <typename T>
 op_status launch_quad(const Geom &g, const T *Vt, double sigma, const T *X, int ld, double *part,
-                      double *out, cudaStream_t st) {
-  RowShape s = row_shape(ld, Pack<T>::N);
-  const int nb = grid_blocks(g.n, s.rows);
-  k_quad<T><<<dim3(nb, s.gy), s.block, 0, st>>>(g, Vt, (T)(g.cdiag + sigma), X, ld, part);
-  count_launch();
+                      double *out, cudaStream_t st, int *err) {
+  int nb = 0;
+  bool tma = false;
+  if constexpr (std::is_same<T, float>::value)
+    tma = err != nullptr && cg_tma_eligible(g, ld, X, X, X);
+  if (tma) {
+    if constexpr (std::is_same<T, float>::value)
+      OP_TRY(tma_quad(g, sigma, ld, Vt, X, part, err, &nb, st));
+  } else {
+    RowShape s = row_shape(ld, Pack<T>::N);
+    nb = grid_blocks(g.n, s.rows);
+    k_quad<T><<<dim3(nb, s.gy), s.block, 0, st>>>(g, Vt, (T)(g.cdiag + sigma), X, ld, part);
+    count_launch();
+  }
   k_fin_cols<<<warp_blocks(2 * ld), 256, 0, st>>>(part, nb, 2, ld, colsum_area(part, ld));
   count_launch();
   k_fin_total<<<1, 256, 0, st>>>(colsum_area(part, ld), 2, ld, out);
@@ -580,7 +589,7 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
   bool tma = false;
   int nb_p = nb;
   if constexpr (kFused) {
-    tma = cg_tma_eligible(g, ld, R, P, Q);
+    tma = cg_tma_eligible(g, ld, R, P, Q) && cg_tma_eligible(g, ld, U, W, W);
     if (tma) {
       OP_TRY(cg_tma_prepare(g, sigma, ld, R, P, Q, &plan));
       nb_p = plan.grid;
@@ -588,12 +597,18 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
   }
 
   prof_begin(w.prof, PK_CG_INIT, st);
-  if (kFused)
-    k_cg_init<T, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
-  else
-    k_cg_init<T, true><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
-  count_launch();
-  k_cg_fin_init<<<fb, 256, 0, st>>>(w.part, nb, ld, p, rtol * rtol, w.state, w.active, ctl);
+  if (tma) {
+    if constexpr (kFused)
+      OP_TRY(cg_tma_init(plan, Vt, U, W, R, w.part, ctl, ctl + 3, st));
+  } else {
+    if (kFused)
+      k_cg_init<T, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+    else
+      k_cg_init<T, true><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+    count_launch();
+  }
+  k_cg_fin_init<<<fb, 256, 0, st>>>(w.part, tma ? nb_p : nb, ld, p, rtol * rtol, w.state,
+                                     w.active, ctl);
   count_launch();
   prof_end(w.prof, st);
   OP_LAUNCH("k_cg_init");
@@ -1064,7 +1079,7 @@ void prof_harvest(Prof *p) {
   template op_status launch_apply<T>(const Geom &, const T *, double, const T *, T *, int,    \
                                      cudaStream_t);                                            \
   template op_status launch_quad<T>(const Geom &, const T *, double, const T *, int, double *, \
-                                    double *, cudaStream_t);                                   \
+                                    double *, cudaStream_t, int *);                            \
   template op_status cg_solve<T>(const Geom &, const T *, double, const T *, T *, int, int,   \
                                  double, int, CGWork &, int *, cudaStream_t);                  \
   template op_status launch_pad_copy<T>(long long, int, int, const double *, T *,             \

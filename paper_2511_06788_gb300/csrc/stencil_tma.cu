@@ -14,8 +14,10 @@
 // plane z, so every element is fetched from L2 about 1.6 times (halo) instead of
 // seven.
 //
-//   k_cg_tma<FIRST>:  Pn = R (+ beta Po unless FIRST), the R box converted in
-//                     place; part = Pn . (H + sigma) Pn per column.
+//   k_cg_tma<M_P_FIRST / M_P>:  Pn = R (+ beta Po), the R box converted in place;
+//                     part = Pn . (H + sigma) Pn per column.
+//   k_cg_tma<M_INIT>: the CG start R = U - (H + sigma) W; part = (||R||^2, ||U||^2).
+//   k_cg_tma<M_QUAD>: the energy sums part = (X . (H + sigma) X, X . X).
 // V of the next plane to compute is loaded into registers one plane ahead, so
 // its latency overlaps the wait for the next box.
 //
@@ -41,12 +43,21 @@ constexpr int kHaloBytes = kHaloV * 16;     // 12800
 constexpr int kThreads = 256;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
-template <bool FIRST> struct Slot {  // R box (and the Po box unless FIRST)
-  static constexpr int bytes = FIRST ? kHaloBytes : 2 * kHaloBytes;
+// Modes of the plane-marching kernel (the box loaded per plane, what is computed):
+//   M_P_FIRST  R box:         Pn = R;            part = Pn . A Pn
+//   M_P        R and Po box:  Pn = R + beta Po;  part = Pn . A Pn
+//   M_QUAD     X box:         part = (X . A X, X . X)
+//   M_INIT     W box:         R = U - A W;       part = (R . R, U . U)
+// with A = H + sigma (the shift of the geometry passed in).
+enum { M_P_FIRST = 0, M_P = 1, M_QUAD = 2, M_INIT = 3 };
+
+template <int MODE> struct Slot {
+  static constexpr int bytes = MODE == M_P ? 2 * kHaloBytes : kHaloBytes;
+  static constexpr int ncomp = MODE >= M_QUAD ? 2 : 1;  // partial sums per column
 };
 
-template <bool FIRST, int NS> constexpr int smem_bytes() {
-  return 128 + NS * Slot<FIRST>::bytes + 2 * NS * 8;
+template <int MODE, int NS> constexpr int smem_bytes() {
+  return 128 + NS * Slot<MODE>::bytes + 2 * NS * 8;
 }
 
 // Work items: (slab, column), column = chunk * ntiles + tile; slab s of S covers
@@ -84,22 +95,22 @@ struct Cursor {
 };
 
 // Thread 0: start load number L (slot L % NS) for the cursor's next plane.
-template <bool FIRST, int NS>
+template <int MODE, int NS>
 __device__ __forceinline__ void issue(const CgTmaGeom &tg, const Cursor &cur, long long L,
                                       unsigned char *slots, uint64_t *bars, const CUtensorMap *mA,
                                       const CUtensorMap *mB) {
   const int plane = cur.za - 1 + cur.j;
   const int slot = (int)(L % NS);
-  unsigned char *s = slots + slot * Slot<FIRST>::bytes;
+  unsigned char *s = slots + slot * Slot<MODE>::bytes;
   uint64_t *bar = bars + slot;
   if (plane < 0 || plane >= tg.nz) {  // outside the grid: zero plane, no copy
     tma::bar_arrive(bar);
     return;
   }
-  tma::bar_expect(bar, Slot<FIRST>::bytes);
+  tma::bar_expect(bar, Slot<MODE>::bytes);
   const int c0 = cur.chunk * kPC;
   tma::load_4d(s, mA, c0, cur.x0 - 1, cur.y0 - 1, plane, bar);
-  if (!FIRST) tma::load_4d(s + kHaloBytes, mB, c0, cur.x0 - 1, cur.y0 - 1, plane, bar);
+  if (MODE == M_P) tma::load_4d(s + kHaloBytes, mB, c0, cur.x0 - 1, cur.y0 - 1, plane, bar);
 }
 
 __device__ __forceinline__ float4 f4_zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -111,7 +122,7 @@ __device__ __forceinline__ void compute_sync() {
 
 // Add acc, summed over the 32 threads sharing its columns (FP64, fixed order), to
 // prow[chunk * 32 + c]; resets acc.  Compute warps only.
-__device__ __forceinline__ void flush(float (&acc)[4], int chunk, int ld, double *prow,
+__device__ __forceinline__ void flush(float *acc, int chunk, int ld, double *prow,
                                       double (*red)[kPC]) {
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   double d[4];
@@ -141,14 +152,16 @@ __device__ __forceinline__ void flush(float (&acc)[4], int chunk, int ld, double
 // plane as soon as every compute warp has released it ("empty" barrier, 8
 // arrivals), and the compute warps wait for the data on the slot's "full"
 // barrier (1 arrival + the copy's bytes).
-template <bool FIRST, int NS>
+template <int MODE, int NS>
 __global__ void __launch_bounds__(kThreads + 32, 2)
     k_cg_tma(CgTmaGeom tg, const float *__restrict__ Vt, const __grid_constant__ CUtensorMap mA,
-             const __grid_constant__ CUtensorMap mB, float *__restrict__ Pn,
-             const double *__restrict__ beta, const int *nact_prev, double *__restrict__ part,
-             int *err) {
-  if (*nact_prev == 0) return;
-  constexpr int SB = Slot<FIRST>::bytes;
+             const __grid_constant__ CUtensorMap mB, const float *__restrict__ Uin,
+             float *__restrict__ out, const double *__restrict__ beta, const int *nact_prev,
+             double *__restrict__ part, int *ctl, int *err) {
+  if (nact_prev && *nact_prev == 0) return;
+  constexpr int SB = Slot<MODE>::bytes;
+  constexpr int NC = Slot<MODE>::ncomp;
+  constexpr bool FIRST = MODE != M_P;  // no P_old box to fold in
   extern __shared__ unsigned char dsm[];
   unsigned char *slots =
       (unsigned char *)(((uintptr_t)dsm + 127) & ~(uintptr_t)127);
@@ -159,8 +172,13 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
 
   const int tid = threadIdx.x;
   const int ld = tg.ld;
-  double *prow = part + (long long)blockIdx.x * ld;  // this CTA's partials (flush adds)
-  for (int col = tid; col < ld; col += kThreads + 32) prow[col] = 0.0;
+  double *prow = part + (long long)blockIdx.x * NC * ld;  // this CTA's partials (flush adds)
+  for (int col = tid; col < NC * ld; col += kThreads + 32) prow[col] = 0.0;
+  if (MODE == M_INIT && ctl && blockIdx.x == 0 && tid == 0) {  // CG control words
+    ctl[1] = 0;
+    ctl[2] = 0;
+    ctl[3] = 0;
+  }
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
       tma::bar_init(full + s, 1);
@@ -183,7 +201,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
         atomicExch(err, 1);
       }
       if (s_abort) break;
-      issue<FIRST, NS>(tg, prod, l, slots, full, &mA, &mB);
+      issue<MODE, NS>(tg, prod, l, slots, full, &mA, &mB);
     }
     // copies still in flight land before the CTA may exit (only the last NS can be)
     if (s_abort)
@@ -198,7 +216,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
   long long L = 0;
   float4 cp[2] = {f4_zero(), f4_zero()}, cc[2] = {f4_zero(), f4_zero()};
   float vc[2] = {0.f, 0.f};  // V of the next plane to compute
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float4 uc[2] = {f4_zero(), f4_zero()};  // its U (M_INIT)
+  float acc[NC][4] = {};
   float cf[4] = {0.f, 0.f, 0.f, 0.f};
   int chunk = -1;
   const float cx = tg.cx, cy = tg.cy, cz = tg.cz;
@@ -222,7 +241,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
       s_abort = 1;
       atomicExch(err, 1);
     }
-    if (!FIRST && in_range) {  // Pn = R + beta Po over the whole box
+    if (MODE == M_P && in_range) {  // Pn = R + beta Po over the whole box
       float4 *r = (float4 *)s;
       const float4 *po = (const float4 *)(s + kHaloBytes);
       for (int e = tid; e < kHaloV; e += kThreads) {  // e % 8 == c4
@@ -265,11 +284,31 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
         q.y = d * c.y - cx * (l.y + r.y) - cy * (dn.y + up.y) - cz * (cp[i].y + cn[i].y);
         q.z = d * c.z - cx * (l.z + r.z) - cy * (dn.z + up.z) - cz * (cp[i].z + cn[i].z);
         q.w = d * c.w - cx * (l.w + r.w) - cy * (dn.w + up.w) - cz * (cp[i].w + cn[i].w);
-        *reinterpret_cast<float4 *>(Pn + pt * ld + col) = c;
-        acc[0] += c.x * q.x;
-        acc[1] += c.y * q.y;
-        acc[2] += c.z * q.z;
-        acc[3] += c.w * q.w;
+        if (MODE == M_INIT) {
+          const float4 u = uc[i];
+          const float4 rr = make_float4(u.x - q.x, u.y - q.y, u.z - q.z, u.w - q.w);
+          *reinterpret_cast<float4 *>(out + pt * ld + col) = rr;
+          acc[0][0] += rr.x * rr.x;
+          acc[0][1] += rr.y * rr.y;
+          acc[0][2] += rr.z * rr.z;
+          acc[0][3] += rr.w * rr.w;
+          acc[NC - 1][0] += u.x * u.x;
+          acc[NC - 1][1] += u.y * u.y;
+          acc[NC - 1][2] += u.z * u.z;
+          acc[NC - 1][3] += u.w * u.w;
+        } else {
+          if (MODE != M_QUAD) *reinterpret_cast<float4 *>(out + pt * ld + col) = c;
+          acc[0][0] += c.x * q.x;
+          acc[0][1] += c.y * q.y;
+          acc[0][2] += c.z * q.z;
+          acc[0][3] += c.w * q.w;
+          if (MODE == M_QUAD) {
+            acc[NC - 1][0] += c.x * c.x;
+            acc[NC - 1][1] += c.y * c.y;
+            acc[NC - 1][2] += c.z * c.z;
+            acc[NC - 1][3] += c.w * c.w;
+          }
+        }
       }
     }
     // slot L - 1 is no longer read by this warp: release it to the producer
@@ -285,7 +324,11 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
       for (int i = 0; i < 2; ++i) {
         const int y = w.y0 + ya + i;
         const long long pt = ((long long)plane * tg.ny + y) * tg.nx + x;
-        vc[i] = (x < tg.nx && y < tg.ny) ? __ldg(Vt + pt) : 0.f;
+        const bool okp = x < tg.nx && y < tg.ny;
+        vc[i] = okp ? __ldg(Vt + pt) : 0.f;
+        if (MODE == M_INIT)
+          uc[i] = (okp && col < ld) ? __ldg(reinterpret_cast<const float4 *>(Uin + pt * ld + col))
+                                    : f4_zero();
       }
     }
 #pragma unroll
@@ -298,7 +341,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
     ++L;
     if (last) {
       const int nc = cons.valid(tg) ? cons.chunk : -1;
-      if (nc != chunk) flush(acc, chunk, ld, prow, red);
+      if (nc != chunk)
+        for (int q = 0; q < NC; ++q) flush(acc[q], chunk, ld, prow + q * ld, red);
     }
   }
 }
@@ -306,23 +350,57 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
 // Ring depth (up to NS - 1 planes in flight): 4 slots of 25.6 KB, two CTAs per SM.
 constexpr int kNS = 4;
 
-template <bool FIRST>
+template <int MODE>
 int resident_ctas() {
   static int cached = -1;
   static std::mutex mu;
   std::lock_guard<std::mutex> lk(mu);
   if (cached < 0) {
-    const int bytes = smem_bytes<FIRST, kNS>();
-    cudaFuncSetAttribute(k_cg_tma<FIRST, kNS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         bytes);
+    const int bytes = smem_bytes<MODE, kNS>();
+    cudaFuncSetAttribute(k_cg_tma<MODE, kNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_tma<FIRST, kNS>,
-                                                      kThreads + 32, bytes) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_tma<MODE, kNS>, kThreads + 32,
+                                                      bytes) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     cached = per_sm;
   }
   return cached;
+}
+
+// Geometry and persistent grid shared by every mode (so that all of them write the
+// same number of partial rows).  One wave of resident CTAs of the largest mode:
+// whole columns (S = 1) when there are at least as many columns as CTAs, else each
+// column cut into S z-slabs.
+void plan_geometry(const Geom &g, double sigma, int ld, CgTmaGeom *tg, int *grid) {
+  tg->nx = g.nx;
+  tg->ny = g.ny;
+  tg->nz = g.nz;
+  tg->ld = ld;
+  tg->ntx = (g.nx + kTX - 1) / kTX;
+  tg->nty = (g.ny + kTY - 1) / kTY;
+  tg->nch = (ld + kPC - 1) / kPC;
+  tg->shift = (float)(g.cdiag + sigma);
+  tg->cx = (float)g.c[0];
+  tg->cy = (float)g.c[1];
+  tg->cz = (float)g.c[2];
+  int per_sm = resident_ctas<M_P>();
+  const int others[3] = {resident_ctas<M_P_FIRST>(), resident_ctas<M_QUAD>(),
+                         resident_ctas<M_INIT>()};
+  for (int o : others) per_sm = o < per_sm ? o : per_sm;
+  const long long cap = (long long)kNumSMs * per_sm;
+  const long long ncols = (long long)tg->nch * tg->ntx * tg->nty;
+  long long S = ncols < cap ? cap / ncols : 1;
+  if (S > g.nz) S = g.nz;
+  tg->slabs = (int)S;
+  tg->items = ncols * S;
+  *grid = (int)(tg->items < cap ? tg->items : cap);
+}
+
+op_status halo_map(const Geom &g, int ld, const float *X, CUtensorMap *map) {
+  const uint64_t dims[4] = {(uint64_t)ld, (uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz};
+  const uint32_t halo[4] = {kPC, kBX, kBY, 1};
+  return tma_map_4d_f32(map, X, dims, halo);
 }
 
 }  // namespace
@@ -334,34 +412,11 @@ bool cg_tma_eligible(const Geom &g, int ld, const void *R, const void *P, const 
 
 op_status cg_tma_prepare(const Geom &g, double sigma, int ld, const float *R, const float *P,
                          const float *Q, CgTmaPlan *plan) {
-  CgTmaGeom &tg = plan->tg;
-  tg.nx = g.nx;
-  tg.ny = g.ny;
-  tg.nz = g.nz;
-  tg.ld = ld;
-  tg.ntx = (g.nx + kTX - 1) / kTX;
-  tg.nty = (g.ny + kTY - 1) / kTY;
-  tg.nch = (ld + kPC - 1) / kPC;
-  tg.shift = (float)(g.cdiag + sigma);
-  tg.cx = (float)g.c[0];
-  tg.cy = (float)g.c[1];
-  tg.cz = (float)g.c[2];
-  const uint64_t dims[4] = {(uint64_t)ld, (uint64_t)g.nx, (uint64_t)g.ny, (uint64_t)g.nz};
-  const uint32_t halo[4] = {kPC, kBX, kBY, 1};
-  OP_TRY(tma_map_4d_f32(&plan->halo[0], R, dims, halo));
-  OP_TRY(tma_map_4d_f32(&plan->halo[1], P, dims, halo));
-  OP_TRY(tma_map_4d_f32(&plan->halo[2], Q, dims, halo));
-  // one wave of resident CTAs: whole columns (S = 1) when there are at least as
-  // many columns as CTAs, else each column cut into S z-slabs
-  const long long cap = (long long)kNumSMs * (resident_ctas<false>() < resident_ctas<true>()
-                                                  ? resident_ctas<false>()
-                                                  : resident_ctas<true>());
-  const long long ncols = (long long)tg.nch * tg.ntx * tg.nty;
-  long long S = ncols < cap ? cap / ncols : 1;
-  if (S > g.nz) S = g.nz;
-  tg.slabs = (int)S;
-  tg.items = ncols * S;
-  plan->grid = (int)(tg.items < cap ? tg.items : cap);
+  plan_geometry(g, sigma, ld, &plan->tg, &plan->grid);
+  plan->geom = g;
+  OP_TRY(halo_map(g, ld, R, &plan->halo[0]));
+  OP_TRY(halo_map(g, ld, P, &plan->halo[1]));
+  OP_TRY(halo_map(g, ld, Q, &plan->halo[2]));
   return OP_OK;
 }
 
@@ -371,13 +426,37 @@ op_status cg_tma_p(const CgTmaPlan &plan, bool first, int po, float *Pn, const f
   const CUtensorMap &mR = plan.halo[0];
   const CUtensorMap &mPo = plan.halo[po == 0 ? 1 : 2];
   if (first)
-    k_cg_tma<true, kNS><<<plan.grid, kThreads + 32, smem_bytes<true, kNS>(), st>>>(
-        plan.tg, Vt, mR, mPo, Pn, beta, nact_prev, part, err);
+    k_cg_tma<M_P_FIRST, kNS><<<plan.grid, kThreads + 32, smem_bytes<M_P_FIRST, kNS>(), st>>>(
+        plan.tg, Vt, mR, mPo, nullptr, Pn, beta, nact_prev, part, nullptr, err);
   else
-    k_cg_tma<false, kNS><<<plan.grid, kThreads + 32, smem_bytes<false, kNS>(), st>>>(
-        plan.tg, Vt, mR, mPo, Pn, beta, nact_prev, part, err);
+    k_cg_tma<M_P, kNS><<<plan.grid, kThreads + 32, smem_bytes<M_P, kNS>(), st>>>(
+        plan.tg, Vt, mR, mPo, nullptr, Pn, beta, nact_prev, part, nullptr, err);
   count_launch();
   OP_LAUNCH("k_cg_tma");
+  return OP_OK;
+}
+
+op_status cg_tma_init(const CgTmaPlan &plan, const float *Vt, const float *U, const float *W,
+                      float *R, double *part, int *ctl, int *err, cudaStream_t st) {
+  CUtensorMap mW;
+  OP_TRY(halo_map(plan.geom, plan.tg.ld, W, &mW));
+  k_cg_tma<M_INIT, kNS><<<plan.grid, kThreads + 32, smem_bytes<M_INIT, kNS>(), st>>>(
+      plan.tg, Vt, mW, mW, U, R, nullptr, nullptr, part, ctl, err);
+  count_launch();
+  OP_LAUNCH("k_cg_tma<init>");
+  return OP_OK;
+}
+
+op_status tma_quad(const Geom &g, double sigma, int ld, const float *Vt, const float *X,
+                   double *part, int *err, int *grid, cudaStream_t st) {
+  CgTmaGeom tg;
+  plan_geometry(g, sigma, ld, &tg, grid);
+  CUtensorMap mX;
+  OP_TRY(halo_map(g, ld, X, &mX));
+  k_cg_tma<M_QUAD, kNS><<<*grid, kThreads + 32, smem_bytes<M_QUAD, kNS>(), st>>>(
+      tg, Vt, mX, mX, nullptr, nullptr, nullptr, nullptr, part, nullptr, err);
+  count_launch();
+  OP_LAUNCH("k_cg_tma<quad>");
   return OP_OK;
 }
 
