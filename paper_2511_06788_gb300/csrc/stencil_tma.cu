@@ -54,6 +54,9 @@ enum { M_P_FIRST = 0, M_P = 1, M_QUAD = 2, M_INIT = 3 };
 template <int MODE> struct Slot {
   static constexpr int bytes = MODE == M_P ? 2 * kHaloBytes : kHaloBytes;
   static constexpr int ncomp = MODE >= M_QUAD ? 2 : 1;  // partial sums per column
+  // ring depth (up to ns - 1 planes in flight): 4 slots of two boxes or 8 of one box,
+  // about 100 KB either way, two CTAs per SM
+  static constexpr int ns = MODE == M_P ? 4 : 8;
 };
 
 template <int MODE, int NS> constexpr int smem_bytes() {
@@ -347,8 +350,6 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
   }
 }
 
-// Ring depth (up to NS - 1 planes in flight): 4 slots of 25.6 KB, two CTAs per SM.
-constexpr int kNS = 4;
 
 template <int MODE>
 int resident_ctas() {
@@ -356,10 +357,11 @@ int resident_ctas() {
   static std::mutex mu;
   std::lock_guard<std::mutex> lk(mu);
   if (cached < 0) {
-    const int bytes = smem_bytes<MODE, kNS>();
-    cudaFuncSetAttribute(k_cg_tma<MODE, kNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    constexpr int NS = Slot<MODE>::ns;
+    const int bytes = smem_bytes<MODE, NS>();
+    cudaFuncSetAttribute(k_cg_tma<MODE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_tma<MODE, kNS>, kThreads + 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_tma<MODE, NS>, kThreads + 32,
                                                       bytes) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
@@ -426,10 +428,10 @@ op_status cg_tma_p(const CgTmaPlan &plan, bool first, int po, float *Pn, const f
   const CUtensorMap &mR = plan.halo[0];
   const CUtensorMap &mPo = plan.halo[po == 0 ? 1 : 2];
   if (first)
-    k_cg_tma<M_P_FIRST, kNS><<<plan.grid, kThreads + 32, smem_bytes<M_P_FIRST, kNS>(), st>>>(
+    k_cg_tma<M_P_FIRST, 8><<<plan.grid, kThreads + 32, smem_bytes<M_P_FIRST, 8>(), st>>>(
         plan.tg, Vt, mR, mPo, nullptr, Pn, beta, nact_prev, part, nullptr, err);
   else
-    k_cg_tma<M_P, kNS><<<plan.grid, kThreads + 32, smem_bytes<M_P, kNS>(), st>>>(
+    k_cg_tma<M_P, 4><<<plan.grid, kThreads + 32, smem_bytes<M_P, 4>(), st>>>(
         plan.tg, Vt, mR, mPo, nullptr, Pn, beta, nact_prev, part, nullptr, err);
   count_launch();
   OP_LAUNCH("k_cg_tma");
@@ -440,7 +442,7 @@ op_status cg_tma_init(const CgTmaPlan &plan, const float *Vt, const float *U, co
                       float *R, double *part, int *ctl, int *err, cudaStream_t st) {
   CUtensorMap mW;
   OP_TRY(halo_map(plan.geom, plan.tg.ld, W, &mW));
-  k_cg_tma<M_INIT, kNS><<<plan.grid, kThreads + 32, smem_bytes<M_INIT, kNS>(), st>>>(
+  k_cg_tma<M_INIT, 8><<<plan.grid, kThreads + 32, smem_bytes<M_INIT, 8>(), st>>>(
       plan.tg, Vt, mW, mW, U, R, nullptr, nullptr, part, ctl, err);
   count_launch();
   OP_LAUNCH("k_cg_tma<init>");
@@ -453,7 +455,7 @@ op_status tma_quad(const Geom &g, double sigma, int ld, const float *Vt, const f
   plan_geometry(g, sigma, ld, &tg, grid);
   CUtensorMap mX;
   OP_TRY(halo_map(g, ld, X, &mX));
-  k_cg_tma<M_QUAD, kNS><<<*grid, kThreads + 32, smem_bytes<M_QUAD, kNS>(), st>>>(
+  k_cg_tma<M_QUAD, 8><<<*grid, kThreads + 32, smem_bytes<M_QUAD, 8>(), st>>>(
       tg, Vt, mX, mX, nullptr, nullptr, nullptr, nullptr, part, nullptr, err);
   count_launch();
   OP_LAUNCH("k_cg_tma<quad>");
