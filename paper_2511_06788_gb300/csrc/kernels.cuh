@@ -155,7 +155,6 @@ struct CgTmaGeom {
 };
 struct CgTmaPlan {
   CgTmaGeom tg;
-  Geom geom;
   CUtensorMap halo[3];  // 10 x 10 x 32 boxes of R, P, Q
   int grid;             // persistent CTAs (rows of the partials buffer)
 };
@@ -163,10 +162,6 @@ struct CgTmaPlan {
 bool cg_tma_eligible(const Geom &g, int ld, const void *R, const void *P, const void *Q);
 op_status cg_tma_prepare(const Geom &g, double sigma, int ld, const float *R, const float *P,
                          const float *Q, CgTmaPlan *plan);
-// R = U - A W (A = H + sigma of the plan); part[grid][2][ld] = (||R||^2, ||U||^2); resets
-// the CG control words ctl[1..3].
-op_status cg_tma_init(const CgTmaPlan &plan, const float *Vt, const float *U, const float *W,
-                      float *R, double *part, int *ctl, int *err, cudaStream_t st);
 // part[grid][2][ld] = (X . (H + sigma) X, X . X) for FP32 blocks on 3-D grids; *grid
 // receives the number of partial rows.
 op_status tma_quad(const Geom &g, double sigma, int ld, const float *Vt, const float *X,

@@ -589,7 +589,7 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
   bool tma = false;
   int nb_p = nb;
   if constexpr (kFused) {
-    tma = cg_tma_eligible(g, ld, R, P, Q) && cg_tma_eligible(g, ld, U, W, W);
+    tma = cg_tma_eligible(g, ld, R, P, Q);
     if (tma) {
       OP_TRY(cg_tma_prepare(g, sigma, ld, R, P, Q, &plan));
       nb_p = plan.grid;
@@ -597,18 +597,13 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
   }
 
   prof_begin(w.prof, PK_CG_INIT, st);
-  if (tma) {
-    if constexpr (kFused)
-      OP_TRY(cg_tma_init(plan, Vt, U, W, R, w.part, ctl, ctl + 3, st));
-  } else {
-    if (kFused)
-      k_cg_init<T, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
-    else
-      k_cg_init<T, true><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
-    count_launch();
-  }
-  k_cg_fin_init<<<fb, 256, 0, st>>>(w.part, tma ? nb_p : nb, ld, p, rtol * rtol, w.state,
-                                     w.active, ctl);
+  // (a TMA plane-marching version of this pass measured slower than the row kernel)
+  if (kFused)
+    k_cg_init<T, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+  else
+    k_cg_init<T, true><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+  count_launch();
+  k_cg_fin_init<<<fb, 256, 0, st>>>(w.part, nb, ld, p, rtol * rtol, w.state, w.active, ctl);
   count_launch();
   prof_end(w.prof, st);
   OP_LAUNCH("k_cg_init");

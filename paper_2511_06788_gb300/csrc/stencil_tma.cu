@@ -16,7 +16,6 @@
 //
 //   k_cg_tma<M_P_FIRST / M_P>:  Pn = R (+ beta Po), the R box converted in place;
 //                     part = Pn . (H + sigma) Pn per column.
-//   k_cg_tma<M_INIT>: the CG start R = U - (H + sigma) W; part = (||R||^2, ||U||^2).
 //   k_cg_tma<M_QUAD>: the energy sums part = (X . (H + sigma) X, X . X).
 // V of the next plane to compute is loaded into registers one plane ahead, so
 // its latency overlaps the wait for the next box.
@@ -47,9 +46,8 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 //   M_P_FIRST  R box:         Pn = R;            part = Pn . A Pn
 //   M_P        R and Po box:  Pn = R + beta Po;  part = Pn . A Pn
 //   M_QUAD     X box:         part = (X . A X, X . X)
-//   M_INIT     W box:         R = U - A W;       part = (R . R, U . U)
 // with A = H + sigma (the shift of the geometry passed in).
-enum { M_P_FIRST = 0, M_P = 1, M_QUAD = 2, M_INIT = 3 };
+enum { M_P_FIRST = 0, M_P = 1, M_QUAD = 2 };
 
 template <int MODE> struct Slot {
   static constexpr int bytes = MODE == M_P ? 2 * kHaloBytes : kHaloBytes;
@@ -158,9 +156,9 @@ __device__ __forceinline__ void flush(float *acc, int chunk, int ld, double *pro
 template <int MODE, int NS>
 __global__ void __launch_bounds__(kThreads + 32, 2)
     k_cg_tma(CgTmaGeom tg, const float *__restrict__ Vt, const __grid_constant__ CUtensorMap mA,
-             const __grid_constant__ CUtensorMap mB, const float *__restrict__ Uin,
-             float *__restrict__ out, const double *__restrict__ beta, const int *nact_prev,
-             double *__restrict__ part, int *ctl, int *err) {
+             const __grid_constant__ CUtensorMap mB, float *__restrict__ out,
+             const double *__restrict__ beta, const int *nact_prev, double *__restrict__ part,
+             int *err) {
   if (nact_prev && *nact_prev == 0) return;
   constexpr int SB = Slot<MODE>::bytes;
   constexpr int NC = Slot<MODE>::ncomp;
@@ -177,11 +175,6 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
   const int ld = tg.ld;
   double *prow = part + (long long)blockIdx.x * NC * ld;  // this CTA's partials (flush adds)
   for (int col = tid; col < NC * ld; col += kThreads + 32) prow[col] = 0.0;
-  if (MODE == M_INIT && ctl && blockIdx.x == 0 && tid == 0) {  // CG control words
-    ctl[1] = 0;
-    ctl[2] = 0;
-    ctl[3] = 0;
-  }
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
       tma::bar_init(full + s, 1);
@@ -219,7 +212,6 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
   long long L = 0;
   float4 cp[2] = {f4_zero(), f4_zero()}, cc[2] = {f4_zero(), f4_zero()};
   float vc[2] = {0.f, 0.f};  // V of the next plane to compute
-  float4 uc[2] = {f4_zero(), f4_zero()};  // its U (M_INIT)
   float acc[NC][4] = {};
   float cf[4] = {0.f, 0.f, 0.f, 0.f};
   int chunk = -1;
@@ -287,30 +279,16 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
         q.y = d * c.y - cx * (l.y + r.y) - cy * (dn.y + up.y) - cz * (cp[i].y + cn[i].y);
         q.z = d * c.z - cx * (l.z + r.z) - cy * (dn.z + up.z) - cz * (cp[i].z + cn[i].z);
         q.w = d * c.w - cx * (l.w + r.w) - cy * (dn.w + up.w) - cz * (cp[i].w + cn[i].w);
-        if (MODE == M_INIT) {
-          const float4 u = uc[i];
-          const float4 rr = make_float4(u.x - q.x, u.y - q.y, u.z - q.z, u.w - q.w);
-          *reinterpret_cast<float4 *>(out + pt * ld + col) = rr;
-          acc[0][0] += rr.x * rr.x;
-          acc[0][1] += rr.y * rr.y;
-          acc[0][2] += rr.z * rr.z;
-          acc[0][3] += rr.w * rr.w;
-          acc[NC - 1][0] += u.x * u.x;
-          acc[NC - 1][1] += u.y * u.y;
-          acc[NC - 1][2] += u.z * u.z;
-          acc[NC - 1][3] += u.w * u.w;
-        } else {
-          if (MODE != M_QUAD) *reinterpret_cast<float4 *>(out + pt * ld + col) = c;
-          acc[0][0] += c.x * q.x;
-          acc[0][1] += c.y * q.y;
-          acc[0][2] += c.z * q.z;
-          acc[0][3] += c.w * q.w;
-          if (MODE == M_QUAD) {
-            acc[NC - 1][0] += c.x * c.x;
-            acc[NC - 1][1] += c.y * c.y;
-            acc[NC - 1][2] += c.z * c.z;
-            acc[NC - 1][3] += c.w * c.w;
-          }
+        if (MODE != M_QUAD) *reinterpret_cast<float4 *>(out + pt * ld + col) = c;
+        acc[0][0] += c.x * q.x;
+        acc[0][1] += c.y * q.y;
+        acc[0][2] += c.z * q.z;
+        acc[0][3] += c.w * q.w;
+        if (MODE == M_QUAD) {
+          acc[NC - 1][0] += c.x * c.x;
+          acc[NC - 1][1] += c.y * c.y;
+          acc[NC - 1][2] += c.z * c.z;
+          acc[NC - 1][3] += c.w * c.w;
         }
       }
     }
@@ -327,11 +305,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
       for (int i = 0; i < 2; ++i) {
         const int y = w.y0 + ya + i;
         const long long pt = ((long long)plane * tg.ny + y) * tg.nx + x;
-        const bool okp = x < tg.nx && y < tg.ny;
-        vc[i] = okp ? __ldg(Vt + pt) : 0.f;
-        if (MODE == M_INIT)
-          uc[i] = (okp && col < ld) ? __ldg(reinterpret_cast<const float4 *>(Uin + pt * ld + col))
-                                    : f4_zero();
+        vc[i] = (x < tg.nx && y < tg.ny) ? __ldg(Vt + pt) : 0.f;
       }
     }
 #pragma unroll
@@ -387,8 +361,7 @@ void plan_geometry(const Geom &g, double sigma, int ld, CgTmaGeom *tg, int *grid
   tg->cy = (float)g.c[1];
   tg->cz = (float)g.c[2];
   int per_sm = resident_ctas<M_P>();
-  const int others[3] = {resident_ctas<M_P_FIRST>(), resident_ctas<M_QUAD>(),
-                         resident_ctas<M_INIT>()};
+  const int others[2] = {resident_ctas<M_P_FIRST>(), resident_ctas<M_QUAD>()};
   for (int o : others) per_sm = o < per_sm ? o : per_sm;
   const long long cap = (long long)kNumSMs * per_sm;
   const long long ncols = (long long)tg->nch * tg->ntx * tg->nty;
@@ -415,7 +388,6 @@ bool cg_tma_eligible(const Geom &g, int ld, const void *R, const void *P, const 
 op_status cg_tma_prepare(const Geom &g, double sigma, int ld, const float *R, const float *P,
                          const float *Q, CgTmaPlan *plan) {
   plan_geometry(g, sigma, ld, &plan->tg, &plan->grid);
-  plan->geom = g;
   OP_TRY(halo_map(g, ld, R, &plan->halo[0]));
   OP_TRY(halo_map(g, ld, P, &plan->halo[1]));
   OP_TRY(halo_map(g, ld, Q, &plan->halo[2]));
@@ -429,23 +401,12 @@ op_status cg_tma_p(const CgTmaPlan &plan, bool first, int po, float *Pn, const f
   const CUtensorMap &mPo = plan.halo[po == 0 ? 1 : 2];
   if (first)
     k_cg_tma<M_P_FIRST, 8><<<plan.grid, kThreads + 32, smem_bytes<M_P_FIRST, 8>(), st>>>(
-        plan.tg, Vt, mR, mPo, nullptr, Pn, beta, nact_prev, part, nullptr, err);
+        plan.tg, Vt, mR, mPo, Pn, beta, nact_prev, part, err);
   else
     k_cg_tma<M_P, 4><<<plan.grid, kThreads + 32, smem_bytes<M_P, 4>(), st>>>(
-        plan.tg, Vt, mR, mPo, nullptr, Pn, beta, nact_prev, part, nullptr, err);
+        plan.tg, Vt, mR, mPo, Pn, beta, nact_prev, part, err);
   count_launch();
   OP_LAUNCH("k_cg_tma");
-  return OP_OK;
-}
-
-op_status cg_tma_init(const CgTmaPlan &plan, const float *Vt, const float *U, const float *W,
-                      float *R, double *part, int *ctl, int *err, cudaStream_t st) {
-  CUtensorMap mW;
-  OP_TRY(halo_map(plan.geom, plan.tg.ld, W, &mW));
-  k_cg_tma<M_INIT, 8><<<plan.grid, kThreads + 32, smem_bytes<M_INIT, 8>(), st>>>(
-      plan.tg, Vt, mW, mW, U, R, nullptr, nullptr, part, ctl, err);
-  count_launch();
-  OP_LAUNCH("k_cg_tma<init>");
   return OP_OK;
 }
 
@@ -456,7 +417,7 @@ op_status tma_quad(const Geom &g, double sigma, int ld, const float *Vt, const f
   CUtensorMap mX;
   OP_TRY(halo_map(g, ld, X, &mX));
   k_cg_tma<M_QUAD, 8><<<*grid, kThreads + 32, smem_bytes<M_QUAD, 8>(), st>>>(
-      tg, Vt, mX, mX, nullptr, nullptr, nullptr, nullptr, part, nullptr, err);
+      tg, Vt, mX, mX, nullptr, nullptr, nullptr, part, err);
   count_launch();
   OP_LAUNCH("k_cg_tma<quad>");
   return OP_OK;
