@@ -118,9 +118,6 @@ template <typename T>
 op_status launch_sumsq(long long n, int ld, const T *X, double *part, double *out,
                        cudaStream_t st);
 
-// Reduce part[nblk][ncomp][ld] over blocks into out[ncomp][ld] (FP64).
-op_status launch_colsum(const double *part, int nblk, int ncomp, int ld, double *out,
-                        cudaStream_t st);
 
 // CG workspace layout and the solver loop.
 struct CGWork {
