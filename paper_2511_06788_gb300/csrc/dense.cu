@@ -254,16 +254,23 @@ __device__ __forceinline__ void gj32_body(int p, int ld, const double *__restric
         break;
       }
       const float pinv = 1.f / d;
+      // pivot row and this thread's column multipliers, read once per pivot
+      float r[8], f[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = ty + 32 * a;
-        const float f = colk[buf][i] * pinv;
+      for (int b = 0; b < 8; ++b) r[b] = rowk[buf][tx + 32 * b];
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const float r = rowk[buf][tx + 32 * b];
-          v[a][b] = (i == k) ? r * pinv : fmaf(-f, r, v[a][b]);
+      for (int a = 0; a < 4; ++a) f[a] = colk[buf][ty + 32 * a] * pinv;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) v[a][b] = fmaf(-f[a], r[b], v[a][b]);
+      // row k itself becomes the scaled pivot row
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        if (a == ak && ty == rk) {
+#pragma unroll
+          for (int b = 0; b < 8; ++b) v[a][b] = r[b] * pinv;
         }
-      }
     }
     if (bad) break;
   }
