@@ -196,6 +196,16 @@ op_status op_profile_read(op_ctx *ctx, int kind, double *total_ms, long long *la
  * op_restore: loads a state written by op_checkpoint into a context of the same
  *   problem size (n, p, ld) and precision (OP_ERR_ARG otherwise, or for a buffer
  *   that is not a checkpoint).  Both synchronise the context's stream. */
+/* Self-test of failure detection (the paper has no counterpart).  Every wait inside
+ * this library's kernels is bounded: on expiry the kernel sets an error word and
+ * the call returns OP_ERR_TIMEOUT instead of hanging.  This call makes one wait of
+ * each kind (the TMA ring's clock-bounded wait with a 0.2 s limit and the tensor-core
+ * kernels' iteration-bounded wait) run out on an mbarrier that nothing completes;
+ * it returns OP_OK when both gave up, and their durations in seconds[0..1] (may be
+ * NULL).  Allocates 32 bytes of device memory; synchronises `stream`; takes about
+ * a second. */
+op_status op_selftest_bounded_waits(double *seconds, void *stream);
+
 size_t op_checkpoint_size(const op_ctx *ctx);
 op_status op_checkpoint(op_ctx *ctx, void *buf, size_t len);
 op_status op_restore(op_ctx *ctx, const void *buf, size_t len);

@@ -8,4 +8,5 @@ call into it raises ImportError when ``libopevo.so`` has not been built.
 """
 from .binding import (OP_EIG_PAPER, OP_EIG_RITZ, OP_FP32, OP_FP64, OP_STOP_ERR_E,  # noqa: F401
                       OP_STOP_RESIDUAL, OP_STOP_STEPS, OpError, Solver, Batch, Net, apply_H, cg_solve,
-                      check, core, gram, last_error, lib, make_problem, update)
+                      check, core, gram, last_error, lib, make_problem, selftest_bounded_waits,
+                      update)

@@ -109,6 +109,7 @@ def lib():
         "op_update_workspace": (sz, [i32, i32]),
         "op_ws_status": (i32, [vp, vp]),
         "op_get_U_device": (i32, [vp, vp, i32]),
+        "op_selftest_bounded_waits": (i32, [P(f64), vp]),
         "op_checkpoint_size": (sz, [vp]),
         "op_checkpoint": (i32, [vp, vp, sz]),
         "op_restore": (i32, [vp, vp, sz]),
@@ -573,3 +574,10 @@ class Net:
                                      C.c_void_p(Ustar.data_ptr()), float(gamma), float(lr),
                                      float(beta1), float(beta2), float(eps), C.byref(loss)))
         return loss.value
+
+
+def selftest_bounded_waits(stream=None):
+    """Make one bounded device wait of each kind run out; returns their durations (s)."""
+    secs = (C.c_double * 2)()
+    check(lib().op_selftest_bounded_waits(secs, _stream_ptr(stream)))
+    return secs[0], secs[1]
