@@ -82,8 +82,9 @@ def algo_bytes(group, prec, n, p, s, launches, solves):
 # at this workload, keyed by kernel group and precision, valid for the kernel source
 # with the given SHA-1 prefix; null in the JSON line when the source has changed.
 NCU_TRAFFIC = {
-    ("cg_axpy", "fp32"): (619270656, "e77393e9f73a"),   # k_cg_wr, stencil_cg.cu
-    ("cg_apply", "fp32"): (371437056, "147e6cde8380"),  # k_cg_tma, stencil_tma.cu
+    ("cg_axpy", "fp32"): (622520320, "4084262628b0"),   # k_cg_wr, stencil_cg.cu
+    ("cg_apply", "fp32"): (368414720, "8e89b2755776"),  # k_cg_tma<P>, stencil_tma.cu
+    ("energy", "fp32"): (136012544, "8e89b2755776"),    # k_cg_tma<QUAD>, stencil_tma.cu
 }
 
 
@@ -93,7 +94,7 @@ def _sha(path):
 
 
 def kernel_source_sha(group, prec):
-    if group == "cg_apply" and prec != "fp64":
+    if group in ("cg_apply", "energy") and prec != "fp64":
         src = "stencil_tma.cu"
     elif group.startswith("cg_") or group == "energy":
         src = "stencil_cg.cu"
