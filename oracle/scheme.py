@@ -35,7 +35,7 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "grid_spacing", "hamiltonian", "spectrum_lower_bound", "default_sigma", "default_tau",
     "gershgorin_norm", "householder_orthonormalize", "cholesky_qr", "inner", "SourceSolver",
-    "block_cg", "core_matrices", "update", "scheme_step", "energy", "residuals",
+    "block_cg", "block_pcg_jacobi", "core_matrices", "update", "scheme_step", "energy", "residuals",
     "paper_eigenvalues", "ritz_values", "orth_error", "energy_lower_bound", "run",
     "RunResult", "step_coefficients", "midpoint_coefficients",
 ]
@@ -162,6 +162,46 @@ def block_cg(A, Bm: np.ndarray, X0: np.ndarray | None = None, rtol: float = 1e-1
         beta = np.where(active & (rr > 0), rr_new / np.where(rr > 0, rr, 1.0), 0.0)
         P = R + P * beta
         rr = rr_new
+        it += 1
+    return X, it
+
+
+def block_pcg_jacobi(A, Bm: np.ndarray, X0: np.ndarray | None = None, rtol: float = 1e-13,
+                     max_iter: int = 20000):
+    """As block_cg, preconditioned with the diagonal of A (Jacobi).
+
+    Step 1 of §4.1 only asks for W = (H + sigma)^-1 U; the paper does not say how
+    the source problems are solved.  This is textbook preconditioned CG with
+    M = diag(A): z = M^-1 r, rho = r . z, alpha = rho / (p . A p),
+    beta = rho_new / rho, p = z + beta p.  Each column stops on the same test as
+    block_cg, ||r_j|| <= rtol ||b_j|| (the unpreconditioned residual).
+    Returns (X, iterations).
+    """
+    d = np.asarray(A.diagonal(), dtype=np.float64)
+    X = np.zeros_like(Bm) if X0 is None else np.array(X0, dtype=np.float64)
+    R = Bm - A @ X
+    Z = R / d[:, None]
+    P = Z.copy()
+    rho = np.einsum("ij,ij->j", R, Z)
+    rr = np.einsum("ij,ij->j", R, R)
+    bnorm = np.sqrt(np.einsum("ij,ij->j", Bm, Bm))
+    target = (rtol * bnorm) ** 2
+    it = 0
+    while it < max_iter:
+        active = rr > target
+        if not np.any(active):
+            break
+        Q = A @ P
+        pq = np.einsum("ij,ij->j", P, Q)
+        alpha = np.where(active & (pq > 0), rho / np.where(pq > 0, pq, 1.0), 0.0)
+        X += P * alpha
+        R -= Q * alpha
+        Z = R / d[:, None]
+        rho_new = np.einsum("ij,ij->j", R, Z)
+        beta = np.where(active & (rho > 0), rho_new / np.where(rho > 0, rho, 1.0), 0.0)
+        P = Z + P * beta
+        rho = rho_new
+        rr = np.einsum("ij,ij->j", R, R)
         it += 1
     return X, it
 

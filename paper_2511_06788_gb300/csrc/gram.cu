@@ -142,10 +142,12 @@ __global__ void k_gram_reduce(int mask, int nt, int njobs, int nsplit,
   int prod, ti, tj;
   decode_job(blockIdx.x, mask, nt, &prod, &ti, &tj);
   double *out = prod == PROD_C ? C : (prod == PROD_S ? S : D);
-  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < kTile * kTile;
+       e += gridDim.y * blockDim.x) {
     const int i = ti * kTile + e / kTile, j = tj * kTile + e % kTile;
     if (i >= ld || j >= ld) continue;
     double s = 0.0;
+#pragma unroll 8
     for (int sp = 0; sp < nsplit; ++sp)
       s += part[((long long)sp * njobs + blockIdx.x) * (kTile * kTile) + e];
     const double v = (i < p && j < p) ? s : 0.0;
@@ -220,7 +222,9 @@ op_status gram(long long n, int p, int ld, const T *U, const T *W, double *C, do
   k_gram<T, T><<<dim3(nj, g.nsplit), dim3(16, 16), 0, st>>>(n, ld, U, W, mask, nt, nj,
                                                            g.rows_per_split, part); count_launch();
   OP_LAUNCH("k_gram");
-  k_gram_reduce<<<nj, 256, 0, st>>>(mask, nt, nj, g.nsplit, part, p, ld, C, S, D); count_launch();
+  k_gram_reduce<<<dim3(nj, kTile * kTile / 256), 256, 0, st>>>(mask, nt, nj, g.nsplit, part, p,
+                                                                ld, C, S, D);
+  count_launch();
   OP_LAUNCH("k_gram_reduce");
   return OP_OK;
 }
@@ -258,7 +262,9 @@ op_status gram_fixed_scratch(long long n, int p, int ld, const T *U, const T *W,
                                                          (double *)part);
   count_launch();
   OP_LAUNCH("k_gram");
-  k_gram_reduce<<<nj, 256, 0, st>>>(mask, nt, nj, nsplit, (const double *)part, p, ld, C, S, D);
+  k_gram_reduce<<<dim3(nj, kTile * kTile / 256), 256, 0, st>>>(mask, nt, nj, nsplit,
+                                                                (const double *)part, p, ld, C,
+                                                                S, D);
   count_launch();
   OP_LAUNCH("k_gram_reduce");
   return OP_OK;

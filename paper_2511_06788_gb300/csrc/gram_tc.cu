@@ -31,6 +31,8 @@ namespace opevo {
 namespace {
 
 constexpr int kTM = 128;                      // output tile (rows and columns)
+// reduce grid: one thread per output element of a tile (the split sums stay in order)
+constexpr int kReduceSlices = kTM * kTM / 256;
 constexpr int kKS = 32;                       // grid points per slab (one 128-byte K row)
 constexpr int kPiece = kTM * 128;             // bytes of one operand piece (128 rows x 128 B)
 constexpr int kStage = 4 * kPiece;            // A_hi, A_lo, B_hi, B_lo
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(256, 1)
                1);
 }
 
-// Batched reduce: grid (jobs, problems).
+// Batched reduce: grid (jobs, problems, element slices).
 __global__ void k_b_gram_tc_reduce(const BatchProb *__restrict__ Bp) {
   const BatchProb &pb = Bp[blockIdx.y];
   if (*pb.frozen || (int)blockIdx.x >= pb.gram_jobs) return;
@@ -256,10 +258,12 @@ __global__ void k_b_gram_tc_reduce(const BatchProb *__restrict__ Bp) {
   int prod, ti, tj;
   decode_job(blockIdx.x, 7, nt, &prod, &ti, &tj);
   double *out = prod == PROD_C ? pb.C : (prod == PROD_S ? pb.S : pb.D);
-  for (int e = threadIdx.x; e < kTM * kTM; e += blockDim.x) {
+  for (int e = blockIdx.z * blockDim.x + threadIdx.x; e < kTM * kTM;
+       e += gridDim.z * blockDim.x) {
     const int i = ti * kTM + e / kTM, j = tj * kTM + e % kTM;
     if (i >= ld || j >= ld) continue;
     double s = 0.0;
+#pragma unroll 8
     for (int sp = 0; sp < pb.n_gram_splits; ++sp)
       s += pb.gram_part[((long long)sp * pb.gram_jobs + blockIdx.x) * (kTM * kTM) + e];
     const double v = (i < p && j < p) ? s : 0.0;
@@ -278,6 +282,7 @@ __global__ void k_gram_tc_reduce(int mask, int nt, int njobs, int nsplit,
     const int i = ti * kTM + e / kTM, j = tj * kTM + e % kTM;
     if (i >= ld || j >= ld) continue;
     double s = 0.0;
+#pragma unroll 8
     for (int sp = 0; sp < nsplit; ++sp)
       s += part[((long long)sp * njobs + blockIdx.x) * (kTM * kTM) + e];
     const double v = (i < p && j < p) ? s : 0.0;
@@ -336,7 +341,8 @@ op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, do
                                                    split);
   count_launch();
   OP_LAUNCH("k_gram_tc");
-  k_gram_tc_reduce<<<dim3(nj, 16), 256, 0, st>>>(mask, nt, nj, nsplit, part, p, ld, C, S, D);
+  k_gram_tc_reduce<<<dim3(nj, kReduceSlices), 256, 0, st>>>(mask, nt, nj, nsplit, part, p, ld,
+                                                             C, S, D);
   count_launch();
   OP_LAUNCH("k_gram_tc_reduce");
   return OP_OK;
@@ -374,8 +380,8 @@ op_status gram_tc_fixed_scratch(long long n, int p, int ld, const float *U, cons
                                                    err, 1);
   count_launch();
   OP_LAUNCH("k_gram_tc");
-  k_gram_tc_reduce<<<dim3(nj, 16), 256, 0, st>>>(mask, nt, nj, nsplit, (const double *)part, p,
-                                                   ld, C, S, D);
+  k_gram_tc_reduce<<<dim3(nj, kReduceSlices), 256, 0, st>>>(mask, nt, nj, nsplit,
+                                                             (const double *)part, p, ld, C, S, D);
   count_launch();
   OP_LAUNCH("k_gram_tc_reduce");
   return OP_OK;
@@ -388,7 +394,7 @@ op_status launch_b_gram(const BatchProb *B, const GramItem *items, int nitems, i
   count_launch();
   OP_LAUNCH("k_b_gram_tc");
   // at most 3 * 8 * 8 + ... jobs for ld <= 1024: grid x covers the largest job count
-  k_b_gram_tc_reduce<<<dim3(tc_jobs(8, 7), nprob), 256, 0, st>>>(B);
+  k_b_gram_tc_reduce<<<dim3(tc_jobs(8, 7), nprob, 4), 256, 0, st>>>(B);
   count_launch();
   OP_LAUNCH("k_b_gram_tc_reduce");
   return OP_OK;

@@ -471,4 +471,29 @@ op_status tma_map_4d_f32(CUtensorMap *map, const void *base, const uint64_t dims
   return OP_OK;
 }
 
+op_status tma_map_2d_f32_sw128(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                               uint32_t box_outer) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return OP_ERR_CUDA;
+  }
+  if (((uintptr_t)base & 15) != 0 || (inner * 4) % 16 != 0) {
+    set_error("tensor map: base or row pitch not 16-byte aligned");
+    return OP_ERR_ARG;
+  }
+  cuuint64_t gd[2] = {inner, outer};
+  cuuint64_t gs[1] = {inner * 4};
+  cuuint32_t bx[2] = {32, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), gd, gs, bx,
+                  es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    return OP_ERR_CUDA;
+  }
+  return OP_OK;
+}
+
 }  // namespace opevo

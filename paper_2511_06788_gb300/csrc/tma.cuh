@@ -22,6 +22,14 @@ namespace opevo {
 op_status tma_map_4d_f32(CUtensorMap *map, const void *base, const uint64_t dims[4],
                          const uint32_t box[4]);
 
+// 2-D FP32 tensor map over a row-major [outer][inner] array with a box of 32 x
+// box_outer elements landing in the 128-byte-swizzled layout (rows of 128 bytes,
+// 16-byte chunk c of row r at chunk c ^ (r % 8) within each 1024-byte group of 8
+// rows): the K-major operand layout of the tensor-core MMA.  The destination must
+// be 1024-byte aligned and every inner coordinate a multiple of 4.
+op_status tma_map_2d_f32_sw128(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                               uint32_t box_outer);
+
 namespace tma {
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -94,6 +102,15 @@ __device__ __forceinline__ void load_4d(void *dst, const CUtensorMap *map, int c
       "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
       "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void load_2d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                        uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
       : "memory");
 }
 

@@ -181,7 +181,11 @@ def test_core_reports_breakdown():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("n,p", [(1, 1), (999, 8), (4097, 40), (3001, 130)])
+# ld a multiple of 32 (p = 90, 128, 256) takes the TMA-fed tensor-core kernel for FP32:
+# a ragged last column tile (90 -> ld 96), more tiles than SMs (20000 x 128) and two
+# column tiles (256)
+@pytest.mark.parametrize("n,p", [(1, 1), (999, 8), (4097, 40), (3001, 130), (5000, 90),
+                                 (20000, 128), (3001, 256)])
 def test_update_matches_oracle(prec, n, p):
     rng = np.random.default_rng(n * p)
     U = rounded(rng.standard_normal((n, p)), prec)

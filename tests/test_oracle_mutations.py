@@ -82,3 +82,45 @@ def test_update_sign_mutant_breaks_orthogonality():
     Ubad = U + tau * (U @ A) + tau * (W @ B)           # wrong sign on the U A term
     assert o.orth_error(Ubad) > 1e-3
     assert o.orth_error(o.update(U, W, A, B, tau)) < 1e-13
+
+
+def _pcg_mutant(kind):
+    """Copy of oracle.block_pcg_jacobi with one plausible mistake."""
+    def pcg(A, Bm, X0=None, rtol=1e-13, max_iter=20000):
+        d = np.asarray(A.diagonal(), dtype=np.float64)
+        X = np.zeros_like(Bm) if X0 is None else np.array(X0, dtype=np.float64)
+        R = Bm - A @ X
+        Z = R / d[:, None]
+        P = (R if kind == "direction_from_r" else Z).copy()
+        rho = np.einsum("ij,ij->j", R, R if kind == "beta_from_rr" else Z)
+        target = (rtol * np.linalg.norm(Bm, axis=0)) ** 2
+        it = 0
+        while it < max_iter and np.any(np.einsum("ij,ij->j", R, R) > target):
+            Q = A @ P
+            alpha = rho / np.einsum("ij,ij->j", P, Q)
+            X += P * alpha
+            R -= Q * alpha
+            Z = R / d[:, None]
+            rho_new = np.einsum("ij,ij->j", R, R if kind == "beta_from_rr" else Z)
+            P = (R if kind == "direction_from_r" else Z) + P * (rho_new / rho)
+            rho = rho_new
+            it += 1
+        return X, it
+    return pcg
+
+
+@pytest.mark.parametrize("kind", ["direction_from_r", "beta_from_rr"])
+def test_pcg_mutants_break_krylov_optimality_pin(monkeypatch, kind):
+    from tests.test_oracle_pins import \
+        test_jacobi_pcg_iterate_minimises_the_energy_error_over_the_krylov_space as pin
+    monkeypatch.setattr(o, "block_pcg_jacobi", _pcg_mutant(kind))
+    with pytest.raises(AssertionError):
+        pin()
+
+
+def test_pcg_mutant_copy_is_faithful_without_mistake(monkeypatch):
+    # the mutant template itself, with no mistake planted, passes the pin
+    from tests.test_oracle_pins import \
+        test_jacobi_pcg_iterate_minimises_the_energy_error_over_the_krylov_space as pin
+    monkeypatch.setattr(o, "block_pcg_jacobi", _pcg_mutant("none"))
+    pin()

@@ -161,6 +161,67 @@ def test_source_solve_direct_and_cg_agree():
     np.testing.assert_allclose(Wc, Gd, rtol=0, atol=1e-11)
 
 
+def test_jacobi_pcg_solves_a_diagonal_system_in_one_iteration():
+    # M^-1 A = I: the first step length is 1 and x_1 = b / d exactly
+    import scipy.sparse as sp
+    d = np.linspace(0.5, 40.0, 30)
+    B = np.random.default_rng(2).standard_normal((30, 4))
+    X, it = o.block_pcg_jacobi(sp.diags(d).tocsr(), B, rtol=1e-14)
+    assert it == 1
+    np.testing.assert_allclose(X, B / d[:, None], rtol=1e-15, atol=0)
+
+
+def test_jacobi_pcg_equals_cg_for_a_constant_diagonal():
+    # a constant diagonal scales the residual only: the iterates are those of CG
+    shape, lo, hi = (5, 4, 3), (-1.0,) * 3, (1.0,) * 3
+    n = int(np.prod(shape))
+    A = o.hamiltonian(shape, lo, hi, np.full(n, 0.7)).tocsr()
+    B = np.random.default_rng(3).standard_normal((n, 3))
+    X0 = 0.1 * np.random.default_rng(4).standard_normal((n, 3))
+    for k in (1, 2, 4, 7):
+        Xp, ip = o.block_pcg_jacobi(A, B, X0, rtol=0.0, max_iter=k)
+        Xc, ic = o.block_cg(A, B, X0, rtol=0.0, max_iter=k)
+        assert ip == ic == k
+        np.testing.assert_allclose(Xp, Xc, rtol=0, atol=1e-12 * np.abs(Xc).max())
+
+
+def test_jacobi_pcg_iterate_minimises_the_energy_error_over_the_krylov_space():
+    # x_k = argmin ||x - x*||_A over x_0 + span{z0, (M^-1 A) z0, ..}, brute force
+    import scipy.sparse as sp
+    shape, lo, hi, V, H, sigma, U = random_problem(7, (4, 3, 3), 2)
+    n = H.shape[0]
+    As = (H + sigma * sp.identity(n)).tocsr()
+    A = As.toarray()
+    d = np.diag(A)
+    b = U[:, 1]
+    x0 = 0.2 * np.random.default_rng(8).standard_normal(n)
+    xs = np.linalg.solve(A, b)
+    z0 = (b - A @ x0) / d
+    for k in (1, 2, 3, 5):
+        K = np.empty((n, k))
+        K[:, 0] = z0
+        for j in range(1, k):
+            K[:, j] = (A @ K[:, j - 1]) / d
+        Q, _ = np.linalg.qr(K)
+        c = np.linalg.solve(Q.T @ A @ Q, Q.T @ (b - A @ x0))
+        x_best = x0 + Q @ c
+        Xk, it = o.block_pcg_jacobi(As, b[:, None], x0[:, None], rtol=0.0, max_iter=k)
+        assert it == k
+        np.testing.assert_allclose(Xk[:, 0], x_best, rtol=0, atol=1e-9 * np.abs(xs).max())
+
+
+def test_jacobi_pcg_converges_to_the_direct_solution():
+    import scipy.sparse as sp
+    shape, lo, hi, V, H, sigma, U = random_problem(1, (6, 5, 4), 5)
+    As = (H + sigma * sp.identity(H.shape[0])).tocsr()
+    Gd = np.linalg.solve(As.toarray(), U)
+    X, it = o.block_pcg_jacobi(As, U, rtol=1e-14)
+    assert 0 < it < 500
+    np.testing.assert_allclose(X, Gd, rtol=0, atol=1e-11)
+    R = U - As @ X
+    assert np.all(np.linalg.norm(R, axis=0) <= 1e-14 * np.linalg.norm(U, axis=0))
+
+
 @pytest.mark.parametrize("p", [1, 3, 6])
 @pytest.mark.parametrize("tau_scale", [0.01, 1.0, 1.5, 40.0])
 def test_steps_2_to_4_equal_cayley_transform(p, tau_scale):
