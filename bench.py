@@ -271,7 +271,7 @@ def run_ours(args):
     V_d = torch.from_numpy(P.V).to(dev)
     U0_d = torch.from_numpy(U0).to(dev)
     solver = pkg.Solver(P.shape, P.lo, P.hi, V_d, U0_d, p, prec=args.prec, stream=stream,
-                        device=True)
+                        device=True, precond=args.precond)
     for _ in range(args.warmup):
         solver.step(1)
     solver.profile(True)
@@ -344,7 +344,7 @@ def run_ours(args):
         barrier()
         t0 = time.perf_counter()
         s2 = pkg.Solver(P.shape, P.lo, P.hi, Vh.numpy(), Uh.numpy(), p, prec=args.prec,
-                        stream=stream)
+                        stream=stream, precond=args.precond)
         s2.step(args.steps)
         s2.get_U(out=Uout.numpy())  # into pinned host memory
         torch.cuda.synchronize(dev)
@@ -371,7 +371,7 @@ def run_ours(args):
             "dtype": {"fp32": "f32", "fp64": "f64", "mix_tf32": "f32+tf32"}[args.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "p": p, "precision": args.prec,
-                       "seed_per_rank": "rank", "l2": "inputs larger than L2 (each n x p block "
+                       "cg_precond": args.precond, "seed_per_rank": "rank", "l2": "inputs larger than L2 (each n x p block "
                        f"{n * p * s_el / 1e6:.0f} MB, working set > 0.8 GB)",
                        "cg_iters_per_step": (st1["cg_iters"] - st0["cg_iters"]) / args.steps},
             "roofline": roofline, "kernel_ms": kernel_times, "cpu_baseline": cpu, "e2e": e2e,
@@ -812,6 +812,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "mix_tf32"])
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "none"],
+                    help="Step-1 CG preconditioner of the 3d_wells_64 workload")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="3d_wells_64",

@@ -63,6 +63,14 @@ typedef enum {
                             to TF32, 10-bit mantissa); context-level API only        */
 } op_prec;
 
+/* Solver of the source problems (H + sigma) w = u of Step 1 (the paper does not say how
+ * they are solved; every choice stops on the same unpreconditioned residual test). */
+typedef enum {
+  OP_PRECOND_NONE = 0,   /* conjugate gradients                                       */
+  OP_PRECOND_JACOBI = 1  /* conjugate gradients preconditioned with d = diag(H + sigma)
+                            (z = r / d; the residual buffer holds z)                   */
+} op_precond;
+
 typedef enum {
   OP_STOP_RESIDUAL = 0,  /* r <= tol, r = ||H U - U Theta||_F / (||H+sigma||_G sqrt(p)) */
   OP_STOP_ERR_E = 1,     /* Algorithm 1: |E(U^{n+1}) - E(U^n)| / |E(U^n)| <= tol   */
@@ -103,6 +111,8 @@ typedef struct {
                             residual normalisation keeps sigma_0.  Algorithm 1 allows
                             a variable tau_n; the fixed points do not depend on sigma
                             or tau. */
+  int cg_precond;        /* op_precond of the Step-1 CG (op_cg_solve and contexts; the
+                            batched solver takes OP_PRECOND_NONE only)               */
 } op_problem;
 
 /* Per-context statistics, filled by op_step / op_solve. */

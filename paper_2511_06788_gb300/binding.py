@@ -31,7 +31,8 @@ class OpProblem(C.Structure):
     _fields_ = [("dim", C.c_int), ("shape", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("p", C.c_int), ("sigma", C.c_double),
                 ("tau", C.c_double), ("prec", C.c_int), ("cg_rtol", C.c_double),
-                ("cg_max_iter", C.c_int), ("check_every", C.c_int), ("adapt_every", C.c_int)]
+                ("cg_max_iter", C.c_int), ("check_every", C.c_int), ("adapt_every", C.c_int),
+                ("cg_precond", C.c_int)]
 
 
 class OpStats(C.Structure):
@@ -141,8 +142,11 @@ def last_error() -> str:
     return lib().op_last_error().decode()
 
 
+PRECONDS = {"none": 0, "jacobi": 1}
+
+
 def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol=0.0,
-                 cg_max_iter=0, check_every=0, adapt_every=0) -> OpProblem:
+                 cg_max_iter=0, check_every=0, adapt_every=0, precond="jacobi") -> OpProblem:
     pb = OpProblem()
     dim = len(shape)
     pb.dim = dim
@@ -158,6 +162,7 @@ def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol
     pb.cg_max_iter = int(cg_max_iter)
     pb.check_every = int(check_every)
     pb.adapt_every = int(adapt_every)
+    pb.cg_precond = PRECONDS[precond] if isinstance(precond, str) else int(precond)
     return pb
 
 
@@ -184,11 +189,11 @@ class Solver:
     """A solver context (op_init ... op_destroy) for one eigenproblem."""
 
     def __init__(self, shape, lo, hi, V, U0, p, *, prec="fp64", sigma=None, tau=None,
-                 cg_rtol=0.0, cg_max_iter=0, check_every=0, adapt_every=0, stream=None,
-                 device=False):
+                 cg_rtol=0.0, cg_max_iter=0, check_every=0, adapt_every=0, precond="jacobi",
+                 stream=None, device=False):
         self.pb = make_problem(shape, lo, hi, p, prec=prec, sigma=sigma, tau=tau,
                                cg_rtol=cg_rtol, cg_max_iter=cg_max_iter, check_every=check_every,
-                               adapt_every=adapt_every)
+                               adapt_every=adapt_every, precond=precond)
         self.n = int(np.prod(shape))
         self.p = int(p)
         self._ctx = C.c_void_p()
@@ -411,11 +416,12 @@ def apply_H(shape, lo, hi, V_t, sigma, X, Y=None, stream=None):
     return Y
 
 
-def cg_solve(shape, lo, hi, V_t, sigma, U, W, p, rtol, max_iter=5000, stream=None):
+def cg_solve(shape, lo, hi, V_t, sigma, U, W, p, rtol, max_iter=5000, stream=None,
+             precond="none"):
     import torch
     n, ld = U.shape
     prec = _prec_of(U)
-    pb = make_problem(shape, lo, hi, p, prec=prec)
+    pb = make_problem(shape, lo, hi, p, prec=prec, precond=precond)
     nbytes = lib().op_cg_workspace(C.byref(pb), ld)
     ws = torch.empty(nbytes, dtype=torch.uint8, device=U.device)
     it = C.c_int()

@@ -121,6 +121,10 @@ op_status check_problem(const op_problem *pb) {
     set_error("unsupported precision mode %d", pb->prec);
     return OP_ERR_ARG;
   }
+  if (pb->cg_precond != OP_PRECOND_NONE && pb->cg_precond != OP_PRECOND_JACOBI) {
+    set_error("unsupported CG preconditioner %d", pb->cg_precond);
+    return OP_ERR_ARG;
+  }
   Geom g;
   OP_TRY(make_geom(pb, &g));
   if (pb->p > g.n) {
@@ -414,6 +418,7 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
   OP_TRY(dev_alloc(c, &c->cg_ws, cg_workspace_bytes(n, ld, sizeof(T))));
   cg_carve(c->cg_ws, n, ld, sizeof(T), &c->cgw);
   c->cgw.prof = &c->prof;
+  c->cgw.jacobi = c->pb.cg_precond == OP_PRECOND_JACOBI;
   c->gram_bytes = gram_workspace_bytes(n, ld, sizeof(T));
   if (sizeof(T) == 4) {
     const size_t tcb = gram_tc_workspace_bytes(n, ld);
@@ -861,8 +866,13 @@ op_status op_cg_solve(const op_problem *pb, int ld, const void *V_t, double sigm
     return OP_ERR_ARG;
   }
   const int elem = pb->prec == OP_FP64 ? 8 : 4;
+  if (pb->cg_precond != OP_PRECOND_NONE && pb->cg_precond != OP_PRECOND_JACOBI) {
+    set_error("op_cg_solve: unsupported CG preconditioner %d", pb->cg_precond);
+    return OP_ERR_ARG;
+  }
   CGWork w;
   cg_carve(ws, g.n, ld, elem, &w);
+  w.jacobi = pb->cg_precond == OP_PRECOND_JACOBI;
   int host_ctl[4] = {0, 0, 0, 0};
   w.host_ctl = host_ctl;
   cudaStream_t st = (cudaStream_t)stream;

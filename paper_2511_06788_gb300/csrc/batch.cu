@@ -156,6 +156,7 @@ op_status build_lists(op_batch *b) {
     pb.P = (float *)c->cgw.P;
     pb.Q = (float *)c->cgw.Q;
     pb.part = c->cgw.part;
+    pb.jacobi = c->cgw.jacobi ? 1 : 0;
     pb.state = c->cgw.state;
     pb.active = c->cgw.active;
     pb.ctl = c->cgw.ctl;
@@ -183,9 +184,11 @@ op_status build_lists(op_batch *b) {
     const long long rpi = b->rows_per_item;
     int local = 0;
     for (long long r0 = 0; r0 < n; r0 += rpi, ++local) rows.push_back({i, local, r0, std::min(n, r0 + rpi)});
-    if (local > c->cgw.max_blocks) {
+    // the CG partials of a row item take up to 3 ld doubles (the context's buffer
+    // holds max_blocks x 2 ld)
+    if (3 * local > 2 * c->cgw.max_blocks) {
       set_error("op_batch: problem %d needs %d row items (max %d): raise rows_per_item", i, local,
-                c->cgw.max_blocks);
+                2 * c->cgw.max_blocks / 3);
       return OP_ERR_ARG;
     }
     pb.n_row_items = local;

@@ -53,7 +53,8 @@ struct BatchProb {
   const float *Vt;
   float *U[2];             // U and U+ (roles alternate with the step parity)
   float *W, *R, *P, *Q;    // Step-1 solution and CG buffers (P, Q: direction buffers)
-  double *part;            // row-kernel CTA partials [items][2][ld] + column sums [2][ld]
+  double *part;            // row-kernel CTA partials [items][<= 3][ld] + column sums [2][ld]
+  int jacobi;              // Step-1 CG preconditioned with diag(H + sigma); R holds r / d
   double *state;           // CG state [6][ld]
   int *active, *ctl;       // CG control (ctl[0..1] active counts, ctl[2] iterations)
   double *cg_rtol2;        // squared relative CG tolerance of the current step
@@ -130,6 +131,7 @@ struct CGWork {
   int *host_ctl;         // >= 4 ints of host memory (pinned for the context)
   int max_blocks;
   int expect_iters = 0;  // iterations of the previous solve (first chunk length)
+  bool jacobi = false;   // CG preconditioned with diag(H + sigma)
   Prof *prof = nullptr;  // optional timing
 };
 // bytes of the CTA-partials scratch used by the reductions of a row width ld

@@ -192,7 +192,10 @@ __global__ void __launch_bounds__(256) k_sumsq(long long n, int ld, const T *__r
 
 // R = U - (H+sigma) W (and P = R when WRITE_P); part[b][0] = ||R_j||^2,
 // part[b][1] = ||U_j||^2.  Resets the control words.
-template <typename T, bool WRITE_P>
+// R = U - (H+sigma) W (P = R as well when WRITE_P); part[b][.][j]: R_j.R_j, U_j.U_j.
+// JACOBI (CG preconditioned with d = diag(H+sigma)): the residual buffer holds
+// Z = R / d instead, and part[b][.][j] = R_j.Z_j, U_j.U_j, R_j.R_j.
+template <typename T, bool WRITE_P, bool JACOBI>
 __global__ void __launch_bounds__(256) k_cg_init(Geom g, const T *__restrict__ Vt, T shift,
                                                  const T *__restrict__ U, const T *__restrict__ W,
                                                  T *__restrict__ R, T *__restrict__ P, int ld,
@@ -203,22 +206,35 @@ __global__ void __launch_bounds__(256) k_cg_init(Geom g, const T *__restrict__ V
     ctl[2] = 0;
     ctl[3] = 0;
   }
-  T acc[2][N] = {};
+  constexpr int NC = JACOBI ? 3 : 2;
+  T acc[NC][N] = {};
   for (long long i = i0; i < g.n; i += istep) {
     Pack<T> aw = stencil_at(g, Vt, shift, W, ld, i, col, (Pack<T> *)nullptr);
     const long long o = i * (long long)ld + col;
     Pack<T> u = Pack<T>::load(U + o);
     Pack<T> r;
+    if (JACOBI) {
+      const T inv = T(1) / (__ldg(Vt + i) + shift);
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      r.v[k] = u.v[k] - aw.v[k];
-      acc[0][k] += r.v[k] * r.v[k];
-      acc[1][k] += u.v[k] * u.v[k];
+      for (int k = 0; k < N; ++k) {
+        const T rk = u.v[k] - aw.v[k];
+        r.v[k] = rk * inv;
+        acc[0][k] += rk * r.v[k];
+        acc[1][k] += u.v[k] * u.v[k];
+        acc[NC - 1][k] += rk * rk;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        r.v[k] = u.v[k] - aw.v[k];
+        acc[0][k] += r.v[k] * r.v[k];
+        acc[1][k] += u.v[k] * u.v[k];
+      }
     }
     r.store(R + o);
     if (WRITE_P) r.store(P + o);
   }
-  block_colsum<T, 2>(acc, ld, part);
+  block_colsum<T, NC>(acc, ld, part);
 }
 
 // ---- three-kernel iteration (FP64: no arithmetic is recomputed) -----------------
@@ -242,10 +258,12 @@ __global__ void __launch_bounds__(256) k_cg_apply(Geom g, const T *__restrict__ 
 }
 
 // W += alpha P; R -= alpha Q; part[b][0][j] = ||R_j||^2.
-template <typename T>
-__global__ void __launch_bounds__(256) k_cg_axpy(long long n, int ld, T *__restrict__ W,
-                                                 T *__restrict__ R, const T *__restrict__ P,
-                                                 const T *__restrict__ Q,
+// W += alpha P, R -= alpha Q; part[b][0][j] = R_j.R_j.  JACOBI: the residual buffer
+// holds Z = R / d, Z -= alpha Q / d, part[b][.][j] = R_j.Z_j, R_j.R_j.
+template <typename T, bool JACOBI>
+__global__ void __launch_bounds__(256) k_cg_axpy(long long n, int ld, const T *__restrict__ Vt,
+                                                 T shift, T *__restrict__ W, T *__restrict__ R,
+                                                 const T *__restrict__ P, const T *__restrict__ Q,
                                                  const double *__restrict__ alpha,
                                                  const int *nact_prev, double *__restrict__ part) {
   if (*nact_prev == 0) return;
@@ -253,21 +271,34 @@ __global__ void __launch_bounds__(256) k_cg_axpy(long long n, int ld, T *__restr
   T a[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) a[k] = (col < ld) ? (T)alpha[col + k] : T(0);
-  T acc[1][N] = {};
+  constexpr int NC = JACOBI ? 2 : 1;
+  T acc[NC][N] = {};
   for (long long i = i0; i < n; i += istep) {
     const long long o = i * (long long)ld + col;
     Pack<T> w = Pack<T>::load_rw(W + o), r = Pack<T>::load_rw(R + o);
     Pack<T> p = Pack<T>::load(P + o), q = Pack<T>::load(Q + o);
+    if (JACOBI) {
+      const T dg = __ldg(Vt + i) + shift, inv = T(1) / dg;
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      w.v[k] += a[k] * p.v[k];
-      r.v[k] -= a[k] * q.v[k];
-      acc[0][k] += r.v[k] * r.v[k];
+      for (int k = 0; k < N; ++k) {
+        w.v[k] += a[k] * p.v[k];
+        r.v[k] -= a[k] * (q.v[k] * inv);
+        const T rk = dg * r.v[k];
+        acc[0][k] += rk * r.v[k];
+        acc[1][k] += rk * rk;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        w.v[k] += a[k] * p.v[k];
+        r.v[k] -= a[k] * q.v[k];
+        acc[0][k] += r.v[k] * r.v[k];
+      }
     }
     w.store(W + o);
     r.store(R + o);
   }
-  block_colsum<T, 1>(acc, ld, part);
+  block_colsum<T, NC>(acc, ld, part);
 }
 
 // P = R + beta P.
@@ -328,7 +359,7 @@ __global__ void __launch_bounds__(256) k_cg_p(Geom g, const T *__restrict__ Vt, 
 }
 
 // q = (H+sigma) Pn (recomputed); W += alpha Pn; R -= alpha q; part[b][0][j] = ||R_j||^2.
-template <typename T>
+template <typename T, bool JACOBI>
 __global__ void __launch_bounds__(256) k_cg_wr(Geom g, const T *__restrict__ Vt, T shift,
                                                T *__restrict__ W, T *__restrict__ R,
                                                const T *__restrict__ Pn, int ld,
@@ -339,22 +370,35 @@ __global__ void __launch_bounds__(256) k_cg_wr(Geom g, const T *__restrict__ Vt,
   T a[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) a[k] = (col < ld) ? (T)alpha[col + k] : T(0);
-  T acc[1][N] = {};
+  constexpr int NC = JACOBI ? 2 : 1;
+  T acc[NC][N] = {};
   for (long long i = i0; i < g.n; i += istep) {
     Pack<T> pc;
     const Pack<T> q = stencil_at(g, Vt, shift, Pn, ld, i, col, &pc);
     const long long o = i * (long long)ld + col;
     Pack<T> w = Pack<T>::load_rw(W + o), r = Pack<T>::load_rw(R + o);
+    if (JACOBI) {  // r holds Z = R / d
+      const T dg = __ldg(Vt + i) + shift, inv = T(1) / dg;
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      w.v[k] += a[k] * pc.v[k];
-      r.v[k] -= a[k] * q.v[k];
-      acc[0][k] += r.v[k] * r.v[k];
+      for (int k = 0; k < N; ++k) {
+        w.v[k] += a[k] * pc.v[k];
+        r.v[k] -= a[k] * (q.v[k] * inv);
+        const T rk = dg * r.v[k];
+        acc[0][k] += rk * r.v[k];
+        acc[1][k] += rk * rk;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        w.v[k] += a[k] * pc.v[k];
+        r.v[k] -= a[k] * q.v[k];
+        acc[0][k] += r.v[k] * r.v[k];
+      }
     }
     w.store(W + o);
     r.store(R + o);
   }
-  block_colsum<T, 1>(acc, ld, part);
+  block_colsum<T, NC>(acc, ld, part);
 }
 
 // ---- finalisers: one warp per column, lanes stride over the CTA partials ----------
@@ -367,15 +411,18 @@ __device__ __forceinline__ double warp_sum_blocks(const double *part, int nblk, 
   return s;
 }
 
-// state rows: 0 rr, 1 target, 2 alpha, 3 beta, 4 ||b||^2
-__global__ void k_cg_fin_init(const double *part, int nblk, int ld, int p, double rtol2,
-                              double *state, int *active, int *ctl) {
+// state rows: 0 rho (r.r, or r.z with the Jacobi preconditioner), 1 target, 2 alpha,
+// 3 beta, 4 ||b||^2.  ncomp = 2: partials (r.r, b.b); 3: (r.z, b.b, r.r).  A column
+// stays active while its unpreconditioned ||r||^2 is above rtol^2 ||b||^2.
+__global__ void k_cg_fin_init(const double *part, int nblk, int ncomp, int ld, int p,
+                              double rtol2, double *state, int *active, int *ctl) {
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j >= ld) return;
-  const double rr = warp_sum_blocks(part, nblk, 2 * ld, j);
-  const double bb = warp_sum_blocks(part, nblk, 2 * ld, ld + j);
+  const double rho = warp_sum_blocks(part, nblk, ncomp * ld, j);
+  const double bb = warp_sum_blocks(part, nblk, ncomp * ld, ld + j);
+  const double rr = ncomp == 3 ? warp_sum_blocks(part, nblk, ncomp * ld, 2 * ld + j) : rho;
   if ((threadIdx.x & 31) == 0) {
-    state[0 * ld + j] = rr;
+    state[0 * ld + j] = rho;
     state[1 * ld + j] = rtol2 * bb;
     state[2 * ld + j] = 0.0;
     state[3 * ld + j] = 0.0;
@@ -399,19 +446,21 @@ __global__ void k_cg_fin_alpha(const double *part, int nblk, int ld, double *sta
   }
 }
 
-__global__ void k_cg_fin_beta(const double *part, int nblk, int ld, double *state, int *active,
-                              const int *nact_prev, int *nact_next, int *iters) {
+// ncomp = 1: partials (r.r); 2: (r.z, r.r) with the Jacobi preconditioner.
+__global__ void k_cg_fin_beta(const double *part, int nblk, int ncomp, int ld, double *state,
+                              int *active, const int *nact_prev, int *nact_next, int *iters) {
   if (*nact_prev == 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) *iters += 1;
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j >= ld) return;
-  const double rrn = warp_sum_blocks(part, nblk, ld, j);
+  const double rhon = warp_sum_blocks(part, nblk, ncomp * ld, j);
+  const double rrn = ncomp == 2 ? warp_sum_blocks(part, nblk, ncomp * ld, ld + j) : rhon;
   if ((threadIdx.x & 31) == 0) {
-    const double rr = state[j];
+    const double rho = state[j];
     int a = active[j];
-    state[3 * ld + j] = (a && rr > 0.0) ? rrn / rr : 0.0;
+    state[3 * ld + j] = (a && rho > 0.0) ? rhon / rho : 0.0;
     if (a) {
-      state[j] = rrn;
+      state[j] = rhon;
       a = rrn > state[ld + j];
       active[j] = a;
     }
@@ -596,14 +645,25 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
     }
   }
 
+  // Jacobi preconditioning: R holds Z = R / diag(H + sigma); the direction kernels
+  // (P = Z + beta P and its stencil) are unchanged, the W/R kernels carry 1 / d
+  const bool jac = w.jacobi;
   prof_begin(w.prof, PK_CG_INIT, st);
   // (a TMA plane-marching version of this pass measured slower than the row kernel)
-  if (kFused)
-    k_cg_init<T, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
-  else
-    k_cg_init<T, true><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+  if (kFused) {
+    if (jac)
+      k_cg_init<T, false, true><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+    else
+      k_cg_init<T, false, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+  } else {
+    if (jac)
+      k_cg_init<T, true, true><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+    else
+      k_cg_init<T, true, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, P, ld, w.part, ctl);
+  }
   count_launch();
-  k_cg_fin_init<<<fb, 256, 0, st>>>(w.part, nb, ld, p, rtol * rtol, w.state, w.active, ctl);
+  k_cg_fin_init<<<fb, 256, 0, st>>>(w.part, nb, jac ? 3 : 2, ld, p, rtol * rtol, w.state,
+                                    w.active, ctl);
   count_launch();
   prof_end(w.prof, st);
   OP_LAUNCH("k_cg_init");
@@ -639,12 +699,17 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
         count_launch();
         prof_end(w.prof, st);
         prof_begin(w.prof, PK_CG_AXPY, st);
-        k_cg_wr<T><<<grid, s.block, 0, st>>>(g, Vt, sg, W, R, Pn, ld, alpha, nprev, w.part);
+        if (jac)
+          k_cg_wr<T, true><<<grid, s.block, 0, st>>>(g, Vt, sg, W, R, Pn, ld, alpha, nprev,
+                                                      w.part);
+        else
+          k_cg_wr<T, false><<<grid, s.block, 0, st>>>(g, Vt, sg, W, R, Pn, ld, alpha, nprev,
+                                                       w.part);
         count_launch();
         prof_end(w.prof, st);
         prof_begin(w.prof, PK_CG_FIN, st);
-        k_cg_fin_beta<<<fb, 256, 0, st>>>(w.part, nb, ld, w.state, w.active, nprev, nnext,
-                                           ctl + 2);
+        k_cg_fin_beta<<<fb, 256, 0, st>>>(w.part, nb, jac ? 2 : 1, ld, w.state, w.active, nprev,
+                                           nnext, ctl + 2);
         count_launch();
         prof_end(w.prof, st);
       } else {
@@ -657,12 +722,17 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
         count_launch();
         prof_end(w.prof, st);
         prof_begin(w.prof, PK_CG_AXPY, st);
-        k_cg_axpy<T><<<grid, s.block, 0, st>>>(g.n, ld, W, R, P, Q, alpha, nprev, w.part);
+        if (jac)
+          k_cg_axpy<T, true><<<grid, s.block, 0, st>>>(g.n, ld, Vt, sg, W, R, P, Q, alpha, nprev,
+                                                        w.part);
+        else
+          k_cg_axpy<T, false><<<grid, s.block, 0, st>>>(g.n, ld, Vt, sg, W, R, P, Q, alpha,
+                                                         nprev, w.part);
         count_launch();
         prof_end(w.prof, st);
         prof_begin(w.prof, PK_CG_FIN, st);
-        k_cg_fin_beta<<<fb, 256, 0, st>>>(w.part, nb, ld, w.state, w.active, nprev, nnext,
-                                           ctl + 2);
+        k_cg_fin_beta<<<fb, 256, 0, st>>>(w.part, nb, jac ? 2 : 1, ld, w.state, w.active, nprev,
+                                           nnext, ctl + 2);
         count_launch();
         prof_end(w.prof, st);
         prof_begin(w.prof, PK_CG_DIR, st);
@@ -762,24 +832,28 @@ __global__ void __launch_bounds__(256) k_b_cg_init(const BatchProb *__restrict__
     pb.ctl[2] = 0;
   }
   const float *U = pb.U[parity];
-  float acc[2][4] = {};
+  // partials (r.z, u.u, r.r); without the Jacobi preconditioner z = r
+  float acc[3][4] = {};
   if (m.active) {
     const int col = m.tx * 4;
     for (long long i = it.r0 + m.ty; i < it.r1; i += m.rows) {
       const Pack<float> aw = stencil_at(pb.g, pb.Vt, pb.shift, pb.W, ld, i, col, (Pack<float> *)nullptr);
       const long long o = i * (long long)ld + col;
       const Pack<float> u = Pack<float>::load(U + o);
+      const float inv = pb.jacobi ? 1.f / (__ldg(pb.Vt + i) + pb.shift) : 1.f;
       Pack<float> r;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        r.v[k] = u.v[k] - aw.v[k];
-        acc[0][k] += r.v[k] * r.v[k];
+        const float rk = u.v[k] - aw.v[k];
+        r.v[k] = pb.jacobi ? rk * inv : rk;
+        acc[0][k] += rk * r.v[k];
         acc[1][k] += u.v[k] * u.v[k];
+        acc[2][k] += rk * rk;
       }
       r.store(pb.R + o);
     }
   }
-  flat_colsum<2>(acc, m, ld, pb.part + (long long)it.local * 2 * ld);
+  flat_colsum<3>(acc, m, ld, pb.part + (long long)it.local * 3 * ld);
 }
 
 // Finalisers: grid (column warps, problems).
@@ -788,12 +862,13 @@ __global__ void k_b_fin_init(const BatchProb *__restrict__ B) {
   const int ld = pb.ld;
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j >= ld || *pb.frozen) return;
-  const double rr = warp_sum_blocks(pb.part, pb.n_row_items, 2 * ld, j);
-  const double bb = warp_sum_blocks(pb.part, pb.n_row_items, 2 * ld, ld + j);
+  const double rho = warp_sum_blocks(pb.part, pb.n_row_items, 3 * ld, j);
+  const double bb = warp_sum_blocks(pb.part, pb.n_row_items, 3 * ld, ld + j);
+  const double rr = warp_sum_blocks(pb.part, pb.n_row_items, 3 * ld, 2 * ld + j);
   if ((threadIdx.x & 31) == 0) {
     const double rtol2 = *pb.cg_rtol2;
     double *state = pb.state;
-    state[0 * ld + j] = rr;
+    state[0 * ld + j] = rho;
     state[1 * ld + j] = rtol2 * bb;
     state[2 * ld + j] = 0.0;
     state[3 * ld + j] = 0.0;
@@ -867,7 +942,8 @@ __global__ void __launch_bounds__(256) k_b_cg_wr(const BatchProb *__restrict__ B
   const int ld = pb.ld;
   const FlatMap m = flat_map(ld);
   const float *Pn = (k & 1) ? pb.P : pb.Q;
-  float acc[1][4] = {};
+  // partials (r.z, r.r); with the Jacobi preconditioner R holds z = r / d
+  float acc[2][4] = {};
   if (m.active) {
     const int col = m.tx * 4;
     float a[4];
@@ -878,17 +954,30 @@ __global__ void __launch_bounds__(256) k_b_cg_wr(const BatchProb *__restrict__ B
       const Pack<float> q = stencil_at(pb.g, pb.Vt, pb.shift, Pn, ld, i, col, &pc);
       const long long o = i * (long long)ld + col;
       Pack<float> w = Pack<float>::load_rw(pb.W + o), r = Pack<float>::load_rw(pb.R + o);
+      if (pb.jacobi) {
+        const float dg = __ldg(pb.Vt + i) + pb.shift, inv = 1.f / dg;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        w.v[e] += a[e] * pc.v[e];
-        r.v[e] -= a[e] * q.v[e];
-        acc[0][e] += r.v[e] * r.v[e];
+        for (int e = 0; e < 4; ++e) {
+          w.v[e] += a[e] * pc.v[e];
+          r.v[e] -= a[e] * (q.v[e] * inv);
+          const float rk = dg * r.v[e];
+          acc[0][e] += rk * r.v[e];
+          acc[1][e] += rk * rk;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          w.v[e] += a[e] * pc.v[e];
+          r.v[e] -= a[e] * q.v[e];
+          acc[0][e] += r.v[e] * r.v[e];
+          acc[1][e] += r.v[e] * r.v[e];
+        }
       }
       w.store(pb.W + o);
       r.store(pb.R + o);
     }
   }
-  flat_colsum<1>(acc, m, ld, pb.part + (long long)it.local * ld);
+  flat_colsum<2>(acc, m, ld, pb.part + (long long)it.local * 2 * ld);
 }
 
 __global__ void k_b_fin_beta(const BatchProb *__restrict__ B, int k) {
@@ -898,14 +987,15 @@ __global__ void k_b_fin_beta(const BatchProb *__restrict__ B, int k) {
   const int ld = pb.ld;
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j >= ld) return;
-  const double rrn = warp_sum_blocks(pb.part, pb.n_row_items, ld, j);
+  const double rhon = warp_sum_blocks(pb.part, pb.n_row_items, 2 * ld, j);
+  const double rrn = warp_sum_blocks(pb.part, pb.n_row_items, 2 * ld, ld + j);
   if ((threadIdx.x & 31) == 0) {
     double *state = pb.state;
-    const double rr = state[j];
+    const double rho = state[j];
     int a = pb.active[j];
-    state[3 * ld + j] = (a && rr > 0.0) ? rrn / rr : 0.0;
+    state[3 * ld + j] = (a && rho > 0.0) ? rhon / rho : 0.0;
     if (a) {
-      state[j] = rrn;
+      state[j] = rhon;
       a = rrn > state[ld + j];
       pb.active[j] = a;
     }

@@ -61,7 +61,7 @@ def _init_status(pb, V, U0):
     return s, ctx, b.last_error()
 
 
-@pytest.mark.parametrize("bad", ["dim", "p0", "shape", "box", "prec", "null"])
+@pytest.mark.parametrize("bad", ["dim", "p0", "shape", "box", "prec", "precond", "null"])
 def test_init_rejects_bad_arguments_before_any_device_work(lib, bad):
     from paper_2511_06788_gb300 import binding as b
     pb = b.make_problem((4, 4), (0, 0), (1, 1), 2)
@@ -78,6 +78,8 @@ def test_init_rejects_bad_arguments_before_any_device_work(lib, bad):
         pb.hi[0] = pb.lo[0]
     elif bad == "prec":
         pb.prec = 9
+    elif bad == "precond":
+        pb.cg_precond = 2
     elif bad == "null":
         Vp = None
     s, ctx, msg = _init_status(pb, Vp, Up)

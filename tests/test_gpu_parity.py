@@ -209,8 +209,9 @@ def _square(K, ld, dtype):
     return out
 
 
+@pytest.mark.parametrize("precond", ["none", "jacobi"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_cg_solve_matches_oracle(prec):
+def test_cg_solve_matches_oracle(prec, precond):
     shape, lo, hi, p = (20, 22, 18), (-8.0,) * 3, (8.0,) * 3, 12
     n = int(np.prod(shape))
     V = rounded(random_potential(shape, lo, hi, 3), prec)
@@ -221,7 +222,8 @@ def test_cg_solve_matches_oracle(prec):
     ld = ld_of(p)
     Ut, Wt = padded(U, ld, DT[prec]), torch.zeros(n, ld, dtype=DT[prec], device=DEV)
     rtol = 1e-12 if prec == "fp64" else 1e-6
-    it = pkg.cg_solve(shape, lo, hi, torch.from_numpy(V).to(DEV, DT[prec]), sigma, Ut, Wt, p, rtol)
+    it = pkg.cg_solve(shape, lo, hi, torch.from_numpy(V).to(DEV, DT[prec]), sigma, Ut, Wt, p, rtol,
+                      precond=precond)
     assert 0 < it < 5000
     W = Wt.double().cpu().numpy()
     # ||W - G U|| <= ||G|| ||residual|| <= (1/lambda_min(H + sigma)) rtol ||u||
@@ -266,6 +268,48 @@ def test_cg_plane_marching_iterates_match_oracle(geom):
     lam_min = o.spectrum_lower_bound(shape, lo, hi, V) + sigma
     err = np.linalg.norm(Wt.double().cpu().numpy()[:, :p] - W_exact, axis=0)
     assert 0 < it < 5000 and np.all(err <= 30 * 1e-6 / lam_min)
+
+
+@pytest.mark.parametrize("prec,geom", [("fp32", TMA_GEOMS[0]), ("fp32", TMA_GEOMS[3]),
+                                       ("fp32", ((17, 15), 24)), ("fp64", ((13, 9, 11), 40)),
+                                       ("fp64", ((17, 15), 12))],
+                         ids=lambda g: g if isinstance(g, str) else
+                         "x".join(map(str, g[0])) + f"_p{g[1]}")
+def test_jacobi_cg_iterates_match_oracle(prec, geom):
+    """W after k Jacobi-preconditioned CG iterations equals the oracle's block_pcg_jacobi
+    after k iterations (3-D FP32: TMA direction kernel; 2-D FP32: row kernels; FP64:
+    the three-kernel iteration)."""
+    shape, p = geom
+    lo, hi = (-4.0,) * len(shape), (4.0,) * len(shape)
+    n = int(np.prod(shape))
+    V = rounded(random_potential(shape, lo, hi, 5), prec)
+    sigma = o.default_sigma(shape, lo, hi, V)
+    U = rounded(o.householder_orthonormalize(syn.gaussian_block(6, n, p)), prec)
+    W0 = rounded(0.05 * syn.gaussian_block(7, n, p), prec)
+    A = (o.hamiltonian(shape, lo, hi, V) + sigma * sp_identity(n)).tocsr()
+    ld = ld_of(p)
+    Vt = torch.from_numpy(V).to(DEV, DT[prec])
+    Ut = padded(U, ld, DT[prec])
+    tol = 2e-5 if prec == "fp32" else 1e-12
+    for k in (1, 2, 5):
+        Wt = padded(W0, ld, DT[prec])
+        it = pkg.cg_solve(shape, lo, hi, Vt, sigma, Ut, Wt, p, 1e-30, max_iter=k,
+                          precond="jacobi")
+        assert it == k
+        W = Wt.double().cpu().numpy()
+        W_ref, _ = o.block_pcg_jacobi(A, U, W0, rtol=0.0, max_iter=k)
+        err = np.abs(W[:, :p] - W_ref).max() / np.abs(W_ref).max()
+        assert err < tol, (k, err)
+        assert np.all(W[:, p:] == 0)
+    # to convergence: the stopping test is on the unpreconditioned residual
+    rtol = 1e-6 if prec == "fp32" else 1e-12
+    Wt = padded(W0, ld, DT[prec])
+    it = pkg.cg_solve(shape, lo, hi, Vt, sigma, Ut, Wt, p, rtol, precond="jacobi")
+    W = Wt.double().cpu().numpy()[:, :p]
+    res = np.linalg.norm(U - A @ W, axis=0) / np.linalg.norm(U, axis=0)
+    _, it_ref = o.block_pcg_jacobi(A, U, W0, rtol=rtol)
+    assert np.all(res <= (5.0 if prec == "fp32" else 1.5) * rtol), res.max()
+    assert abs(it - it_ref) <= (3 if prec == "fp32" else 1), (it, it_ref)
 
 
 def sp_identity(n):
