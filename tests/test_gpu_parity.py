@@ -301,15 +301,23 @@ def test_jacobi_cg_iterates_match_oracle(prec, geom):
         err = np.abs(W[:, :p] - W_ref).max() / np.abs(W_ref).max()
         assert err < tol, (k, err)
         assert np.all(W[:, p:] == 0)
-    # to convergence: the stopping test is on the unpreconditioned residual
+    # to convergence: the stopping test is on the unpreconditioned (recursively updated)
+    # residual; in FP32 the true residual of the result also carries the rounding of
+    # the updates, so it is checked like the plain CG's: through the solution error
+    # ||W - G U|| <= ||G|| ||residual|| <= rtol ||u|| / lambda_min(H + sigma)
     rtol = 1e-6 if prec == "fp32" else 1e-12
     Wt = padded(W0, ld, DT[prec])
     it = pkg.cg_solve(shape, lo, hi, Vt, sigma, Ut, Wt, p, rtol, precond="jacobi")
     W = Wt.double().cpu().numpy()[:, :p]
-    res = np.linalg.norm(U - A @ W, axis=0) / np.linalg.norm(U, axis=0)
     _, it_ref = o.block_pcg_jacobi(A, U, W0, rtol=rtol)
-    assert np.all(res <= (5.0 if prec == "fp32" else 1.5) * rtol), res.max()
     assert abs(it - it_ref) <= (3 if prec == "fp32" else 1), (it, it_ref)
+    W_exact = o.SourceSolver(o.hamiltonian(shape, lo, hi, V), sigma).solve(U)
+    lam_min = o.spectrum_lower_bound(shape, lo, hi, V) + sigma
+    err = np.linalg.norm(W - W_exact, axis=0)
+    assert np.all(err <= 30 * rtol / lam_min), err.max()
+    if prec == "fp64":
+        res = np.linalg.norm(U - A @ W, axis=0) / np.linalg.norm(U, axis=0)
+        assert np.all(res <= 1.5 * rtol), res.max()
 
 
 def sp_identity(n):
