@@ -201,20 +201,28 @@ __global__ void k_tri_cols(int p, int ld, const double *__restrict__ L, int mode
   for (int i = t; i < ld; i += nt) out[(long long)i * ld + j] = (i < p) ? y[i] : 0.0;
 }
 
-// Inverse of the p x p matrix M (stride ld, p <= 128) in FP32 by Gauss-Jordan
+// Inverse of the p x p matrix M (stride ld, p <= 128) in FP32 by blocked Gauss-Jordan
 // elimination without pivoting, one CTA of 32 x 32 threads.  [M | I] is padded to
-// 128 x 256 with an identity block and held in registers: thread (tx, ty) owns
-// rows ty + 32a (a < 4) and columns tx + 32b (b < 8).  Step k publishes row k
-// and column k through shared memory (double-buffered: one barrier per step) and
-// every thread updates its 32 entries.  The result seeds the FP64 Newton-Schulz
-// refinement in core(): on GB300 an FP64 factorisation on one SM costs
-// ~p^3/3 / (2 FMA/clk), while FP32 runs 64x faster.
+// 128 x 256 with an identity block and held in registers: thread (tx, ty) owns rows
+// ty + 32a (a < 4) and columns tx + 32b (b < 8).  The 128 pivots are taken in 16
+// groups K of kG = 8.  For a group, with P = A[K, K]:
+//   A[K, :] <- P^-1 A[K, :]                       (the pivot rows, Z)
+//   A[i, :] <- A[i, :] - A[i, K] Z    (i not in K)
+// which equals kG single-pivot steps in exact arithmetic.  Per group the pivot rows and
+// columns are published to shared memory, 256 threads form Z column by column (each
+// Gauss-Jordan on the kG x 256 panel), and every thread applies the rank-kG update to
+// its 32 entries.  The panel elimination synchronises only the 8 warps that hold it.
+// The result seeds the FP64 Newton-Schulz refinement in core(); on GB300 an FP64
+// factorisation on one SM costs ~p^3/3 / (2 FMA/clk), while FP32 runs 64x faster.
 // status <- 1 on a zero or non-finite pivot.
+constexpr int kG = 8;
 __device__ __forceinline__ void gj32_body(int p, int ld, const double *__restrict__ M,
                                           double *__restrict__ X, int *status) {
-  __shared__ float rowk[2][256];
-  __shared__ float colk[2][128];
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  __shared__ float rowblk[kG][256];  // A[K, :]
+  __shared__ float colblk[128][kG];  // A[:, K]
+  __shared__ float zblk[kG][256];    // P^-1 A[K, :]
+  __shared__ float pcol[2][kG];      // pivot column of the panel elimination (double-buffered)
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
   float v[4][8];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -228,51 +236,73 @@ __device__ __forceinline__ void gj32_body(int p, int ld, const double *__restric
     }
   bool bad = false;
 #pragma unroll 1
-  for (int ak = 0; ak < 4; ++ak) {
-#pragma unroll 1
-    for (int rk = 0; rk < 32; ++rk) {
-      const int k = 32 * ak + rk, buf = k & 1;
-      // publish row k (owners: ty == rk) and column k (owners: tx == rk)
+  for (int k0 = 0; k0 < 128; k0 += kG) {
+    const int ak = k0 >> 5, r0 = k0 & 31;
+    // publish the pivot rows (owners: a == ak, ty in [r0, r0 + kG)) and columns
+    // (owners: b == ak, tx in [r0, r0 + kG))
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        if (a == ak && ty == rk) {
+    for (int a = 0; a < 4; ++a)
+      if (a == ak && ty >= r0 && ty < r0 + kG) {
 #pragma unroll
-          for (int b = 0; b < 8; ++b) rowk[buf][tx + 32 * b] = v[a][b];
-        }
+        for (int b = 0; b < 8; ++b) rowblk[ty - r0][tx + 32 * b] = v[a][b];
       }
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        if (b == ak && tx == rk) {
+    for (int b = 0; b < 4; ++b)
+      if (b == ak && tx >= r0 && tx < r0 + kG) {
 #pragma unroll
-          for (int a = 0; a < 4; ++a) colk[buf][ty + 32 * a] = v[a][b];
-        }
+        for (int a = 0; a < 4; ++a) colblk[ty + 32 * a][tx - r0] = v[a][b];
       }
-      __syncthreads();
-      const float d = rowk[buf][k];
-      if (!(fabsf(d) > 1e-30f) || !isfinite(d)) {
-        bad = true;  // uniform: every thread reads the same pivot
-        break;
-      }
-      const float pinv = 1.f / d;
-      // pivot row and this thread's column multipliers, read once per pivot
-      float r[8], f[4];
+    __syncthreads();
+    // Z = P^-1 A[K, :]: Gauss-Jordan on the kG x 256 panel A[K, :], thread t < 256
+    // holding column t; the pivot column of step c is column k0 + c, published by its
+    // owner (warps 0..7 synchronise among themselves with barrier 1)
+    bool fail = false;
+    if (t < 256) {
+      float z[kG];
 #pragma unroll
-      for (int b = 0; b < 8; ++b) r[b] = rowk[buf][tx + 32 * b];
+      for (int r = 0; r < kG; ++r) z[r] = rowblk[r][t];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) f[a] = colk[buf][ty + 32 * a] * pinv;
+      for (int c = 0; c < kG; ++c) {
+        if (t == k0 + c) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 8; ++b) v[a][b] = fmaf(-f[a], r[b], v[a][b]);
-      // row k itself becomes the scaled pivot row
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-        if (a == ak && ty == rk) {
-#pragma unroll
-          for (int b = 0; b < 8; ++b) v[a][b] = r[b] * pinv;
+          for (int r = 0; r < kG; ++r) pcol[c & 1][r] = z[r];
         }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        const float d = pcol[c & 1][c];
+        if (!(fabsf(d) > 1e-30f) || !isfinite(d)) fail = true;  // uniform
+        const float zc = z[c] / d;
+#pragma unroll
+        for (int r = 0; r < kG; ++r) z[r] = (r == c) ? zc : fmaf(-pcol[c & 1][r], zc, z[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < kG; ++r) zblk[r][t] = z[r];
     }
-    if (bad) break;
+    if (__syncthreads_or(fail)) {
+      bad = true;
+      break;
+    }
+    // rank-kG update of this thread's entries (one multiplier and one Z value per load,
+    // applied to all four rows); the pivot rows become Z
+    const bool own = ty >= r0 && ty < r0 + kG;
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+      float c[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) c[a] = (a == ak && own) ? 0.f : colblk[ty + 32 * a][g];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const float zv = zblk[g][tx + 32 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a][b] = fmaf(-c[a], zv, v[a][b]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+      if (a == ak && own) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) v[a][b] = zblk[ty - r0][tx + 32 * b];
+      }
+    __syncthreads();  // rowblk / colblk / zblk are rewritten by the next group
   }
   if (bad) {
     if (tx == 0 && ty == 0) *status = 1;
