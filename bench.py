@@ -752,13 +752,15 @@ def run_ttr(args):
     milestones = [1e-3, 1e-4, 1e-5, 1e-6]
     rows, lams = {}, {}
     for mode in args.ttr_modes.split(","):
-        prec, _, adapt = mode.partition("+adapt")   # e.g. "fp32+adapt100"
-        adapt = int(adapt) if adapt else 0
+        # e.g. "fp32+adapt100"; "+plain" selects the unpreconditioned Step-1 CG
+        prec, *opts = mode.split("+")
+        adapt = next((int(o[5:]) for o in opts if o.startswith("adapt")), 0)
+        precond = "none" if "plain" in opts else "jacobi"
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         hit, k, r = {}, 0, float("inf")
         with pkg.Solver(P.shape, P.lo, P.hi, V_d, U0_d, P.p, prec=prec, device=True,
-                        adapt_every=adapt) as s:
+                        adapt_every=adapt, precond=precond) as s:
             while k < args.ttr_cap and len(hit) < len(milestones):
                 if adapt:
                     # re-tuning runs inside op_solve (stop rule: steps), which ends
