@@ -189,50 +189,64 @@ __global__ void __launch_bounds__(256, 1)
                  err, split);
 }
 
-// ---- persistent, TMA-fed variant (ld a multiple of 32) --------------------------------
+// ---- persistent, warp-specialised variant (ld a multiple of 32) ----------------------
 // The same products, split and accumulation order as update_tc_body, so the result is
-// bit-identical; only the staging differs.  One CTA per SM walks the output tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ... (consecutive tiles share their rows of
-// [U W] through L2 when ld > 128).  A producer warp streams the (tile, slab)
-// sequence into a ring of kRing stages with TMA: the A slab (128 grid points x 32 K
-// values of U or W) and the B slabs (128 columns of KT_hi / KT_lo), each landing
-// directly in the 128B-swizzled K-major layout.  The 8 compute warps split the A slab
-// into TF32 hi (in place) and lo, thread 0 issues the MMAs into one of two TMEM
-// accumulators and commits them to the accumulator's barrier and the stage's "empty"
-// barrier, and the warps drain the previous slab into FP32 registers meanwhile.
+// bit-identical; only the staging and the division of labour differ.  One CTA per SM
+// walks the output tiles blockIdx.x, blockIdx.x + gridDim.x, ... (consecutive tiles share
+// their rows of [U W] through L2 when ld > 128), slab by slab, with four roles that
+// meet only at mbarriers, so the tensor core is fed while earlier slabs drain:
+//   warp 9, lane 0  TMA producer: the A slab (128 grid points x 32 K values of U or W)
+//                   and the B slabs (128 columns of KT_hi / KT_lo) into a ring of kRing
+//                   stages, each landing in the 128B-swizzled K-major layout;
+//   warps 4..7      split the A slab into TF32 hi (in place) and lo;
+//   warp 8, lane 0  issues the slab's MMAs into one of kAcc TMEM accumulators and
+//                   commits them to that accumulator's "done" barrier and the stage's
+//                   "empty" barrier;
+//   warps 0..3      drain each accumulator into FP32 registers (one tile row per thread,
+//                   all 128 columns), free it, and store U + acc when a tile ends.
+// Every wait is bounded in time; a role that gives up raises a flag the others poll.
 constexpr int kRing = 3;
+constexpr int kAcc = 4;
 constexpr int kStageR = 4 * kPieceA;  // A hi (TMA destination, split in place) | A lo | B hi | B lo
 constexpr int kSmemR = kRing * kStageR + 1024;
-constexpr uint64_t kWaitNs = 2000000000ull;  // every TMA-side wait gives up after 2 s
-constexpr int kComputeThreads = 256;
+constexpr uint64_t kWaitNs = 2000000000ull;  // every wait gives up after 2 s
+constexpr int kWarpsWS = 10;
 
-__device__ __forceinline__ void compute_bar() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kComputeThreads) : "memory");
-}
-// Barrier of the compute warps that also ORs a predicate over them: every thread gets
-// the same answer, so all leave the pipeline together.
-__device__ __forceinline__ bool compute_bar_or(bool pred) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "barrier.cta.red.or.pred q, 1, %2, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}\n"
-      : "=r"(r)
-      : "r"((uint32_t)pred), "n"(kComputeThreads)
-      : "memory");
-  return r != 0;
+// Wait for the phase of `parity` of `bar`; false after kWaitNs or once *abort is set.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
+                                              volatile int *abort) {
+  const uint32_t a = tc::smem_u32(bar);
+  uint64_t t0 = 0;
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*abort) return false;
+    const uint64_t now = tma::global_ns();
+    if (t0 == 0) {
+      t0 = now;
+    } else if (now - t0 > kWaitNs) {
+      *abort = 1;
+      return false;
+    }
+  }
 }
 
-__global__ void __launch_bounds__(kComputeThreads + 32, 1)
-    k_update_tma(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mW,
-                 const __grid_constant__ CUtensorMap mKh, const __grid_constant__ CUtensorMap mKl,
-                 long long n, int ld, const float *__restrict__ U, float *__restrict__ Unew,
-                 int *err, int split) {
+__global__ void __launch_bounds__(kWarpsWS * 32, 1)
+    k_update_ws(const __grid_constant__ CUtensorMap mU, const __grid_constant__ CUtensorMap mW,
+                const __grid_constant__ CUtensorMap mKh, const __grid_constant__ CUtensorMap mKl,
+                long long n, int ld, const float *__restrict__ U, float *__restrict__ Unew,
+                int *err, int split) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t full[kRing], empty[kRing], done[2];
+  __shared__ uint64_t full[kRing], empty[kRing], conv[kRing], done[kAcc], freed[kAcc];
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int abort_sh;  // set by compute thread 0 when the pipeline stops early
+  __shared__ int abort_sh;
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -241,15 +255,19 @@ __global__ void __launch_bounds__(kComputeThreads + 32, 1)
   const long long ntiles = (n + kTM - 1) / kTM * ntn;
   const long long mine =
       ntiles > (long long)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long total = mine * nslab;
 
-  if (warp == 0) tc::tmem_alloc(&tmem_base_sh, 2 * kTN);
+  if (warp == 0) tc::tmem_alloc(&tmem_base_sh, kAcc * kTN);
   if (t == 0) {
     for (int i = 0; i < kRing; ++i) {
       tma::bar_init(&full[i], 1);
       tma::bar_init(&empty[i], 1);
+      tma::bar_init(&conv[i], 128);
     }
-    tma::bar_init(&done[0], 1);
-    tma::bar_init(&done[1], 1);
+    for (int i = 0; i < kAcc; ++i) {
+      tma::bar_init(&done[i], 1);
+      tma::bar_init(&freed[i], 128);
+    }
     tma::fence_bar_init();
     abort_sh = 0;
   }
@@ -257,157 +275,147 @@ __global__ void __launch_bounds__(kComputeThreads + 32, 1)
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
+  volatile int *abort = &abort_sh;
 
-  if (warp == kComputeThreads / 32) {  // producer warp
-    if (lane != 0) return;
-    long long issued = 0;
-    bool ok = true;
-    for (long long i = 0; i < mine && ok; ++i) {
-      const long long tile = blockIdx.x + i * gridDim.x;
-      const int m0 = (int)(tile / ntn) * kTM, n0 = (int)(tile % ntn) * kTN;
-      for (int s = 0; s < nslab; ++s, ++issued) {
-        const int st = (int)(issued % kRing);
-        // the stage's previous slab must have been read by its MMAs
-        if (issued >= kRing &&
-            !tma::bar_wait(&empty[st], (uint32_t)((issued / kRing - 1) & 1), kWaitNs)) {
-          atomicExch(err, 1);  // the compute warps then time out on this slab
-          ok = false;
+  if (warp == 9) {
+    if (lane == 0) {  // ---- TMA producer
+      long long g = 0;
+      bool ok = true;
+      for (long long i = 0; i < mine && ok; ++i) {
+        const long long tile = blockIdx.x + i * gridDim.x;
+        const int m0 = (int)(tile / ntn) * kTM, n0 = (int)(tile % ntn) * kTN;
+        for (int s = 0; s < nslab; ++s, ++g) {
+          const int st = (int)(g % kRing);
+          // the stage's previous slab must have been read by its MMAs
+          if (g >= kRing && !wait_or_abort(&empty[st], (uint32_t)((g / kRing - 1) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          uint8_t *stage = smem + st * kStageR;
+          const int k0 = s * kKS;
+          tma::bar_expect(&full[st], (uint32_t)((split ? 3 : 2) * kPieceA));
+          if (k0 < ld)
+            tma::load_2d(stage, &mU, k0, m0, &full[st]);
+          else
+            tma::load_2d(stage, &mW, k0 - ld, m0, &full[st]);
+          tma::load_2d(stage + 2 * kPieceA, &mKh, k0, n0, &full[st]);
+          if (split) tma::load_2d(stage + 3 * kPieceA, &mKl, k0, n0, &full[st]);
         }
-        if (*(volatile int *)&abort_sh) ok = false;
-        if (!ok) break;
-        uint8_t *stage = smem + st * kStageR;
-        const int k0 = s * kKS;
-        tma::bar_expect(&full[st], (uint32_t)((split ? 3 : 2) * kPieceA));
-        if (k0 < ld)
-          tma::load_2d(stage, &mU, k0, m0, &full[st]);
-        else
-          tma::load_2d(stage, &mW, k0 - ld, m0, &full[st]);
-        tma::load_2d(stage + 2 * kPieceA, &mKh, k0, n0, &full[st]);
-        if (split) tma::load_2d(stage + 3 * kPieceA, &mKl, k0, n0, &full[st]);
+      }
+      if (!ok) {
+        atomicExch(err, 1);
+        // copies still in flight land before the CTA may exit (only the last kRing can be)
+        for (long long q = (g > kRing ? g - kRing : 0); q < g; ++q)
+          (void)tma::bar_wait(&full[q % kRing], (uint32_t)((q / kRing) & 1), kWaitNs);
       }
     }
-    // copies still in flight land before the CTA may exit (only the last kRing can be)
-    if (!ok)
-      for (long long q = (issued > kRing ? issued - kRing : 0); q < issued; ++q)
-        (void)tma::bar_wait(&full[q % kRing], (uint32_t)((q / kRing) & 1), kWaitNs);
-    return;
-  } else {
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    const int drow = (warp & 3) * 32 + lane;  // drain: tile row (TMEM lane)
-    const int half = warp >> 2;               // drain: columns 64 half .. 64 half + 63
-    float acc[64];
+  } else if (warp == 8) {
+    if (lane == 0) {  // ---- MMA issuer
+      long long g = 0;
+      for (; g < total; ++g) {
+        const int st = (int)(g % kRing), a = (int)(g % kAcc);
+        if (!wait_or_abort(&conv[st], (uint32_t)((g / kRing) & 1), abort)) break;
+        if (g >= kAcc && !wait_or_abort(&freed[a], (uint32_t)((g / kAcc - 1) & 1), abort)) break;
+        tc::tc_fence_after();
+        const uint32_t base = tc::smem_u32(smem + st * kStageR);
+        const uint32_t d = tmem + (uint32_t)(a * kTN);
 #pragma unroll
-    for (int i = 0; i < 64; ++i) acc[i] = 0.f;
-
-    auto drain = [&](long long g) -> bool {
-      const int a = (int)(g & 1);
-      if (compute_bar_or(t == 0 && !tc::mbar_wait(&done[a], (uint32_t)((g >> 1) & 1))))
-        return false;
-      tc::tc_fence_after();
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        float v[32];
-        tc::tmem_ld32(tmem + lane_base + (uint32_t)(a * kTN + half * 64 + c * 32), v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
-      }
-      tc::tc_fence_before();
-      return true;
-    };
-    auto epilogue = [&](long long tile) {
-      const long long row = (tile / ntn) * kTM + drow;
-      const int n0 = (int)(tile % ntn) * kTN;
-      if (row < n) {
-#pragma unroll
-        for (int i = 0; i < 64; i += 4) {
-          const int col = n0 + half * 64 + i;
-          if (col < ld) {
-            const float4 u = __ldg(reinterpret_cast<const float4 *>(U + row * ld + col));
-            *reinterpret_cast<float4 *>(Unew + row * ld + col) =
-                make_float4(u.x + acc[i], u.y + acc[i + 1], u.z + acc[i + 2], u.w + acc[i + 3]);
+        for (int kk = 0; kk < kKS / 8; ++kk) {
+          const uint64_t ah = tc::desc_sw128(base + kk * 32);
+          const uint64_t al = tc::desc_sw128(base + kPieceA + kk * 32);
+          const uint64_t bh = tc::desc_sw128(base + 2 * kPieceA + kk * 32);
+          const uint64_t bl = tc::desc_sw128(base + 3 * kPieceA + kk * 32);
+          tc::mma_tf32(d, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
+          if (split) {
+            tc::mma_tf32(d, ah, bl, kIdesc, 1u);
+            tc::mma_tf32(d, al, bh, kIdesc, 1u);
           }
         }
+        tc::mma_commit(&done[a]);
+        tc::mma_commit(&empty[st]);
       }
+      if (g < total) {
+        atomicExch(err, 1);
+        // MMAs issued but not drained: let them finish before the TMEM is freed
+        if (g > 0) {
+          const long long q = g - 1;
+          (void)tc::mbar_wait(&done[q % kAcc], (uint32_t)((q / kAcc) & 1));
+        }
+      }
+    }
+  } else if (warp >= 4) {  // ---- splitters (warps 4..7)
+    const int ct = t - 128;
+    for (long long g = 0; g < total; ++g) {
+      const int st = (int)(g % kRing);
+      if (!wait_or_abort(&full[st], (uint32_t)((g / kRing) & 1), abort)) break;
+      uint8_t *stage = smem + st * kStageR;
+      // 1024 16-byte chunks of the A slab, 8 per thread (any bijection of chunks keeps
+      // hi and lo in the same swizzled positions)
 #pragma unroll
-      for (int i = 0; i < 64; ++i) acc[i] = 0.f;
-    };
-
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t off = (uint32_t)(ct + 128 * j) * 16u;
+        float4 *pa = reinterpret_cast<float4 *>(stage + off);
+        const float4 x = *pa;
+        float4 h, l;
+        tc::split_tf32(x.x, h.x, l.x);
+        tc::split_tf32(x.y, h.y, l.y);
+        tc::split_tf32(x.z, h.z, l.z);
+        tc::split_tf32(x.w, h.w, l.w);
+        *pa = h;
+        if (split) *reinterpret_cast<float4 *>(stage + kPieceA + off) = l;
+      }
+      tc::fence_async_smem();
+      tma::bar_arrive(&conv[st]);
+    }
+  } else {  // ---- drain and epilogue (warps 0..3: TMEM lanes 32 warp .. 32 warp + 31)
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int trow = warp * 32 + lane;
+    float acc[128];
+#pragma unroll
+    for (int i = 0; i < 128; ++i) acc[i] = 0.f;
+    long long g = 0;
     bool ok = true;
-    long long g = 0;          // slabs consumed (their MMAs issued)
-    long long committed = 0;  // thread 0: MMA groups committed
     for (long long i = 0; i < mine && ok; ++i) {
-      for (int s = 0; s < nslab; ++s) {
-        const int st = (int)(g % kRing);
-        uint8_t *stage = smem + st * kStageR;
-        if (compute_bar_or(t == 0 &&
-                           !tma::bar_wait(&full[st], (uint32_t)((g / kRing) & 1), kWaitNs))) {
+      for (int s = 0; s < nslab; ++s, ++g) {
+        const int a = (int)(g % kAcc);
+        if (!wait_or_abort(&done[a], (uint32_t)((g / kAcc) & 1), abort)) {
           ok = false;
           break;
         }
-        // split the A slab: 1024 16-byte chunks, 4 per thread (any bijection of chunks
-        // keeps hi and lo in the same swizzled positions)
+        tc::tc_fence_after();
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t off = (uint32_t)(t + kComputeThreads * j) * 16u;
-          float4 *pa = reinterpret_cast<float4 *>(stage + off);
-          const float4 x = *pa;
-          float4 h, l;
-          tc::split_tf32(x.x, h.x, l.x);
-          tc::split_tf32(x.y, h.y, l.y);
-          tc::split_tf32(x.z, h.z, l.z);
-          tc::split_tf32(x.w, h.w, l.w);
-          *pa = h;
-          if (split) *reinterpret_cast<float4 *>(stage + kPieceA + off) = l;
+        for (int c = 0; c < 4; ++c) {
+          float v[32];
+          tc::tmem_ld32(tmem + lane_base + (uint32_t)(a * kTN + c * 32), v);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) acc[c * 32 + e] += v[e];
         }
-        tc::fence_async_smem();
         tc::tc_fence_before();
-        compute_bar();
-        if (t == 0) {
-          tc::tc_fence_after();
-          const uint32_t base = tc::smem_u32(stage);
-          const uint32_t d = tmem + (uint32_t)((g & 1) * kTN);
+        tma::bar_arrive(&freed[a]);
+      }
+      if (!ok) break;
+      const long long tile = blockIdx.x + i * gridDim.x;
+      const long long row = (tile / ntn) * kTM + trow;
+      const int n0 = (int)(tile % ntn) * kTN;
+      if (row < n) {
 #pragma unroll
-          for (int kk = 0; kk < kKS / 8; ++kk) {
-            const uint64_t ah = tc::desc_sw128(base + kk * 32);
-            const uint64_t al = tc::desc_sw128(base + kPieceA + kk * 32);
-            const uint64_t bh = tc::desc_sw128(base + 2 * kPieceA + kk * 32);
-            const uint64_t bl = tc::desc_sw128(base + 3 * kPieceA + kk * 32);
-            tc::mma_tf32(d, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
-            if (split) {
-              tc::mma_tf32(d, ah, bl, kIdesc, 1u);
-              tc::mma_tf32(d, al, bh, kIdesc, 1u);
-            }
+        for (int c = 0; c < 128; c += 4) {
+          const int col = n0 + c;
+          if (col < ld) {
+            const float4 u = __ldg(reinterpret_cast<const float4 *>(U + row * ld + col));
+            *reinterpret_cast<float4 *>(Unew + row * ld + col) =
+                make_float4(u.x + acc[c], u.y + acc[c + 1], u.z + acc[c + 2], u.w + acc[c + 3]);
           }
-          tc::mma_commit(&done[g & 1]);
-          tc::mma_commit(&empty[st]);
-          committed = g + 1;
-        }
-        ++g;
-        if (g >= 2) {
-          ok = drain(g - 2);
-          if (!ok) break;
-          // the drained slab closed a tile: write that tile
-          if (s == 0) epilogue(blockIdx.x + (i - 1) * gridDim.x);
         }
       }
+#pragma unroll
+      for (int c = 0; c < 128; ++c) acc[c] = 0.f;
     }
-    if (ok && g >= 1) {
-      ok = drain(g - 1);
-      if (ok) epilogue(blockIdx.x + (mine - 1) * gridDim.x);
-    }
-    if (t == 0 && !ok) {
-      abort_sh = 1;  // stops the producer
-      atomicExch(err, 1);
-      // MMAs issued but not drained: let them finish before the TMEM is freed
-      if (committed > 0) {
-        const long long q = committed - 1;
-        (void)tc::mbar_wait(&done[q & 1], (uint32_t)((q >> 1) & 1));
-      }
-    }
+    if (!ok && lane == 0) atomicExch(err, 1);
   }
   tc::tc_fence_before();
-  compute_bar();
-  if (warp == 0) tc::tmem_dealloc(tmem, 2 * kTN);
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kAcc * kTN);
 }
 
 // Batched: one CTA per TileItem (problem, 128-point tile, column tile); U -> U+.
@@ -499,12 +507,12 @@ op_status update_tc(long long n, int ld, const float *U, const float *W, const f
     OP_TRY(tma_map_2d_f32_sw128(&mKl, KT_lo, 2 * ld, ld, kTN));
     const long long ntiles = (n + kTM - 1) / kTM * ((ld + kTN - 1) / kTN);
     const int grid = (int)std::min<long long>(ntiles, kNumSMs);
-    OP_CUDA(cudaFuncSetAttribute(k_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    OP_CUDA(cudaFuncSetAttribute(k_update_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemR));
-    k_update_tma<<<grid, kComputeThreads + 32, kSmemR, st>>>(mU, mW, mKh, mKl, n, ld, U, Unew,
-                                                             err, split);
+    k_update_ws<<<grid, kWarpsWS * 32, kSmemR, st>>>(mU, mW, mKh, mKl, n, ld, U, Unew, err,
+                                                     split);
     count_launch();
-    OP_LAUNCH("k_update_tma");
+    OP_LAUNCH("k_update_ws");
     return OP_OK;
   }
   OP_CUDA(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
