@@ -356,14 +356,17 @@ __global__ void k_core_stats(int p, int ld, const double *__restrict__ C,
                              double *out) {
   __shared__ double sh[32];
   double trs = 0.0, cc = 0.0, dd = 0.0;
-  for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x) {
-    const int i = (int)(e / p), j = (int)(e % p);
-    const long long o = (long long)i * ld + j;
-    if (S && i == j) trs += S[o];
-    if (C) cc += C[o] * C[o];
-    if (D) {
-      const double d = D[o] - (i == j ? 1.0 : 0.0);
-      dd += d * d;
+  // one warp per row, lanes along the row (no index division)
+  const int nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x >> 5; i < p; i += nw) {
+    if (S && lane == 0) trs += S[(long long)i * ld + i];
+    for (int j = lane; j < p; j += 32) {
+      const long long o = (long long)i * ld + j;
+      if (C) cc += C[o] * C[o];
+      if (D) {
+        const double d = D[o] - (i == j ? 1.0 : 0.0);
+        dd += d * d;
+      }
     }
   }
   trs = block_sum(trs, sh);
@@ -554,13 +557,16 @@ __global__ void k_b_core_misc(const BatchProb *__restrict__ Bp, int stage) {
     __shared__ double sh[32];
     if (threadIdx.x == 0) *pb.core_status = 0;
     double trs = 0.0, cc = 0.0, dd = 0.0;
-    for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x) {
-      const int i = (int)(e / p), j = (int)(e % p);
-      const long long o = (long long)i * ld + j;
-      if (i == j) trs += pb.S[o];
-      cc += pb.C[o] * pb.C[o];
-      const double d = pb.D[o] - (i == j ? 1.0 : 0.0);
-      dd += d * d;
+    // one warp per row, lanes along the row (no index division)
+    const int nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x >> 5; i < p; i += nw) {
+      if (lane == 0) trs += pb.S[(long long)i * ld + i];
+      for (int j = lane; j < p; j += 32) {
+        const long long o = (long long)i * ld + j;
+        cc += pb.C[o] * pb.C[o];
+        const double d = pb.D[o] - (i == j ? 1.0 : 0.0);
+        dd += d * d;
+      }
     }
     trs = block_sum(trs, sh);
     cc = block_sum(cc, sh);
