@@ -404,17 +404,8 @@ __global__ void __launch_bounds__(256) k_cg_wr(Geom g, const T *__restrict__ Vt,
 // ---- finalisers: one warp per column, lanes stride over the CTA partials ----------
 __device__ __forceinline__ double warp_sum_blocks(const double *part, int nblk, int stride, int e) {
   const int lane = threadIdx.x & 31;
-  // four independent chains keep four loads per lane in flight
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int b = lane;
-  for (; b + 96 < nblk; b += 128) {
-    s0 += part[(long long)b * stride + e];
-    s1 += part[(long long)(b + 32) * stride + e];
-    s2 += part[(long long)(b + 64) * stride + e];
-    s3 += part[(long long)(b + 96) * stride + e];
-  }
-  for (; b < nblk; b += 32) s0 += part[(long long)b * stride + e];
-  double s = (s0 + s1) + (s2 + s3);
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += part[(long long)b * stride + e];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;

@@ -195,26 +195,22 @@ __global__ void __launch_bounds__(256, 1)
 // walks the output tiles blockIdx.x, blockIdx.x + gridDim.x, ... (consecutive tiles share
 // their rows of [U W] through L2 when ld > 128), slab by slab, with four roles that
 // meet only at mbarriers, so the tensor core is fed while earlier slabs drain:
-//   warp 9, lane 0  TMA producer of the A slabs (128 grid points x 32 K values of U or W)
-//                   into a ring of kRingA stages;
-//   warp 10, lane 0 TMA producer of the B slabs (128 columns of KT_hi / KT_lo) into a
-//                   ring of kRingB stages (both land in the 128B-swizzled K-major layout);
+//   warp 9, lane 0  TMA producer: the A slab (128 grid points x 32 K values of U or W)
+//                   and the B slabs (128 columns of KT_hi / KT_lo) into a ring of kRing
+//                   stages, each landing in the 128B-swizzled K-major layout;
 //   warps 4..7      split the A slab into TF32 hi (in place) and lo;
 //   warp 8, lane 0  issues the slab's MMAs into one of kAcc TMEM accumulators and
-//                   commits them to that accumulator's "done" barrier and the two
-//                   stages' "empty" barriers;
+//                   commits them to that accumulator's "done" barrier and the stage's
+//                   "empty" barrier;
 //   warps 0..3      drain each accumulator into FP32 registers (one tile row per thread,
 //                   all 128 columns), free it, and store U + acc when a tile ends.
 // Every wait is bounded in time; a role that gives up raises a flag the others poll.
-// A and B have rings of their own: A comes from HBM and wants the deeper one
-constexpr int kRingA = 4;             // A slabs: hi (TMA destination, split in place) | lo
-constexpr int kRingB = 3;             // B slabs: hi | lo
+constexpr int kRing = 3;
 constexpr int kAcc = 4;
-constexpr int kStageA = 2 * kPieceA;
-constexpr int kStageB = 2 * kPieceB;
-constexpr int kSmemR = kRingA * kStageA + kRingB * kStageB + 1024;
+constexpr int kStageR = 4 * kPieceA;  // A hi (TMA destination, split in place) | A lo | B hi | B lo
+constexpr int kSmemR = kRing * kStageR + 1024;
 constexpr uint64_t kWaitNs = 2000000000ull;  // every wait gives up after 2 s
-constexpr int kWarpsWS = 11;
+constexpr int kWarpsWS = 10;
 
 // Wait for the phase of `parity` of `bar`; false after kWaitNs or once *abort is set.
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
@@ -248,13 +244,10 @@ __global__ void __launch_bounds__(kWarpsWS * 32, 1)
                 long long n, int ld, const float *__restrict__ U, float *__restrict__ Unew,
                 int *err, int split) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t fullA[kRingA], emptyA[kRingA], conv[kRingA];
-  __shared__ uint64_t fullB[kRingB], emptyB[kRingB];
-  __shared__ uint64_t done[kAcc], freed[kAcc];
+  __shared__ uint64_t full[kRing], empty[kRing], conv[kRing], done[kAcc], freed[kAcc];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
-  uint8_t *smemA = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *smemB = smemA + kRingA * kStageA;
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int nslab = 2 * ld / kKS;
@@ -266,14 +259,10 @@ __global__ void __launch_bounds__(kWarpsWS * 32, 1)
 
   if (warp == 0) tc::tmem_alloc(&tmem_base_sh, kAcc * kTN);
   if (t == 0) {
-    for (int i = 0; i < kRingA; ++i) {
-      tma::bar_init(&fullA[i], 1);
-      tma::bar_init(&emptyA[i], 1);
+    for (int i = 0; i < kRing; ++i) {
+      tma::bar_init(&full[i], 1);
+      tma::bar_init(&empty[i], 1);
       tma::bar_init(&conv[i], 128);
-    }
-    for (int i = 0; i < kRingB; ++i) {
-      tma::bar_init(&fullB[i], 1);
-      tma::bar_init(&emptyB[i], 1);
     }
     for (int i = 0; i < kAcc; ++i) {
       tma::bar_init(&done[i], 1);
@@ -288,65 +277,54 @@ __global__ void __launch_bounds__(kWarpsWS * 32, 1)
   const uint32_t tmem = tmem_base_sh;
   volatile int *abort = &abort_sh;
 
-  if (warp == 9 || warp == 10) {
-    if (lane == 0) {  // ---- TMA producers: warp 9 the A slabs, warp 10 the B slabs
-      const bool isA = warp == 9;
-      const int ring = isA ? kRingA : kRingB;
-      uint64_t *full = isA ? fullA : fullB;
-      uint64_t *empty = isA ? emptyA : emptyB;
+  if (warp == 9) {
+    if (lane == 0) {  // ---- TMA producer
       long long g = 0;
       bool ok = true;
       for (long long i = 0; i < mine && ok; ++i) {
         const long long tile = blockIdx.x + i * gridDim.x;
         const int m0 = (int)(tile / ntn) * kTM, n0 = (int)(tile % ntn) * kTN;
         for (int s = 0; s < nslab; ++s, ++g) {
-          const int st = (int)(g % ring);
+          const int st = (int)(g % kRing);
           // the stage's previous slab must have been read by its MMAs
-          if (g >= ring && !wait_or_abort(&empty[st], (uint32_t)((g / ring - 1) & 1), abort)) {
+          if (g >= kRing && !wait_or_abort(&empty[st], (uint32_t)((g / kRing - 1) & 1), abort)) {
             ok = false;
             break;
           }
+          uint8_t *stage = smem + st * kStageR;
           const int k0 = s * kKS;
-          if (isA) {
-            uint8_t *stage = smemA + st * kStageA;
-            tma::bar_expect(&full[st], (uint32_t)kPieceA);
-            if (k0 < ld)
-              tma::load_2d(stage, &mU, k0, m0, &full[st]);
-            else
-              tma::load_2d(stage, &mW, k0 - ld, m0, &full[st]);
-          } else {
-            uint8_t *stage = smemB + st * kStageB;
-            tma::bar_expect(&full[st], (uint32_t)((split ? 2 : 1) * kPieceB));
-            tma::load_2d(stage, &mKh, k0, n0, &full[st]);
-            if (split) tma::load_2d(stage + kPieceB, &mKl, k0, n0, &full[st]);
-          }
+          tma::bar_expect(&full[st], (uint32_t)((split ? 3 : 2) * kPieceA));
+          if (k0 < ld)
+            tma::load_2d(stage, &mU, k0, m0, &full[st]);
+          else
+            tma::load_2d(stage, &mW, k0 - ld, m0, &full[st]);
+          tma::load_2d(stage + 2 * kPieceA, &mKh, k0, n0, &full[st]);
+          if (split) tma::load_2d(stage + 3 * kPieceA, &mKl, k0, n0, &full[st]);
         }
       }
       if (!ok) {
         atomicExch(err, 1);
-        // copies still in flight land before the CTA may exit (only the last `ring` can be)
-        for (long long q = (g > ring ? g - ring : 0); q < g; ++q)
-          (void)tma::bar_wait(&full[q % ring], (uint32_t)((q / ring) & 1), kWaitNs);
+        // copies still in flight land before the CTA may exit (only the last kRing can be)
+        for (long long q = (g > kRing ? g - kRing : 0); q < g; ++q)
+          (void)tma::bar_wait(&full[q % kRing], (uint32_t)((q / kRing) & 1), kWaitNs);
       }
     }
   } else if (warp == 8) {
     if (lane == 0) {  // ---- MMA issuer
       long long g = 0;
       for (; g < total; ++g) {
-        const int sa = (int)(g % kRingA), sb = (int)(g % kRingB), a = (int)(g % kAcc);
-        if (!wait_or_abort(&conv[sa], (uint32_t)((g / kRingA) & 1), abort)) break;
-        if (!wait_or_abort(&fullB[sb], (uint32_t)((g / kRingB) & 1), abort)) break;
+        const int st = (int)(g % kRing), a = (int)(g % kAcc);
+        if (!wait_or_abort(&conv[st], (uint32_t)((g / kRing) & 1), abort)) break;
         if (g >= kAcc && !wait_or_abort(&freed[a], (uint32_t)((g / kAcc - 1) & 1), abort)) break;
         tc::tc_fence_after();
-        const uint32_t abase = tc::smem_u32(smemA + sa * kStageA);
-        const uint32_t bbase = tc::smem_u32(smemB + sb * kStageB);
+        const uint32_t base = tc::smem_u32(smem + st * kStageR);
         const uint32_t d = tmem + (uint32_t)(a * kTN);
 #pragma unroll
         for (int kk = 0; kk < kKS / 8; ++kk) {
-          const uint64_t ah = tc::desc_sw128(abase + kk * 32);
-          const uint64_t al = tc::desc_sw128(abase + kPieceA + kk * 32);
-          const uint64_t bh = tc::desc_sw128(bbase + kk * 32);
-          const uint64_t bl = tc::desc_sw128(bbase + kPieceB + kk * 32);
+          const uint64_t ah = tc::desc_sw128(base + kk * 32);
+          const uint64_t al = tc::desc_sw128(base + kPieceA + kk * 32);
+          const uint64_t bh = tc::desc_sw128(base + 2 * kPieceA + kk * 32);
+          const uint64_t bl = tc::desc_sw128(base + 3 * kPieceA + kk * 32);
           tc::mma_tf32(d, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
           if (split) {
             tc::mma_tf32(d, ah, bl, kIdesc, 1u);
@@ -354,8 +332,7 @@ __global__ void __launch_bounds__(kWarpsWS * 32, 1)
           }
         }
         tc::mma_commit(&done[a]);
-        tc::mma_commit(&emptyA[sa]);
-        tc::mma_commit(&emptyB[sb]);
+        tc::mma_commit(&empty[st]);
       }
       if (g < total) {
         atomicExch(err, 1);
@@ -369,9 +346,9 @@ __global__ void __launch_bounds__(kWarpsWS * 32, 1)
   } else if (warp >= 4) {  // ---- splitters (warps 4..7)
     const int ct = t - 128;
     for (long long g = 0; g < total; ++g) {
-      const int st = (int)(g % kRingA);
-      if (!wait_or_abort(&fullA[st], (uint32_t)((g / kRingA) & 1), abort)) break;
-      uint8_t *stage = smemA + st * kStageA;
+      const int st = (int)(g % kRing);
+      if (!wait_or_abort(&full[st], (uint32_t)((g / kRing) & 1), abort)) break;
+      uint8_t *stage = smem + st * kStageR;
       // 1024 16-byte chunks of the A slab, 8 per thread (any bijection of chunks keeps
       // hi and lo in the same swizzled positions)
 #pragma unroll
