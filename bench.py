@@ -82,8 +82,8 @@ def algo_bytes(group, prec, n, p, s, launches, solves):
 # at this workload, keyed by kernel group and precision, valid for the kernel source
 # with the given SHA-1 prefix; null in the JSON line when the source has changed.
 NCU_TRAFFIC = {
-    ("cg_axpy", "fp32"): (622520320, "4084262628b0"),   # k_cg_wr, stencil_cg.cu
-    ("cg_apply", "fp32"): (368414720, "8e89b2755776"),  # k_cg_tma<P>, stencil_tma.cu
+    ("cg_axpy", "fp32"): (619872427, "38c22965f963"),   # k_cg_wr<float, Jacobi>, stencil_cg.cu
+    ("cg_apply", "fp32"): (369443584, "bd7b2934dda8"),  # k_cg_tma<P>, stencil_tma.cu
     ("energy", "fp32"): (136012544, "8e89b2755776"),    # k_cg_tma<QUAD>, stencil_tma.cu
 }
 
@@ -314,7 +314,9 @@ def run_ours(args):
     # the CG, stencil and energy kernels of the TF32 mode are the FP32 mode's
     key = (dom, "fp32" if args.prec == "mix_tf32" and dom.startswith(("cg_", "energy"))
            else args.prec)
-    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_source_sha(dom, args.prec):
+    # (the W/R kernel's capture is of its Jacobi variant)
+    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_source_sha(dom, args.prec) and \
+            not (dom == "cg_axpy" and args.precond != "jacobi"):
         traffic = NCU_TRAFFIC[key][0]
     if args.prec == "fp64" and dom in FP64_FLOPS:
         # FP64 Gram and update run on the FP64 pipe (about 2 DFMA / clock / SM on GB300):
