@@ -64,8 +64,10 @@ FP64_TFLOPS = 1.25  # GB300 nominal FP64 (non-tensor) rate
 KERNEL_NAME = {("cg_apply", "fp32"): "k_cg_tma", ("cg_axpy", "fp32"): "k_cg_wr",
                ("cg_apply", "fp64"): "k_cg_apply", ("cg_axpy", "fp64"): "k_cg_axpy",
                ("cg_dir", "fp64"): "k_cg_dir", ("gram", "fp32"): "k_gram_tc",
-               ("update", "fp32"): "k_update_tc", ("gram", "fp64"): "k_gram<double>",
+               ("update", "fp32"): "k_update_ws", ("gram", "fp64"): "k_gram<double>",
                ("update", "fp64"): "k_update<double>"}
+# the TF32 mode runs the FP32 mode's kernels (one MMA per product in the Gram and update)
+KERNEL_NAME.update({(g, "mix_tf32"): k for (g, q), k in list(KERNEL_NAME.items()) if q == "fp32"})
 
 
 def algo_bytes(group, prec, n, p, s, launches, solves):
