@@ -71,6 +71,17 @@ typedef enum {
                             (z = r / d; the residual buffer holds z)                   */
 } op_precond;
 
+/* The evolution the scheme discretises.  OP_FLOW_G is the paper's model (§2.2):
+ * dU/dt = G U <U,U> - U <G U,U>, Step 1 solving W = (H + sigma)^-1 U.  OP_FLOW_L2 is the
+ * L2 gradient flow of the earlier orthogonality-preserving schemes the paper contrasts
+ * itself with (§1): the same midpoint Steps 2-4 with W = -(H + sigma) U (a stencil apply,
+ * no solve; sigma drops out of U+ for orthonormal U).  Its useful time step shrinks
+ * with the mesh width like h^2 (the CFL restriction the paper's model removes). */
+typedef enum {
+  OP_FLOW_G = 0,
+  OP_FLOW_L2 = 1
+} op_flow;
+
 typedef enum {
   OP_STOP_RESIDUAL = 0,  /* r <= tol, r = ||H U - U Theta||_F / (||H+sigma||_G sqrt(p)) */
   OP_STOP_ERR_E = 1,     /* Algorithm 1: |E(U^{n+1}) - E(U^n)| / |E(U^n)| <= tol   */
@@ -90,7 +101,9 @@ typedef struct {
   int p;                 /* number of eigenpairs N (>= 1)                           */
   double sigma;          /* shift of G = (H+sigma)^-1; NaN: max(0, 1 - L) with L =
                             sum_d (2/h_d^2) sin^2(pi/(2(n_d+1))) + min V            */
-  double tau;            /* uniform time step; NaN: 1.5 (L + sigma)                 */
+  double tau;            /* uniform time step; NaN: 1.5 (L + sigma), or for OP_FLOW_L2
+                            1 / ||H + sigma||_G (Gershgorin bound 2 sum_d 1/h_d^2 +
+                            max |V + sigma|)                                         */
   int prec;              /* op_prec                                                 */
   double cg_rtol;        /* Step-1 CG: relative residual per column; <= 0 selects
                             max(floor, min(1e-2, 0.1 g)) with g the relative
@@ -111,8 +124,9 @@ typedef struct {
                             residual normalisation keeps sigma_0.  Algorithm 1 allows
                             a variable tau_n; the fixed points do not depend on sigma
                             or tau. */
-  int cg_precond;        /* op_precond of the Step-1 CG (op_cg_solve and contexts; the
-                            batched solver takes OP_PRECOND_NONE only)               */
+  int cg_precond;        /* op_precond of the Step-1 CG                              */
+  int flow;              /* op_flow (contexts; the batched solver and the adaptive
+                            shift take OP_FLOW_G only)                               */
 } op_problem;
 
 /* Per-context statistics, filled by op_step / op_solve. */

@@ -37,7 +37,7 @@ __all__ = [
     "gershgorin_norm", "householder_orthonormalize", "cholesky_qr", "inner", "SourceSolver",
     "block_cg", "block_pcg_jacobi", "core_matrices", "update", "scheme_step", "energy", "residuals",
     "paper_eigenvalues", "ritz_values", "orth_error", "energy_lower_bound", "run",
-    "RunResult", "step_coefficients", "midpoint_coefficients",
+    "RunResult", "step_coefficients", "midpoint_coefficients", "l2_flow_step",
 ]
 
 
@@ -290,6 +290,19 @@ def scheme_step(U: np.ndarray, W: np.ndarray, tau: float) -> np.ndarray:
     """One time step (4.1) given W = G U^n (Steps 2-4)."""
     A, B, _ = core_matrices(W, U, tau)
     return update(U, W, A, B, tau)
+
+
+def l2_flow_step(H, sigma: float, U: np.ndarray, tau: float) -> np.ndarray:
+    """One midpoint step of the L2 gradient flow the paper contrasts its model with (§1).
+
+    The earlier orthogonality-preserving schemes evolve the orbitals by the L2 gradient
+    flow dU/dt = -(H U - U <H U, U>).  For <U, U> = I this is the model of §2.2 with
+    G U replaced by -H U: dU/dt = W <U, U> - U <W, U> with W = -H U.  So the same
+    midpoint Steps 2-4 apply, with W = -(H + sigma) U (for orthonormal U the shift
+    cancels in U+).  Its time step is limited by the mesh (a CFL condition).
+    """
+    Hs = H + sigma * sp.identity(H.shape[0], format="csr")
+    return scheme_step(U, -(Hs @ U), tau)
 
 
 # ----------------------------------------------------------------------------

@@ -32,7 +32,7 @@ class OpProblem(C.Structure):
                 ("hi", C.c_double * 3), ("p", C.c_int), ("sigma", C.c_double),
                 ("tau", C.c_double), ("prec", C.c_int), ("cg_rtol", C.c_double),
                 ("cg_max_iter", C.c_int), ("check_every", C.c_int), ("adapt_every", C.c_int),
-                ("cg_precond", C.c_int)]
+                ("cg_precond", C.c_int), ("flow", C.c_int)]
 
 
 class OpStats(C.Structure):
@@ -143,10 +143,12 @@ def last_error() -> str:
 
 
 PRECONDS = {"none": 0, "jacobi": 1}
+FLOWS = {"g": 0, "l2": 1}
 
 
 def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol=0.0,
-                 cg_max_iter=0, check_every=0, adapt_every=0, precond="jacobi") -> OpProblem:
+                 cg_max_iter=0, check_every=0, adapt_every=0, precond="jacobi",
+                 flow="g") -> OpProblem:
     pb = OpProblem()
     dim = len(shape)
     pb.dim = dim
@@ -163,6 +165,7 @@ def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol
     pb.check_every = int(check_every)
     pb.adapt_every = int(adapt_every)
     pb.cg_precond = PRECONDS[precond] if isinstance(precond, str) else int(precond)
+    pb.flow = FLOWS[flow] if isinstance(flow, str) else int(flow)
     return pb
 
 
@@ -190,10 +193,10 @@ class Solver:
 
     def __init__(self, shape, lo, hi, V, U0, p, *, prec="fp64", sigma=None, tau=None,
                  cg_rtol=0.0, cg_max_iter=0, check_every=0, adapt_every=0, precond="jacobi",
-                 stream=None, device=False):
+                 flow="g", stream=None, device=False):
         self.pb = make_problem(shape, lo, hi, p, prec=prec, sigma=sigma, tau=tau,
                                cg_rtol=cg_rtol, cg_max_iter=cg_max_iter, check_every=check_every,
-                               adapt_every=adapt_every, precond=precond)
+                               adapt_every=adapt_every, precond=precond, flow=flow)
         self.n = int(np.prod(shape))
         self.p = int(p)
         self._ctx = C.c_void_p()

@@ -125,6 +125,14 @@ op_status check_problem(const op_problem *pb) {
     set_error("unsupported CG preconditioner %d", pb->cg_precond);
     return OP_ERR_ARG;
   }
+  if (pb->flow != OP_FLOW_G && pb->flow != OP_FLOW_L2) {
+    set_error("unsupported flow %d", pb->flow);
+    return OP_ERR_ARG;
+  }
+  if (pb->flow == OP_FLOW_L2 && pb->adapt_every > 0) {
+    set_error("the adaptive shift re-tunes the step of the G flow only (flow %d)", pb->flow);
+    return OP_ERR_ARG;
+  }
   Geom g;
   OP_TRY(make_geom(pb, &g));
   if (pb->p > g.n) {
@@ -180,8 +188,15 @@ op_status gram_any(op_ctx *c, const T *U, const T *W, double *C, double *S, doub
 template <typename T> op_status step_impl(op_ctx *c) {
   NvtxRange step_range("opevo step");
   int iters = 0;
-  // Step 1: W = (H + sigma)^-1 U, warm-started from the previous W
-  {
+  if (c->pb.flow == OP_FLOW_L2) {
+    // the L2 gradient flow: W = -(H + sigma) U
+    NvtxRange r("step 1: W = -(H + sigma) U");
+    prof_begin(&c->prof, PK_CG_APPLY, c->st);
+    OP_TRY(launch_apply<T>(c->g, (const T *)c->Vt, c->sigma, (const T *)c->U, (T *)c->W, c->ld,
+                           c->st, -1.0));
+    prof_end(&c->prof, c->st);
+  } else {
+    // Step 1: W = (H + sigma)^-1 U, warm-started from the previous W
     NvtxRange r("step 1: CG");
     OP_TRY(cg_solve<T>(c->g, (const T *)c->Vt, c->sigma, (const T *)c->U, (T *)c->W, c->p,
                        c->ld, cg_rtol_for(c), cg_max_iter(c), c->cgw, &iters, c->st));
@@ -385,7 +400,15 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
   }
   const double L = spectrum_lower_bound(&c->pb, vmin);
   c->sigma = isnan(c->pb.sigma) ? (1.0 - L > 0.0 ? 1.0 - L : 0.0) : c->pb.sigma;
-  c->tau = isnan(c->pb.tau) ? 1.5 * (L + c->sigma) : c->pb.tau;
+  c->hnorm = 2.0 * c->g.cdiag +
+             (fabs(vmax + c->sigma) > fabs(vmin + c->sigma) ? fabs(vmax + c->sigma)
+                                                            : fabs(vmin + c->sigma));
+  // default step: 1.5 (L + sigma) for the G flow; the explicit scale 1 / ||H + sigma||
+  // for the L2 flow
+  if (isnan(c->pb.tau))
+    c->tau = c->pb.flow == OP_FLOW_L2 ? 1.0 / c->hnorm : 1.5 * (L + c->sigma);
+  else
+    c->tau = c->pb.tau;
   if (!(c->tau > 0.0) || !isfinite(c->sigma)) {
     set_error("tau must be positive (got %g) and sigma finite", c->tau);
     return OP_ERR_ARG;
@@ -393,9 +416,6 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
   c->Lb = L;
   c->sigma0 = c->sigma;
   c->adapt_off = 0;
-  c->hnorm = 2.0 * c->g.cdiag +
-             (fabs(vmax + c->sigma) > fabs(vmin + c->sigma) ? fabs(vmax + c->sigma)
-                                                            : fabs(vmin + c->sigma));
   // device buffers
   void *p;
   OP_TRY(dev_alloc(c, &c->U, blk));

@@ -352,8 +352,9 @@ op_status op_batch_create(op_batch **out, op_ctx *const *ctxs, int count, int cg
   }
   for (int i = 0; i < count; ++i) {
     op_ctx *c = ctxs[i];
-    if (!c || (c->prec != OP_FP32) || c->p > 128) {
-      set_error("op_batch_create: context %d must be an OP_FP32 context with p <= 128", i);
+    if (!c || (c->prec != OP_FP32) || c->p > 128 || c->pb.flow != OP_FLOW_G) {
+      set_error("op_batch_create: context %d must be an OP_FP32 context of the G flow with "
+                "p <= 128", i);
       cudaStreamDestroy(b->st);
       delete b;
       return OP_ERR_ARG;

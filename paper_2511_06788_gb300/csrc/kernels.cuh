@@ -102,10 +102,10 @@ op_status launch_b_update(const BatchProb *B, const TileItem *items, int nitems,
 
 // ---- stencil and Step-1 CG (stencil_cg.cu) --------------------------------
 // Vt: n values of V in T; the diagonal of H + sigma is Vt_i + cdiag + sigma.
-// Y = (H + sigma) X.
+// Y = scale (H + sigma) X.
 template <typename T>
 op_status launch_apply(const Geom &g, const T *Vt, double sigma, const T *X, T *Y, int ld,
-                       cudaStream_t st);
+                       cudaStream_t st, double scale = 1.0);
 
 // out[0] = sum X .* ((H + sigma) X), out[1] = sum X .* X (FP64, device); part is
 // scratch of [max_blocks][2][ld] doubles.  With err (device int, set when a bounded

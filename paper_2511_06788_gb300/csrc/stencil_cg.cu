@@ -139,13 +139,16 @@ __device__ __forceinline__ void block_colsum(const T (&acc)[NCOMP][Pack<T>::N], 
 // ---------------------------------------------------------------------------
 // Stencil kernels
 // ---------------------------------------------------------------------------
+// Y = scale (H + sigma) X (scale = 1 or -1).
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply(Geom g, const T *__restrict__ Vt, T shift,
-                                               const T *__restrict__ X, T *__restrict__ Y, int ld) {
+                                               const T *__restrict__ X, T *__restrict__ Y, int ld,
+                                               T scale) {
   ROW_PROLOGUE(g.n)
-  (void)N;
   for (long long i = i0; i < g.n; i += istep) {
     Pack<T> y = stencil_at(g, Vt, shift, X, ld, i, col, (Pack<T> *)nullptr);
+#pragma unroll
+    for (int k = 0; k < N; ++k) y.v[k] *= scale;
     y.store(Y + i * (long long)ld + col);
   }
 }
@@ -544,10 +547,10 @@ size_t part_bytes(int ld) {
 // ---------------------------------------------------------------------------
 template <typename T>
 op_status launch_apply(const Geom &g, const T *Vt, double sigma, const T *X, T *Y, int ld,
-                       cudaStream_t st) {
+                       cudaStream_t st, double scale) {
   RowShape s = row_shape(ld, Pack<T>::N);
   k_apply<T><<<dim3(grid_blocks(g.n, s.rows), s.gy), s.block, 0, st>>>(
-      g, Vt, (T)(g.cdiag + sigma), X, Y, ld);
+      g, Vt, (T)(g.cdiag + sigma), X, Y, ld, (T)scale);
   count_launch();
   OP_LAUNCH("k_apply");
   return OP_OK;
@@ -1162,7 +1165,7 @@ void prof_harvest(Prof *p) {
   template op_status launch_sumsq<T>(long long, int, const T *, double *, double *,           \
                                      cudaStream_t);                                            \
   template op_status launch_apply<T>(const Geom &, const T *, double, const T *, T *, int,    \
-                                     cudaStream_t);                                            \
+                                     cudaStream_t, double);                                    \
   template op_status launch_quad<T>(const Geom &, const T *, double, const T *, int, double *, \
                                     double *, cudaStream_t, int *);                            \
   template op_status cg_solve<T>(const Geom &, const T *, double, const T *, T *, int, int,   \

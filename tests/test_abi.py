@@ -61,7 +61,8 @@ def _init_status(pb, V, U0):
     return s, ctx, b.last_error()
 
 
-@pytest.mark.parametrize("bad", ["dim", "p0", "shape", "box", "prec", "precond", "null"])
+@pytest.mark.parametrize("bad", ["dim", "p0", "shape", "box", "prec", "precond", "flow",
+                                 "l2_adapt", "null"])
 def test_init_rejects_bad_arguments_before_any_device_work(lib, bad):
     from paper_2511_06788_gb300 import binding as b
     pb = b.make_problem((4, 4), (0, 0), (1, 1), 2)
@@ -80,6 +81,10 @@ def test_init_rejects_bad_arguments_before_any_device_work(lib, bad):
         pb.prec = 9
     elif bad == "precond":
         pb.cg_precond = 2
+    elif bad == "flow":
+        pb.flow = 2
+    elif bad == "l2_adapt":
+        pb.flow, pb.adapt_every = 1, 10
     elif bad == "null":
         Vp = None
     s, ctx, msg = _init_status(pb, Vp, Up)

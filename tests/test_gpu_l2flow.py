@@ -1,0 +1,91 @@
+"""The L2 gradient-flow variant (op_problem.flow = OP_FLOW_L2) on the GPU.
+
+§1 contrasts the paper's model with the earlier orthogonality-preserving schemes
+that evolve the orbitals by the L2 gradient flow, whose time step is limited by a
+CFL condition.  The variant runs the same midpoint Steps 2-4 with W = -(H + sigma) U.
+
+- one and three steps equal the oracle's l2_flow_step (FP64 to rounding, FP32 to
+  FP32 accuracy), with the default step 1 / ||H + sigma||_G;
+- the shift drops out of U+;
+- with that step the number of steps to a fixed energy accuracy grows about 4x per
+  halving of h, while the paper's G flow needs about the same number on every mesh
+  (oracle: 150 / 609 / 2345 steps on 7^2 / 15^2 / 31^2 against 11 / 13 / 17).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as o
+import synthetic as syn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2511_06788_gb300 as pkg  # noqa: E402
+
+TOL = {"fp64": 1e-11, "fp32": 2e-5}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_l2_steps_match_oracle(prec):
+    P = syn.wells_3d(12, 8, 3, seed=4)
+    U0 = syn.gaussian_block(4, P.n, P.p)
+    H = o.hamiltonian(P.shape, P.lo, P.hi, P.V)
+    sigma = o.default_sigma(P.shape, P.lo, P.hi, P.V)
+    tau = 1.0 / o.gershgorin_norm(P.shape, P.lo, P.hi, P.V, sigma)
+    ref = [o.householder_orthonormalize(U0)]
+    for _ in range(3):
+        ref.append(o.l2_flow_step(H, sigma, ref[-1], tau))
+    with pkg.Solver(P.shape, P.lo, P.hi, P.V, U0, P.p, prec=prec, flow="l2") as s:
+        assert s.stats()["tau"] == pytest.approx(tau, rel=1e-12)
+        done = 0
+        for k in (1, 3):
+            s.step(k - done)
+            done = k
+            err = np.abs(s.get_U() - ref[k]).max() / np.abs(ref[k]).max()
+            assert err <= TOL[prec], (k, err)
+            assert s.stats()["last_cg_iters"] == 0
+        assert s.stats()["energy"] == pytest.approx(o.energy(H, ref[3]), rel=10 * TOL[prec])
+
+
+def test_l2_step_does_not_depend_on_the_shift():
+    P = syn.wells_3d(10, 6, 2, seed=6)
+    U0 = syn.gaussian_block(6, P.n, P.p)
+    tau = 0.7 / o.gershgorin_norm(P.shape, P.lo, P.hi, P.V, o.default_sigma(P.shape, P.lo, P.hi, P.V))
+    out = []
+    for sigma in (None, 7.5):
+        with pkg.Solver(P.shape, P.lo, P.hi, P.V, U0, P.p, prec="fp64", flow="l2", sigma=sigma,
+                        tau=tau) as s:
+            s.step(5)
+            out.append(s.get_U())
+    assert np.abs(out[0] - out[1]).max() < 1e-11
+
+
+def _steps_to(N, flow, p=2, rtol=1e-6, cap=60000):
+    shape, lo, hi = (N, N), (0.0, 0.0), (math.pi, math.pi)
+    n = N * N
+    V = np.zeros(n)
+    import scipy.sparse.linalg as spla
+    E_star = 0.5 * np.sum(spla.eigsh(o.hamiltonian(shape, lo, hi, V), k=p, which="SA")[0])
+    U0 = syn.gaussian_block(5, n, p)
+    chunk = 1 if flow == "g" else 25
+    with pkg.Solver(shape, lo, hi, V, U0, p, prec="fp64", flow=flow) as s:
+        k = 0
+        while k < cap:
+            s.step(chunk)
+            k += chunk
+            if s.stats()["energy"] - E_star <= rtol * E_star:
+                return k
+    return None
+
+
+def test_l2_flow_steps_grow_like_one_over_h_squared():
+    l2 = [_steps_to(N, "l2") for N in (31, 63)]
+    g = [_steps_to(N, "g") for N in (31, 63)]
+    print("L2 flow steps", l2, "G flow steps", g)
+    assert None not in l2 and None not in g
+    assert 3.0 <= l2[1] / l2[0] <= 5.0, l2
+    assert g[1] <= 1.5 * g[0] + 2, g

@@ -438,3 +438,57 @@ def test_table1_step_counts_fd_analog():
         assert abs(r.steps - paper_steps) <= 0.25 * paper_steps, (tau, r.steps, paper_steps)
         err = np.abs(o.ritz_values(H, r.U) / lam[: g["N"]] - 1.0)
         assert err.max() <= g["max_err_i_all"]
+
+# ----------------------------------------------------------------------------
+# The L2 gradient flow of §1 (the contrast variant)
+# ----------------------------------------------------------------------------
+def test_l2_flow_step_is_first_order_consistent_with_the_gradient():
+    # (U+ - U) / tau -> -(H U - U U^T H U) with an O(tau) error
+    shape, lo, hi, V, H, sigma, _ = random_problem(21, (5, 4, 3), 3)
+    U = o.householder_orthonormalize(np.random.default_rng(22).standard_normal((60, 3)))
+    F = -(H @ U - U @ (U.T @ (H @ U)))
+    errs = []
+    for tau in (1e-3, 1e-4):
+        errs.append(np.abs((o.l2_flow_step(H, sigma, U, tau) - U) / tau - F).max())
+    assert errs[1] < 0.2 * errs[0]
+    assert errs[1] < 1e-3 * np.abs(F).max()
+
+
+def test_l2_flow_step_does_not_depend_on_the_shift_and_keeps_orthogonality():
+    shape, lo, hi, V, H, sigma, _ = random_problem(23, (5, 4, 3), 4)
+    U = o.householder_orthonormalize(np.random.default_rng(24).standard_normal((60, 4)))
+    hn = o.gershgorin_norm(shape, lo, hi, V, sigma)
+    for tau in (0.5 / hn, 100.0 / hn):
+        a = o.l2_flow_step(H, 0.0, U, tau)
+        b = o.l2_flow_step(H, 3.7, U, tau)
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+        assert o.orth_error(a) < 1e-12
+
+
+def test_l2_flow_needs_steps_growing_like_one_over_h_squared():
+    # the CFL restriction the paper's model removes (§1, Table 3): with the explicit step
+    # 1 / ||H||, the L2 flow needs ~4x the steps per halving of h; the G flow does not
+    def steps(N, flow):
+        shape, lo, hi = (N, N), (0.0, 0.0), (math.pi, math.pi)
+        n = N * N
+        V = np.zeros(n)
+        H = o.hamiltonian(shape, lo, hi, V)
+        sigma = o.default_sigma(shape, lo, hi, V)
+        U = o.householder_orthonormalize(syn.gaussian_block(5, n, 1))
+        E_star = 0.5 * spla.eigsh(H, k=1, which="SA")[0][0]
+        if flow == "l2":
+            tau = 1.0 / o.gershgorin_norm(shape, lo, hi, V, sigma)
+        else:
+            tau = o.default_tau(shape, lo, hi, V, sigma)
+            G = o.SourceSolver(H, sigma)
+        for k in range(1, 20000):
+            U = o.l2_flow_step(H, sigma, U, tau) if flow == "l2" else \
+                o.scheme_step(U, G.solve(U), tau)
+            if o.energy(H, U) - E_star <= 1e-6 * E_star:
+                return k
+        return None
+    l2 = [steps(N, "l2") for N in (7, 15)]
+    g = [steps(N, "g") for N in (7, 15)]
+    assert None not in l2 and None not in g
+    assert 3.0 <= l2[1] / l2[0] <= 5.0, l2
+    assert g[1] <= 1.5 * g[0], g
