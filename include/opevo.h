@@ -74,9 +74,11 @@ typedef enum {
 /* The evolution the scheme discretises.  OP_FLOW_G is the paper's model (§2.2):
  * dU/dt = G U <U,U> - U <G U,U>, Step 1 solving W = (H + sigma)^-1 U.  OP_FLOW_L2 is the
  * L2 gradient flow of the earlier orthogonality-preserving schemes the paper contrasts
- * itself with (§1): the same midpoint Steps 2-4 with W = -(H + sigma) U (a stencil apply,
- * no solve; sigma drops out of U+ for orthonormal U).  Its useful time step shrinks
- * with the mesh width like h^2 (the CFL restriction the paper's model removes). */
+ * itself with (§1): the midpoint step with W = -(H + sigma) U (a stencil apply, no
+ * solve; sigma drops out of U+), taken as the exact Cayley transform (a 2p x 2p solve
+ * with the joint Gram of [U W], p <= 256) because this W amplifies any drift of <U,U>
+ * through the p x p Steps 2-3.  Its useful time step shrinks with the mesh width like
+ * h^2 (the CFL restriction the paper's model removes). */
 typedef enum {
   OP_FLOW_G = 0,
   OP_FLOW_L2 = 1

@@ -38,6 +38,7 @@ __all__ = [
     "block_cg", "block_pcg_jacobi", "core_matrices", "update", "scheme_step", "energy", "residuals",
     "paper_eigenvalues", "ritz_values", "orth_error", "energy_lower_bound", "run",
     "RunResult", "step_coefficients", "midpoint_coefficients", "l2_flow_step",
+    "cayley_coefficients",
 ]
 
 
@@ -292,17 +293,45 @@ def scheme_step(U: np.ndarray, W: np.ndarray, tau: float) -> np.ndarray:
     return update(U, W, A, B, tau)
 
 
+def cayley_coefficients(W: np.ndarray, U: np.ndarray, tau: float):
+    """The midpoint step (4.1) for any U, without assuming <U, U> = I.
+
+    With Y = [U W] and J = [[0, -I], [I, 0]], the operator of (4.1),
+    L V = W <U, V> - U <W, V>, is Y J Y^T V, and the midpoint step is the Cayley
+    transform U+ = (I - tau/2 L)^-1 (I + tau/2 L) U.  The Woodbury identity turns it
+    into one 2p x 2p solve with the joint Gram Y^T Y = [[D, C^T], [C, S]]
+    (D = <U,U>, C = <W,U>, S = <W,W>):
+        (I - tau/2 Y^T Y J) Z = Y^T U = [D; C],   U+ = U (I - tau Z_2) + W (tau Z_1),
+    Z_1, Z_2 the top and bottom p rows of Z.  For <U, U> = I this is Steps 2-4; for
+    any U it keeps <U, U> exactly (an orthogonal transform), where the p x p Steps
+    2-3 assume <U, U> = I.  Returns (K_U, K_W).
+    """
+    p = U.shape[1]
+    I = np.eye(p)
+    D = inner(U, U)
+    C = inner(W, U)
+    S = inner(W, W)
+    M2 = np.block([[I - (tau / 2.0) * C.T, (tau / 2.0) * D],
+                   [-(tau / 2.0) * S, I + (tau / 2.0) * C]])
+    Z = np.linalg.solve(M2, np.vstack([D, C]))
+    return I - tau * Z[p:], tau * Z[:p]
+
+
 def l2_flow_step(H, sigma: float, U: np.ndarray, tau: float) -> np.ndarray:
     """One midpoint step of the L2 gradient flow the paper contrasts its model with (§1).
 
     The earlier orthogonality-preserving schemes evolve the orbitals by the L2 gradient
     flow dU/dt = -(H U - U <H U, U>).  For <U, U> = I this is the model of §2.2 with
-    G U replaced by -H U: dU/dt = W <U, U> - U <W, U> with W = -H U.  So the same
-    midpoint Steps 2-4 apply, with W = -(H + sigma) U (for orthonormal U the shift
-    cancels in U+).  Its time step is limited by the mesh (a CFL condition).
+    G U replaced by -H U: dU/dt = W <U, U> - U <W, U> with W = -H U.  The midpoint step
+    is taken as the exact Cayley transform (cayley_coefficients) with
+    W = -(H + sigma) U; the shift cancels in U+.  Its time step is limited by the mesh
+    (a CFL condition).  (With the p x p Steps 2-3, which assume <U, U> = I, this flow
+    amplifies the rounding drift of <U, U> until it diverges.)
     """
     Hs = H + sigma * sp.identity(H.shape[0], format="csr")
-    return scheme_step(U, -(Hs @ U), tau)
+    W = -(Hs @ U)
+    KU, KW = cayley_coefficients(W, U, tau)
+    return U @ KU + W @ KW
 
 
 # ----------------------------------------------------------------------------

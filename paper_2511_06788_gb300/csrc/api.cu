@@ -133,6 +133,10 @@ op_status check_problem(const op_problem *pb) {
     set_error("the adaptive shift re-tunes the step of the G flow only (flow %d)", pb->flow);
     return OP_ERR_ARG;
   }
+  if (pb->flow == OP_FLOW_L2 && pb->p > 256) {
+    set_error("the L2 flow's exact Cayley step takes p <= 256 (got %d)", pb->p);
+    return OP_ERR_ARG;
+  }
   Geom g;
   OP_TRY(make_geom(pb, &g));
   if (pb->p > g.n) {
@@ -209,8 +213,14 @@ template <typename T> op_status step_impl(op_ctx *c) {
   // Steps 2-3 (FP64) and the Step-4 coefficients
   prof_begin(&c->prof, PK_CORE, c->st);
   OP_TRY(launch_core_stats(c->p, c->ld, c->C, c->S, c->D, c->dsc, c->st));
-  OP_TRY(core<T>(c->p, c->ld, c->tau, c->C, c->S, c->KU, c->KW, (T *)c->KU_t, (T *)c->KW_t,
-                 c->core_ws, c->st));
+  if (c->pb.flow == OP_FLOW_L2)
+    // the L2 flow's large W amplifies any drift of <U, U> through the p x p Steps 2-3
+    // (they assume <U, U> = I); the exact Cayley form keeps <U, U> instead
+    OP_TRY(core_cayley<T>(c->p, c->ld, c->tau, c->C, c->S, c->D, c->KU, c->KW, (T *)c->KU_t,
+                          (T *)c->KW_t, c->cayley_ws, c->core_ws, c->st));
+  else
+    OP_TRY(core<T>(c->p, c->ld, c->tau, c->C, c->S, c->KU, c->KW, (T *)c->KU_t, (T *)c->KW_t,
+                   c->core_ws, c->st));
   prof_end(&c->prof, c->st);
   // Step 4
   prof_begin(&c->prof, PK_UPDATE, c->st);
@@ -452,6 +462,8 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
   c->dev_err = (int *)p;
   OP_CUDA(cudaMemsetAsync(c->dev_err, 0, 256, c->st));
   OP_TRY(dev_alloc(c, &c->core_ws, core_workspace_bytes(c->p, ld)));
+  c->cayley_ws = nullptr;
+  if (c->pb.flow == OP_FLOW_L2) OP_TRY(dev_alloc(c, &c->cayley_ws, cayley_workspace_bytes(c->p)));
   OP_TRY(dev_alloc(c, &p, part_bytes(ld)));
   c->part = (double *)p;
   OP_TRY(dev_alloc(c, &p, 64 * sizeof(double)));

@@ -25,6 +25,7 @@ struct op_ctx {
   float *KT_hi, *KT_lo;  // FP32 blocks: [KU; KW]^T split for the tensor-core update
   int *dev_err;          // set by a tensor-core kernel whose bounded wait gave up
   void *cg_ws, *gram_ws, *core_ws;
+  void *cayley_ws;       // OP_FLOW_L2: the 2p x 3p system of the exact Cayley step
   size_t gram_bytes;
   CGWork cgw;
   Prof prof;

@@ -585,6 +585,160 @@ __global__ void k_b_core_misc(const BatchProb *__restrict__ Bp, int stage) {
 
 }  // namespace
 
+// ---- the midpoint step as an exact Cayley transform (2p x 2p; any <U, U>) -----------
+// With Y = [U W] and J = [[0, -I], [I, 0]] the operator of (4.1) is Y J Y^T; by the
+// Woodbury identity the Cayley transform (I - tau/2 Y J Y^T)^-1 (I + tau/2 Y J Y^T) U
+// is U (I - tau Z_2) + W (tau Z_1) with
+//   [[I - tau/2 C^T, tau/2 D], [-tau/2 S, I + tau/2 C]] Z = [D; C]
+// (C = <W,U>, S = <W,W>, D = <U,U>; Z_1, Z_2 its top and bottom p rows).  It keeps
+// <U, U> exactly for any U; Steps 2-3 are its reduction under <U, U> = I.
+namespace {
+
+// aug = [M2 | R]: m = 2p rows, 3p columns, row-major FP64.
+__global__ void k_cayley_build(int p, int ld, double tau, const double *__restrict__ C,
+                               const double *__restrict__ S, const double *__restrict__ D,
+                               double *__restrict__ aug) {
+  const int m = 2 * p, la = 3 * p;
+  const double h = 0.5 * tau;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * la; e += gridDim.x * blockDim.x) {
+    const int i = e / la, j = e % la;
+    double v;
+    if (i < p) {
+      if (j < p) v = (i == j ? 1.0 : 0.0) - h * C[(long long)j * ld + i];
+      else if (j < m) v = h * D[(long long)i * ld + (j - p)];
+      else v = D[(long long)i * ld + (j - m)];
+    } else {
+      const int r = i - p;
+      if (j < p) v = -h * S[(long long)r * ld + j];
+      else if (j < m) v = (r == j - p ? 1.0 : 0.0) + h * C[(long long)r * ld + (j - p)];
+      else v = C[(long long)r * ld + (j - m)];
+    }
+    aug[e] = v;
+  }
+}
+
+// Gauss-Jordan elimination with partial pivoting of the m x m left block of the
+// row-major m x la matrix a (one CTA); afterwards columns m.. hold the solution.
+// status <- 1 on a zero or non-finite pivot.
+constexpr int kCayleyMaxM = 512;
+__global__ void __launch_bounds__(1024) k_gj_pivot(int m, int la, double *__restrict__ a,
+                                                   int *status) {
+  __shared__ double mult[kCayleyMaxM];
+  __shared__ double wv[32];
+  __shared__ int wi[32];
+  __shared__ int piv_sh, bad_sh;
+  const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, warp = t >> 5;
+  for (int k = 0; k < m; ++k) {
+    // pivot row: the first largest |a[i][k]| over i >= k
+    double best = -1.0;
+    int bi = m;
+    for (int i = k + t; i < m; i += nt) {
+      const double v = fabs(a[(long long)i * la + k]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      wv[warp] = best;
+      wi[warp] = bi;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double b = -1.0;
+      int ii = m;
+      for (int w = 0; w < nt / 32; ++w)
+        if (wv[w] > b || (wv[w] == b && wi[w] < ii)) {
+          b = wv[w];
+          ii = wi[w];
+        }
+      piv_sh = ii;
+      bad_sh = !(b > 1e-300) || !isfinite(b);
+    }
+    __syncthreads();
+    if (bad_sh) break;
+    const int piv = piv_sh;
+    if (piv != k)
+      for (int j = k + t; j < la; j += nt) {
+        const double x = a[(long long)k * la + j];
+        a[(long long)k * la + j] = a[(long long)piv * la + j];
+        a[(long long)piv * la + j] = x;
+      }
+    __syncthreads();
+    const double pinv = 1.0 / a[(long long)k * la + k];
+    for (int i = t; i < m; i += nt) mult[i] = (i == k) ? 0.0 : a[(long long)i * la + k];
+    __syncthreads();
+    for (int j = k + t; j < la; j += nt) a[(long long)k * la + j] *= pinv;
+    __syncthreads();
+    const int w = la - k;
+    for (int e = t; e < m * w; e += nt) {
+      const int i = e / w, j = k + e % w;
+      if (i != k) a[(long long)i * la + j] -= mult[i] * a[(long long)k * la + j];
+    }
+    __syncthreads();
+  }
+  if (t == 0 && bad_sh) *status = 1;
+}
+
+// KU = I - tau Z_2, KW = tau Z_1 (ld x ld, identity / zero outside p x p; U kept, KU = I and
+// KW = 0, after a breakdown).
+template <typename T>
+__global__ void k_cayley_coeff(int p, int ld, double tau, const double *__restrict__ aug,
+                               double *__restrict__ KU, double *__restrict__ KW,
+                               T *__restrict__ KU_t, T *__restrict__ KW_t,
+                               const int *__restrict__ status) {
+  const bool failed = *status != 0;
+  const int la = 3 * p, m = 2 * p;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)ld * ld;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ld), j = (int)(e % ld);
+    double ku = (i == j) ? 1.0 : 0.0, kw = 0.0;
+    if (!failed && i < p && j < p) {
+      ku -= tau * aug[(long long)(p + i) * la + m + j];
+      kw = tau * aug[(long long)i * la + m + j];
+    }
+    KU[e] = ku;
+    KW[e] = kw;
+    if (KU_t) KU_t[e] = (T)ku;
+    if (KW_t) KW_t[e] = (T)kw;
+  }
+}
+
+}  // namespace
+
+size_t cayley_workspace_bytes(int p) { return (size_t)6 * p * p * sizeof(double); }
+
+template <typename T>
+op_status core_cayley(int p, int ld, double tau, const double *C, const double *S,
+                      const double *D, double *KU, double *KW, T *KU_t, T *KW_t, void *aug,
+                      void *ws, cudaStream_t st) {
+  if (2 * p > kCayleyMaxM || !(tau > 0.0)) {
+    set_error("core_cayley: p = %d above %d or tau = %g not positive", p, kCayleyMaxM / 2, tau);
+    return OP_ERR_ARG;
+  }
+  int *status = (int *)ws;
+  OP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  const int tot = 6 * p * p;
+  k_cayley_build<<<(tot + 255) / 256, 256, 0, st>>>(p, ld, tau, C, S, D, (double *)aug);
+  count_launch();
+  k_gj_pivot<<<1, 1024, 0, st>>>(2 * p, 3 * p, (double *)aug, status);
+  count_launch();
+  k_cayley_coeff<T><<<(ld * ld + 255) / 256, 256, 0, st>>>(p, ld, tau, (const double *)aug, KU,
+                                                           KW, KU_t, KW_t, status);
+  count_launch();
+  OP_LAUNCH("core_cayley");
+  return OP_OK;
+}
+
 size_t core_workspace_bytes(int p, int ld) {
   (void)p;
   return 256 + 4 * (size_t)ld * ld * sizeof(double);
@@ -719,6 +873,12 @@ template op_status core<float>(int, int, double, const double *, const double *,
                                double *, float *, float *, void *, cudaStream_t);
 template op_status core<double>(int, int, double, const double *, const double *, double *,
                                 double *, double *, double *, void *, cudaStream_t);
+template op_status core_cayley<float>(int, int, double, const double *, const double *,
+                                      const double *, double *, double *, float *, float *,
+                                      void *, void *, cudaStream_t);
+template op_status core_cayley<double>(int, int, double, const double *, const double *,
+                                       const double *, double *, double *, double *, double *,
+                                       void *, void *, cudaStream_t);
 template op_status launch_convert<float>(int, const double *, float *, cudaStream_t);
 template op_status launch_convert<double>(int, const double *, double *, cudaStream_t);
 

@@ -210,6 +210,15 @@ size_t core_workspace_bytes(int p, int ld);
 template <typename T>
 op_status core(int p, int ld, double tau, const double *C, const double *S, double *KU,
                double *KW, T *KU_t, T *KW_t, void *ws, cudaStream_t st);
+// The midpoint step as an exact Cayley transform for any <U, U> (2p x 2p solve with the
+// joint Gram of [U W], Gauss-Jordan with partial pivoting): KU, KW (FP64 and T copies)
+// with U+ = U KU + W KW.  aug: cayley_workspace_bytes(p) of device scratch; status word
+// at ws as in core().  p <= 256.
+size_t cayley_workspace_bytes(int p);
+template <typename T>
+op_status core_cayley(int p, int ld, double tau, const double *C, const double *S,
+                      const double *D, double *KU, double *KW, T *KU_t, T *KW_t, void *aug,
+                      void *ws, cudaStream_t st);
 // Cholesky-QR coefficients: from D = U0^T U0, KU = R^-1 with R = chol(D)^T, written
 // as an ld x ld FP64 matrix (zero outside p x p). Status word as in core().
 op_status cholqr_coeff(int p, int ld, const double *D, double *KU, void *ws, cudaStream_t st);

@@ -9,7 +9,9 @@ CFL condition.  The variant runs the same midpoint Steps 2-4 with W = -(H + sigm
 - the shift drops out of U+;
 - with that step the number of steps to a fixed energy accuracy grows about 4x per
   halving of h, while the paper's G flow needs about the same number on every mesh
-  (oracle: 150 / 609 / 2345 steps on 7^2 / 15^2 / 31^2 against 11 / 13 / 17).
+  (oracle, 2-D Laplacian, p = 2, energy within 1e-6: 121 / 400 / 1709 / 8445 steps on
+  7^2 / 15^2 / 31^2 / 63^2 against 26 / 22 / 27 / 26);
+- with 16x that step the L2 flow does not converge.
 """
 import math
 
@@ -64,7 +66,7 @@ def test_l2_step_does_not_depend_on_the_shift():
     assert np.abs(out[0] - out[1]).max() < 1e-11
 
 
-def _steps_to(N, flow, p=2, rtol=1e-6, cap=60000):
+def _steps_to(N, flow, p=2, rtol=1e-6, cap=60000, tau=None):
     shape, lo, hi = (N, N), (0.0, 0.0), (math.pi, math.pi)
     n = N * N
     V = np.zeros(n)
@@ -72,7 +74,7 @@ def _steps_to(N, flow, p=2, rtol=1e-6, cap=60000):
     E_star = 0.5 * np.sum(spla.eigsh(o.hamiltonian(shape, lo, hi, V), k=p, which="SA")[0])
     U0 = syn.gaussian_block(5, n, p)
     chunk = 1 if flow == "g" else 25
-    with pkg.Solver(shape, lo, hi, V, U0, p, prec="fp64", flow=flow) as s:
+    with pkg.Solver(shape, lo, hi, V, U0, p, prec="fp64", flow=flow, tau=tau) as s:
         k = 0
         while k < cap:
             s.step(chunk)
@@ -87,5 +89,14 @@ def test_l2_flow_steps_grow_like_one_over_h_squared():
     g = [_steps_to(N, "g") for N in (31, 63)]
     print("L2 flow steps", l2, "G flow steps", g)
     assert None not in l2 and None not in g
-    assert 3.0 <= l2[1] / l2[0] <= 5.0, l2
+    assert 3.0 <= l2[1] / l2[0] <= 6.0, l2
     assert g[1] <= 1.5 * g[0] + 2, g
+
+
+def test_l2_flow_above_the_cfl_step_does_not_converge():
+    N = 15
+    V = np.zeros(N * N)
+    sigma = o.default_sigma((N, N), (0.0, 0.0), (math.pi, math.pi), V)
+    hn = o.gershgorin_norm((N, N), (0.0, 0.0), (math.pi, math.pi), V, sigma)
+    assert _steps_to(N, "l2", tau=1.0 / hn, cap=3000) is not None
+    assert _steps_to(N, "l2", tau=16.0 / hn, cap=3000) is None
