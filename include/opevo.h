@@ -59,8 +59,11 @@ typedef enum {
   OP_FP32 = 1,           /* blocks, stencil and CG in FP32; Gram and update on the
                             tensor cores with a TF32 hi/lo split (FP32-class accuracy),
                             Gram chunk sums in FP64; Step 2-3 core in FP64           */
-  OP_MIX_TF32 = 2        /* as OP_FP32 but one TF32 MMA per product (operands rounded
+  OP_MIX_TF32 = 2,       /* as OP_FP32 but one TF32 MMA per product (operands rounded
                             to TF32, 10-bit mantissa); context-level API only        */
+  OP_MIX_BF16X3 = 3      /* as OP_FP32 but the Gram and update take BF16 operands split
+                            in three (x = b0 + b1 + b2 to 2^-24) and six kind::f16 MMAs
+                            per product (piece index sum <= 2), FP32 accumulation    */
 } op_prec;
 
 /* Solver of the source problems (H + sigma) w = u of Step 1 (the paper does not say how
@@ -308,8 +311,9 @@ size_t op_cg_workspace(const op_problem *pb, int ld);
 /* Inner matrices of [U W] (§2.1): C = <W,U> (C_ij = w_i . u_j), S = <W,W>, D = <U,U>,
  * each ld x ld FP64 row-major on the device (entries with i or j >= p are zero).
  * Any of C, S, D may be NULL to skip it.  OP_FP64: FP64 FMA, chunk partials in FP64.
- * OP_FP32: tcgen05 tensor-core MMAs (TF32 inputs split hi + lo, three MMAs per
+ * OP_FP32: tcgen05 tensor-core MMAs (TF32 inputs split hi + lo, four MMAs per
  * product, FP32 accumulation per chunk of grid points, chunk partials summed in FP64).
+ * OP_MIX_BF16X3: FP32 blocks, BF16 inputs split in three, six kind::f16 MMAs per product.
  * ws: device scratch of at least op_gram_workspace() bytes; its first int is set when a
  * bounded device wait gave up (check with op_ws_status). */
 op_status op_gram(int prec, long long n, int p, int ld, const void *U, const void *W,
@@ -359,8 +363,9 @@ size_t op_core_workspace(int p, int ld);
 op_status op_core_status(void *ws, void *stream);
 
 /* Step 4: Unew = U KU + W KW (KU, KW: ld x ld in the block type T, device).
- * OP_FP64: FP64 FMA.  OP_FP32: tcgen05 tensor-core MMAs with the 3xTF32 split (as in
- * op_gram).  Unew must not alias U or W.  ws: device scratch of at least
+ * OP_FP64: FP64 FMA.  OP_FP32: tcgen05 tensor-core MMAs with the 3xTF32 split
+ * (hi*hi + hi*lo + lo*hi).  OP_MIX_BF16X3: FP32 blocks and KU, KW, BF16 x 3 pieces and
+ * six kind::f16 MMAs per product.  Unew must not alias U or W.  ws: device scratch of at least
  * op_update_workspace() bytes (first int: timeout flag, see op_ws_status). */
 op_status op_update(int prec, long long n, int p, int ld, const void *U, const void *W,
                     const void *KU_t, const void *KW_t, void *Unew, void *ws, size_t ws_bytes,

@@ -18,10 +18,10 @@ LIB_PATH = os.path.join(_HERE, "libopevo.so")
 
 OP_OK, OP_ERR_ARG, OP_ERR_CUDA, OP_ERR_NOTSPD, OP_ERR_DIVERGED, OP_ERR_TIMEOUT, OP_ERR_OOM, \
     OP_ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7
-OP_FP64, OP_FP32, OP_MIX_TF32 = 0, 1, 2
+OP_FP64, OP_FP32, OP_MIX_TF32, OP_MIX_BF16X3 = 0, 1, 2, 3
 OP_STOP_RESIDUAL, OP_STOP_ERR_E, OP_STOP_STEPS = 0, 1, 2
 OP_EIG_RITZ, OP_EIG_PAPER = 0, 1
-PRECS = {"fp64": OP_FP64, "fp32": OP_FP32, "mix_tf32": OP_MIX_TF32}
+PRECS = {"fp64": OP_FP64, "fp32": OP_FP32, "mix_tf32": OP_MIX_TF32, "mix_bf16x3": OP_MIX_BF16X3}
 STATUS_NAMES = {0: "OP_OK", -1: "OP_ERR_ARG", -2: "OP_ERR_CUDA", -3: "OP_ERR_NOTSPD",
                 -4: "OP_ERR_DIVERGED", -5: "OP_ERR_TIMEOUT", -6: "OP_ERR_OOM",
                 -7: "OP_ERR_STATE"}
@@ -434,11 +434,12 @@ def cg_solve(shape, lo, hi, V_t, sigma, U, W, p, rtol, max_iter=5000, stream=Non
     return it.value
 
 
-def gram(U, W, p, want=("C", "S", "D"), stream=None):
-    """(C, S, D) = (<W,U>, <W,W>, <U,U>) as ld x ld float64 CUDA tensors."""
+def gram(U, W, p, want=("C", "S", "D"), stream=None, prec=None):
+    """(C, S, D) = (<W,U>, <W,W>, <U,U>) as ld x ld float64 CUDA tensors.  prec: None (by
+    the dtype) or "mix_bf16x3" for FP32 blocks on the BF16 x 3 tensor-core path."""
     import torch
     n, ld = U.shape
-    prec = _prec_of(U)
+    prec = _prec_of(U) if prec is None else PRECS[prec]
     out = {k: (torch.empty(ld, ld, dtype=torch.float64, device=U.device) if k in want else None)
            for k in ("C", "S", "D")}
     nbytes = lib().op_gram_workspace(prec, n, ld)
@@ -482,10 +483,10 @@ def core(Cm, Sm, p, tau, dtype=None, stream=None):
     return KU, KW, KU_t, KW_t
 
 
-def update(U, W, KU_t, KW_t, p, out=None, stream=None):
+def update(U, W, KU_t, KW_t, p, out=None, stream=None, prec=None):
     import torch
     n, ld = U.shape
-    prec = _prec_of(U)
+    prec = _prec_of(U) if prec is None else PRECS[prec]
     if out is None:
         out = torch.empty_like(U)
     nbytes = lib().op_update_workspace(prec, ld)

@@ -117,7 +117,8 @@ op_status check_problem(const op_problem *pb) {
     set_error("p must be >= 1 (got %d)", pb->p);
     return OP_ERR_ARG;
   }
-  if (pb->prec != OP_FP64 && pb->prec != OP_FP32 && pb->prec != OP_MIX_TF32) {
+  if (pb->prec != OP_FP64 && pb->prec != OP_FP32 && pb->prec != OP_MIX_TF32 &&
+      pb->prec != OP_MIX_BF16X3) {
     set_error("unsupported precision mode %d", pb->prec);
     return OP_ERR_ARG;
   }
@@ -184,7 +185,7 @@ template <typename T>
 op_status gram_any(op_ctx *c, const T *U, const T *W, double *C, double *S, double *D) {
   if constexpr (std::is_same<T, float>::value)
     return gram_tc(c->n, c->p, c->ld, U, W, C, S, D, c->gram_ws, c->gram_bytes, c->dev_err,
-                   c->st, c->prec == OP_MIX_TF32 ? 0 : 1);
+                   c->st, c->prec == OP_MIX_TF32 ? 0 : (c->prec == OP_MIX_BF16X3 ? 2 : 1));
   else
     return gram<T>(c->n, c->p, c->ld, U, W, C, S, D, c->gram_ws, c->gram_bytes, c->st);
 }
@@ -225,9 +226,17 @@ template <typename T> op_status step_impl(op_ctx *c) {
   // Step 4
   prof_begin(&c->prof, PK_UPDATE, c->st);
   if constexpr (std::is_same<T, float>::value) {
-    OP_TRY(launch_make_kt(c->ld, c->KU, c->KW, c->KT_hi, c->KT_lo, c->st));
-    OP_TRY(update_tc(c->n, c->ld, (const float *)c->U, (const float *)c->W, c->KT_hi, c->KT_lo,
-                     (float *)c->U2, c->dev_err, c->st, c->prec == OP_MIX_TF32 ? 0 : 1));
+    if (c->prec == OP_MIX_BF16X3) {
+      // the three BF16 pieces of [KU - I; KW]^T take 12 ld^2 bytes of the 16 ld^2 of KT_hi|lo
+      OP_TRY(launch_make_kt_bf16(c->ld, c->KU, c->KW, (uint16_t *)c->KT_hi, c->st));
+      OP_TRY(update_bf16(c->n, c->ld, (const float *)c->U, (const float *)c->W,
+                         (const uint16_t *)c->KT_hi, (float *)c->U2, c->dev_err, c->st));
+    } else {
+      OP_TRY(launch_make_kt(c->ld, c->KU, c->KW, c->KT_hi, c->KT_lo, c->st));
+      OP_TRY(update_tc(c->n, c->ld, (const float *)c->U, (const float *)c->W, c->KT_hi,
+                       c->KT_lo, (float *)c->U2, c->dev_err, c->st,
+                       c->prec == OP_MIX_TF32 ? 0 : 1));
+    }
   } else {
     OP_TRY(update<T>(c->n, c->ld, (const T *)c->U, (const T *)c->W, (const T *)c->KU_t,
                      (const T *)c->KW_t, (T *)c->U2, c->st));
@@ -848,7 +857,7 @@ void op_destroy(op_ctx *c) {
 // Kernel-level entry points
 // ---------------------------------------------------------------------------
 static op_status check_blocks(int prec, int p, int ld, const void *a, const void *b) {
-  if (prec != OP_FP64 && prec != OP_FP32) {
+  if (prec != OP_FP64 && prec != OP_FP32 && prec != OP_MIX_BF16X3) {
     set_error("unsupported precision mode %d", prec);
     return OP_ERR_ARG;
   }
@@ -923,7 +932,7 @@ op_status op_cg_solve(const op_problem *pb, int ld, const void *V_t, double sigm
 static const size_t kWsHeader = 256;
 
 size_t op_gram_workspace(int prec, long long n, int ld) {
-  if (prec == OP_FP32) return kWsHeader + gram_tc_workspace_bytes(n, ld);
+  if (prec == OP_FP32 || prec == OP_MIX_BF16X3) return kWsHeader + gram_tc_workspace_bytes(n, ld);
   return kWsHeader + gram_workspace_bytes(n, ld, 8);
 }
 
@@ -941,7 +950,7 @@ op_status op_gram(int prec, long long n, int p, int ld, const void *U, const voi
   if (prec == OP_FP64)
     return gram<double>(n, p, ld, (const double *)U, (const double *)W, C, S, D, part, pbytes, st);
   return gram_tc(n, p, ld, (const float *)U, (const float *)W, C, S, D, part, pbytes, (int *)ws,
-                 st);
+                 st, prec == OP_MIX_BF16X3 ? 2 : 1);
 }
 
 op_status op_ws_status(void *ws, void *stream) {
@@ -995,7 +1004,8 @@ op_status op_core_status(void *ws, void *stream) {
 }
 
 size_t op_update_workspace(int prec, int ld) {
-  return kWsHeader + (prec == OP_FP32 ? 2 * (size_t)ld * 2 * ld * sizeof(float) : 0);
+  return kWsHeader +
+         (prec == OP_FP32 || prec == OP_MIX_BF16X3 ? 2 * (size_t)ld * 2 * ld * sizeof(float) : 0);
 }
 
 op_status op_update(int prec, long long n, int p, int ld, const void *U, const void *W,
@@ -1015,6 +1025,12 @@ op_status op_update(int prec, long long n, int p, int ld, const void *U, const v
                           (const double *)KW_t, (double *)Unew, st);
   float *KT_hi = (float *)((char *)ws + kWsHeader);
   float *KT_lo = KT_hi + (size_t)ld * 2 * ld;
+  if (prec == OP_MIX_BF16X3) {
+    OP_TRY(launch_make_kt_bf16_f32(ld, (const float *)KU_t, (const float *)KW_t,
+                                   (uint16_t *)KT_hi, st));
+    return update_bf16(n, ld, (const float *)U, (const float *)W, (const uint16_t *)KT_hi,
+                       (float *)Unew, (int *)ws, st);
+  }
   OP_TRY(launch_make_kt_f32(ld, (const float *)KU_t, (const float *)KW_t, KT_hi, KT_lo, st));
   return update_tc(n, ld, (const float *)U, (const float *)W, KT_hi, KT_lo, (float *)Unew,
                    (int *)ws, st);

@@ -224,6 +224,171 @@ __device__ __forceinline__ void gram_tc_body(long long n, int ld, const float *_
   if (warp == 0) tc::tmem_dealloc(tmem, 2 * kTM);
 }
 
+// ---- BF16 x 3 variant --------------------------------------------------------------
+// The same tiling with BF16 operands: every value is split in three BF16 pieces
+// (x = b0 + b1 + b2 to 2^-24), and each product takes the six MMAs (kind::f16) whose
+// pieces have index sum <= 2; a slab is 64 grid points (one 128-byte row of BF16 K
+// values).  The staging patch is 8 grid points x 4 columns; the register buffer runs
+// one slab ahead.
+constexpr int kKSb = 64;
+constexpr int kStageB16 = 6 * kPiece;  // A0 A1 A2 B0 B1 B2
+constexpr int kSmemB16 = 2 * kStageB16 + 1024;
+constexpr uint32_t kIdescB16 = tc::idesc_bf16(kTM, kTM);
+
+__device__ __forceinline__ void load_patch8(const float *__restrict__ X, long long row,
+                                            long long r1, int col, int ld, float (&v)[8][4]) {
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row + r < r1 && col < ld) x = __ldg(reinterpret_cast<const float4 *>(X + (row + r) * ld + col));
+    v[r][0] = x.x;
+    v[r][1] = x.y;
+    v[r][2] = x.z;
+    v[r][3] = x.w;
+  }
+}
+
+// operand row m = 4q + e gets the K-chunk kq (8 BF16 values) of each of the three pieces
+__device__ __forceinline__ void store_patch8(uint8_t *piece0, int q, int kq, const float (&v)[8][4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float col[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) col[r] = v[r][e];
+    uint4 c0, c1, c2;
+    tc::split8_bf16x3(col, c0, c1, c2);
+    const uint32_t off = tc::sw128_offset(4 * q + e, kq);
+    *reinterpret_cast<uint4 *>(piece0 + off) = c0;
+    *reinterpret_cast<uint4 *>(piece0 + kPiece + off) = c1;
+    *reinterpret_cast<uint4 *>(piece0 + 2 * kPiece + off) = c2;
+  }
+}
+
+__device__ __forceinline__ void gram_bf16_body(long long n, int ld, const float *__restrict__ U,
+                                               const float *__restrict__ W, int prod, int ti,
+                                               int tj, long long r0, long long r1,
+                                               double *__restrict__ dst_tile, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+
+  const float *A = (prod == PROD_D) ? U : W;
+  const float *B = (prod == PROD_S) ? W : U;
+  const int ca = ti * kTM, cb = tj * kTM;
+  const bool same = (A == B) && (ca == cb);
+  if (r1 > n) r1 = n;
+  const int nslab = r1 > r0 ? (int)((r1 - r0 + kKSb - 1) / kKSb) : 0;
+
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int kq = t & 7, q = t >> 3;
+  const int row = (warp & 3) * 32 + lane;
+  const int half = warp >> 2;
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base_sh, 2 * kTM);
+  if (t == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::fence_mbar_init();
+    abort_sh = 0;
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+
+  float acc[64];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+
+  auto drain = [&](int s) -> bool {
+    const int a = s & 1;
+    if (t == 0 && !tc::mbar_wait(&mbar[a], (uint32_t)((s >> 1) & 1))) abort_sh = 1;
+    __syncthreads();
+    if (abort_sh) return false;
+    tc::tc_fence_after();
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float v[32];
+      tc::tmem_ld32(tmem + lane_base + (uint32_t)(a * kTM + half * 64 + c * 32), v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
+    }
+    tc::tc_fence_before();
+    return true;
+  };
+
+  float va[8][4], vb[8][4];
+  if (nslab > 0) {
+    load_patch8(A, r0 + 8 * kq, r1, ca + 4 * q, ld, va);
+    if (!same) load_patch8(B, r0 + 8 * kq, r1, cb + 4 * q, ld, vb);
+  }
+  bool ok = true;
+  for (int s = 0; s < nslab && ok; ++s) {
+    const int st = s & 1;
+    uint8_t *stage = smem + st * kStageB16;
+    // stage st was read by the MMAs of slab s-2, which the drain of slab s-2 waited for
+    store_patch8(stage, q, kq, va);
+    if (!same) store_patch8(stage + 3 * kPiece, q, kq, vb);
+    if (s + 1 < nslab) {
+      const long long r = r0 + (long long)(s + 1) * kKSb + 8 * kq;
+      load_patch8(A, r, r1, ca + 4 * q, ld, va);
+      if (!same) load_patch8(B, r, r1, cb + 4 * q, ld, vb);
+    }
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc::tc_fence_after();
+      const uint32_t base = tc::smem_u32(stage);
+      const uint32_t bbase = same ? base : base + 3 * kPiece;
+      const uint32_t d = tmem + (uint32_t)(st * kTM);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        uint64_t a[3], b[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          a[r] = tc::desc_sw128(base + r * kPiece + kk * 32);
+          b[r] = tc::desc_sw128(bbase + r * kPiece + kk * 32);
+        }
+        tc::mma_bf16(d, a[0], b[0], kIdescB16, kk > 0 ? 1u : 0u);
+        tc::mma_bf16(d, a[0], b[1], kIdescB16, 1u);
+        tc::mma_bf16(d, a[1], b[0], kIdescB16, 1u);
+        tc::mma_bf16(d, a[0], b[2], kIdescB16, 1u);
+        tc::mma_bf16(d, a[1], b[1], kIdescB16, 1u);
+        tc::mma_bf16(d, a[2], b[0], kIdescB16, 1u);
+      }
+      tc::mma_commit(&mbar[st]);
+    }
+    if (s >= 1) ok = drain(s - 1);
+  }
+  if (ok && nslab > 0) ok = drain(nslab - 1);
+  __syncthreads();
+  if (!ok || abort_sh) {
+    if (t == 0) atomicExch(err, 1);
+  } else {
+    double *dst = dst_tile + row * kTM + half * 64;
+#pragma unroll
+    for (int i = 0; i < 64; ++i) dst[i] = (double)acc[i];
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * kTM);
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_gram_bf16(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
+                int mask, int nt, int njobs, long long rows_per_split, double *__restrict__ part,
+                int *err) {
+  int prod, ti, tj;
+  decode_job(blockIdx.x, mask, nt, &prod, &ti, &tj);
+  const long long r0 = (long long)blockIdx.y * rows_per_split;
+  gram_bf16_body(n, ld, U, W, prod, ti, tj, r0, r0 + rows_per_split,
+                 part + ((long long)blockIdx.y * njobs + blockIdx.x) * (kTM * kTM), err);
+}
+
 __global__ void __launch_bounds__(256, 1)
     k_gram_tc(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
               int mask, int nt, int njobs, long long rows_per_split, double *__restrict__ part,
@@ -335,12 +500,21 @@ op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, do
     set_error("gram_tc: workspace too small (%zu < %zu)", ws_bytes, need);
     return OP_ERR_ARG;
   }
-  OP_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
   double *part = (double *)ws;
-  k_gram_tc<<<dim3(nj, nsplit), 256, kSmem, st>>>(n, ld, U, W, mask, nt, nj, rps, part, err,
-                                                   split);
-  count_launch();
-  OP_LAUNCH("k_gram_tc");
+  if (split == 2) {  // BF16 x 3
+    OP_CUDA(cudaFuncSetAttribute(k_gram_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemB16));
+    k_gram_bf16<<<dim3(nj, nsplit), 256, kSmemB16, st>>>(n, ld, U, W, mask, nt, nj, rps, part,
+                                                          err);
+    count_launch();
+    OP_LAUNCH("k_gram_bf16");
+  } else {
+    OP_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+    k_gram_tc<<<dim3(nj, nsplit), 256, kSmem, st>>>(n, ld, U, W, mask, nt, nj, rps, part, err,
+                                                     split);
+    count_launch();
+    OP_LAUNCH("k_gram_tc");
+  }
   k_gram_tc_reduce<<<dim3(nj, kReduceSlices), 256, 0, st>>>(mask, nt, nj, nsplit, part, p, ld,
                                                              C, S, D);
   count_launch();

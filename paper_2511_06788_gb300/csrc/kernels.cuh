@@ -254,5 +254,14 @@ op_status launch_make_kt_f32(int ld, const float *KU, const float *KW, float *KT
 // Unew = [U W] [KU; KW] on the tensor cores (FP32 blocks); *err as for gram_tc.
 op_status update_tc(long long n, int ld, const float *U, const float *W, const float *KT_hi,
                     const float *KT_lo, float *Unew, int *err, cudaStream_t st, int split = 1);
+// BF16 x 3 form: KT = the three BF16 pieces of [KU - I; KW]^T (3 x ld x 2 ld values,
+// kt_bf16_bytes(ld)), then Unew = U + [U W] KT^T with six MMAs per product.
+size_t kt_bf16_bytes(int ld);
+op_status launch_make_kt_bf16(int ld, const double *KU, const double *KW, uint16_t *KT,
+                              cudaStream_t st);
+op_status launch_make_kt_bf16_f32(int ld, const float *KU, const float *KW, uint16_t *KT,
+                                  cudaStream_t st);
+op_status update_bf16(long long n, int ld, const float *U, const float *W, const uint16_t *KT,
+                      float *Unew, int *err, cudaStream_t st);
 
 }  // namespace opevo

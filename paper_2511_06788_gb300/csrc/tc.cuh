@@ -10,6 +10,7 @@
 //   (row / 8) * 1024 + (row % 8) * 128 + (((k / 4) ^ (row % 8)) * 16) + (k % 4) * 4.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 namespace opevo {
@@ -101,6 +102,23 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor: D in FP32, A and B BF16 (kind::f16), both K-major, M x N tile.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A * B^T over K = 16 BF16 values (one instruction), one thread.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // D[tmem] (+)= A * B^T over K = 8 (one instruction), issued by a single thread.
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                          uint32_t idesc, uint32_t accumulate) {
@@ -148,6 +166,39 @@ __device__ __forceinline__ float to_tf32(float x) {
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
   hi = to_tf32(x);
   lo = to_tf32(x - hi);
+}
+
+// ---- BF16 x 3 splitting --------------------------------------------------------------
+// x = b0 + b1 + b2 + O(2^-24 |x|): b0 = bf16(x), b1 = bf16(x - b0), b2 = bf16(x - b0 - b1)
+// (each difference is exact in FP32).  Returned as raw 16-bit patterns.
+__device__ __forceinline__ void split_bf16x3(float x, uint16_t &b0, uint16_t &b1, uint16_t &b2) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h0);
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(h1);
+  const __nv_bfloat16 h2 = __float2bfloat16_rn(r2);
+  b0 = __bfloat16_as_ushort(h0);
+  b1 = __bfloat16_as_ushort(h1);
+  b2 = __bfloat16_as_ushort(h2);
+}
+
+// Split 8 consecutive K values and pack each piece into one 16-byte chunk (value k in
+// the low half of word k / 2 when k is even).
+__device__ __forceinline__ void split8_bf16x3(const float (&v)[8], uint4 &c0, uint4 &c1,
+                                              uint4 &c2) {
+  uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    uint16_t a0, a1, a2, b0, b1, b2;
+    split_bf16x3(v[2 * i], a0, a1, a2);
+    split_bf16x3(v[2 * i + 1], b0, b1, b2);
+    w0[i] = (uint32_t)a0 | ((uint32_t)b0 << 16);
+    w1[i] = (uint32_t)a1 | ((uint32_t)b1 << 16);
+    w2[i] = (uint32_t)a2 | ((uint32_t)b2 << 16);
+  }
+  c0 = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+  c1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+  c2 = make_uint4(w2[0], w2[1], w2[2], w2[3]);
 }
 
 }  // namespace tc

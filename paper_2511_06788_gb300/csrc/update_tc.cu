@@ -463,6 +463,182 @@ __global__ void k_make_kt(int ld, const S *__restrict__ KU, const S *__restrict_
   }
 }
 
+// ---- BF16 x 3 variant (register-staged, one output tile per CTA) --------------------
+// Operands split in three BF16 pieces; six kind::f16 MMAs per 16-value K step (piece
+// index sum <= 2); a slab is 64 K values (one 128-byte row of BF16).  The B pieces
+// KT0..KT2 of [KU - I; KW]^T are formed once per step (k_make_kt_bf16).  Accumulation,
+// drain and epilogue are those of update_tc_body.
+constexpr int kKSb = 64;
+constexpr int kStageB16 = 6 * kPieceA;  // A0 A1 A2 B0 B1 B2
+constexpr int kSmemB16 = 2 * kStageB16 + 1024;
+constexpr uint32_t kIdescB16 = tc::idesc_bf16(kTM, kTN);
+
+template <typename S>
+__global__ void k_make_kt_bf16(int ld, const S *__restrict__ KU, const S *__restrict__ KW,
+                               uint16_t *__restrict__ KT) {
+  const int K = 2 * ld;
+  const long long total = (long long)ld * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int nn = (int)(e / K), k = (int)(e % K);
+    const double v = (k < ld) ? (double)KU[(long long)k * ld + nn] - (k == nn ? 1.0 : 0.0)
+                              : (double)KW[(long long)(k - ld) * ld + nn];
+    const __nv_bfloat16 b0 = __float2bfloat16_rn((float)v);
+    const double r1 = v - (double)__bfloat162float(b0);
+    const __nv_bfloat16 b1 = __float2bfloat16_rn((float)r1);
+    const double r2 = r1 - (double)__bfloat162float(b1);
+    KT[e] = __bfloat16_as_ushort(b0);
+    KT[total + e] = __bfloat16_as_ushort(b1);
+    KT[2 * total + e] = __bfloat16_as_ushort(__float2bfloat16_rn((float)r2));
+  }
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_update_bf16(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
+                  const uint16_t *__restrict__ KT, float *__restrict__ Unew, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+
+  const long long m0 = (long long)blockIdx.x * kTM;
+  const int n0 = blockIdx.y * kTN;
+  const int K = 2 * ld;
+  const long long ktot = (long long)ld * K;
+  const int nslab = (K + kKSb - 1) / kKSb;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int kq = t & 7, rr = t >> 3;        // staging: K-chunk kq (8 values) of rows rr + 32 j
+  const int drow = (warp & 3) * 32 + lane;  // drain: tile row (TMEM lane)
+  const int half = warp >> 2;               // drain: columns 64 half .. 64 half + 63
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base_sh, 2 * kTN);
+  if (t == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::fence_mbar_init();
+    abort_sh = 0;
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+
+  float acc[64];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+
+  // one slab ahead in registers: 8 A values and 3 B chunks for each of 4 rows
+  float va[4][8];
+  uint4 vb[4][3];
+  auto load = [&](int s) {
+    const int k = s * kKSb + 8 * kq;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long row = m0 + rr + 32 * j;
+      float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+      if (row < n && k < K) {
+        const float *src = (k < ld) ? U + row * ld + k : W + row * ld + (k - ld);
+        x0 = __ldg(reinterpret_cast<const float4 *>(src));
+        x1 = __ldg(reinterpret_cast<const float4 *>(src + 4));
+      }
+      va[j][0] = x0.x; va[j][1] = x0.y; va[j][2] = x0.z; va[j][3] = x0.w;
+      va[j][4] = x1.x; va[j][5] = x1.y; va[j][6] = x1.z; va[j][7] = x1.w;
+      const int col = n0 + rr + 32 * j;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        vb[j][r] = make_uint4(0u, 0u, 0u, 0u);
+        if (col < ld && k < K)
+          vb[j][r] = __ldg(reinterpret_cast<const uint4 *>(KT + r * ktot + (long long)col * K + k));
+      }
+    }
+  };
+  auto drain = [&](int s) -> bool {
+    const int a = s & 1;
+    if (t == 0 && !tc::mbar_wait(&mbar[a], (uint32_t)((s >> 1) & 1))) abort_sh = 1;
+    __syncthreads();
+    if (abort_sh) return false;
+    tc::tc_fence_after();
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float v[32];
+      tc::tmem_ld32(tmem + lane_base + (uint32_t)(a * kTN + half * 64 + c * 32), v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
+    }
+    tc::tc_fence_before();
+    return true;
+  };
+
+  load(0);
+  bool ok = true;
+  for (int s = 0; s < nslab && ok; ++s) {
+    const int st = s & 1;
+    uint8_t *stage = smem + st * kStageB16;
+    // stage st was read by the MMAs of slab s-2, which the drain of slab s-2 waited for
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t off = tc::sw128_offset(rr + 32 * j, kq);
+      uint4 c0, c1, c2;
+      tc::split8_bf16x3(va[j], c0, c1, c2);
+      *reinterpret_cast<uint4 *>(stage + off) = c0;
+      *reinterpret_cast<uint4 *>(stage + kPieceA + off) = c1;
+      *reinterpret_cast<uint4 *>(stage + 2 * kPieceA + off) = c2;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        *reinterpret_cast<uint4 *>(stage + (3 + r) * kPieceA + off) = vb[j][r];
+    }
+    if (s + 1 < nslab) load(s + 1);
+    tc::fence_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc::tc_fence_after();
+      const uint32_t base = tc::smem_u32(stage);
+      const uint32_t d = tmem + (uint32_t)(st * kTN);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        uint64_t a[3], b[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          a[r] = tc::desc_sw128(base + r * kPieceA + kk * 32);
+          b[r] = tc::desc_sw128(base + (3 + r) * kPieceA + kk * 32);
+        }
+        tc::mma_bf16(d, a[0], b[0], kIdescB16, kk > 0 ? 1u : 0u);
+        tc::mma_bf16(d, a[0], b[1], kIdescB16, 1u);
+        tc::mma_bf16(d, a[1], b[0], kIdescB16, 1u);
+        tc::mma_bf16(d, a[0], b[2], kIdescB16, 1u);
+        tc::mma_bf16(d, a[1], b[1], kIdescB16, 1u);
+        tc::mma_bf16(d, a[2], b[0], kIdescB16, 1u);
+      }
+      tc::mma_commit(&mbar[st]);
+    }
+    if (s >= 1) ok = drain(s - 1);
+  }
+  if (ok) ok = drain(nslab - 1);
+  __syncthreads();
+  if (!ok || abort_sh) {
+    if (t == 0) atomicExch(err, 1);
+  } else {
+    const long long row = m0 + drow;
+    if (row < n) {
+#pragma unroll
+      for (int i = 0; i < 64; i += 4) {
+        const int col = n0 + half * 64 + i;
+        if (col < ld) {
+          const float4 u = __ldg(reinterpret_cast<const float4 *>(U + row * ld + col));
+          *reinterpret_cast<float4 *>(Unew + row * ld + col) =
+              make_float4(u.x + acc[i], u.y + acc[i + 1], u.z + acc[i + 2], u.w + acc[i + 3]);
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * kTN);
+}
+
 }  // namespace
 
 op_status launch_b_update(const BatchProb *B, const TileItem *items, int nitems, int nprob,
@@ -520,6 +696,39 @@ op_status update_tc(long long n, int ld, const float *U, const float *W, const f
   k_update_tc<<<grid, 256, kSmem, st>>>(n, ld, U, W, KT_hi, KT_lo, Unew, err, split);
   count_launch();
   OP_LAUNCH("k_update_tc");
+  return OP_OK;
+}
+
+size_t kt_bf16_bytes(int ld) { return (size_t)3 * ld * 2 * ld * sizeof(uint16_t); }
+
+op_status launch_make_kt_bf16(int ld, const double *KU, const double *KW, uint16_t *KT,
+                              cudaStream_t st) {
+  k_make_kt_bf16<double><<<(2 * ld * ld + 255) / 256, 256, 0, st>>>(ld, KU, KW, KT);
+  count_launch();
+  OP_LAUNCH("k_make_kt_bf16");
+  return OP_OK;
+}
+
+op_status launch_make_kt_bf16_f32(int ld, const float *KU, const float *KW, uint16_t *KT,
+                                  cudaStream_t st) {
+  k_make_kt_bf16<float><<<(2 * ld * ld + 255) / 256, 256, 0, st>>>(ld, KU, KW, KT);
+  count_launch();
+  OP_LAUNCH("k_make_kt_bf16");
+  return OP_OK;
+}
+
+op_status update_bf16(long long n, int ld, const float *U, const float *W, const uint16_t *KT,
+                      float *Unew, int *err, cudaStream_t st) {
+  if (ld % 8 != 0 || n < 1) {
+    set_error("update_bf16: bad sizes n=%lld ld=%d", n, ld);
+    return OP_ERR_ARG;
+  }
+  OP_CUDA(cudaFuncSetAttribute(k_update_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kSmemB16));
+  const dim3 grid((unsigned)((n + kTM - 1) / kTM), (ld + kTN - 1) / kTN);
+  k_update_bf16<<<grid, 256, kSmemB16, st>>>(n, ld, U, W, KT, Unew, err);
+  count_launch();
+  OP_LAUNCH("k_update_bf16");
   return OP_OK;
 }
 

@@ -26,7 +26,7 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU runs deselect -m gpu
 import paper_2511_06788_gb300 as pkg  # noqa: E402
 
 DEV = torch.device("cuda:0")
-DT = {"fp64": torch.float64, "fp32": torch.float32}
+DT = {"fp64": torch.float64, "fp32": torch.float32, "mix_bf16x3": torch.float32}
 
 
 def padded(A, ld, dtype):
@@ -41,7 +41,12 @@ def ld_of(p):
 
 
 def rounded(A, prec):
-    return A.astype(np.float32).astype(np.float64) if prec == "fp32" else A
+    return A.astype(np.float32).astype(np.float64) if prec != "fp64" else A
+
+
+def mode_of(prec):
+    """The prec argument of pkg.gram / pkg.update (None: by the dtype)."""
+    return prec if prec == "mix_bf16x3" else None
 
 
 GEOMS = [
@@ -84,17 +89,19 @@ def test_apply_H_matches_oracle(prec, geom):
     assert np.all(Yh[:, p:] == 0.0)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_bf16x3"])
 @pytest.mark.parametrize("n,p", [(1, 3), (100, 8), (5003, 72), (20000, 136), (777, 257)])
 def test_gram_matches_oracle(prec, n, p):
     rng = np.random.default_rng(n + p)
     U = rounded(rng.standard_normal((n, p)), prec)
     W = rounded(rng.standard_normal((n, p)), prec)
     ld = ld_of(p)
-    Cm, Sm, Dm = pkg.gram(padded(U, ld, DT[prec]), padded(W, ld, DT[prec]), p)
+    Cm, Sm, Dm = pkg.gram(padded(U, ld, DT[prec]), padded(W, ld, DT[prec]), p,
+                          prec=mode_of(prec))
     # rounding bound of a dot product: c * eps * sqrt(run length) * sum_k |x_k y_k|.
-    # FP64: whole chunks in FP64.  FP32 (tensor cores, 3xTF32): products to ~2^-21,
-    # FP32 accumulation over chunks of <= 2048 grid points, chunks summed in FP64.
+    # FP64: whole chunks in FP64.  FP32 (tensor cores, 4xTF32 or 6xBF16 from three-piece
+    # splits): products to ~2^-21, FP32 accumulation over chunks of <= 2048 grid points,
+    # chunks summed in FP64.
     if prec == "fp64":
         scale = 2.0 * 2.2e-16 * math.sqrt(n)
     else:
@@ -180,7 +187,7 @@ def test_core_reports_breakdown():
         pkg.core(torch.from_numpy(C).to(DEV), torch.from_numpy(S).to(DEV), p, 1.0)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mix_bf16x3"])
 # ld a multiple of 32 (p = 90, 128, 256) takes the TMA-fed tensor-core kernel for FP32:
 # a ragged last column tile (90 -> ld 96), more tiles than SMs (20000 x 128) and two
 # column tiles (256)
@@ -194,7 +201,7 @@ def test_update_matches_oracle(prec, n, p):
     KW = rounded(rng.standard_normal((p, p)), prec)
     ld = ld_of(p)
     out = pkg.update(padded(U, ld, DT[prec]), padded(W, ld, DT[prec]), _square(KU, ld, DT[prec]),
-                     _square(KW, ld, DT[prec]), p)
+                     _square(KW, ld, DT[prec]), p, prec=mode_of(prec))
     ref = U @ KU + W @ KW
     got = out.double().cpu().numpy()
     tol = (1e-14 if prec == "fp64" else 1e-6) * 2 * p * 4

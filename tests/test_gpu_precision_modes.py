@@ -8,6 +8,8 @@ residual each mode reaches:
   OP_MIX_TF32  2e-3,  5e-3    (one TF32 MMA per product: operands rounded to 2^-11
                                relative; the residual stalls near 1e-5, so this
                                mode does not meet the 1e-5 target)
+  OP_MIX_BF16X3 1e-5, 1e-5    (residual 1e-6; BF16 pieces x = b0 + b1 + b2 to 2^-24,
+                               six MMAs per product, FP64 core)
 """
 import numpy as np
 import pytest
@@ -26,6 +28,7 @@ MODES = {
     "fp64": (1e-10, 20000, 1e-10, 1e-12),
     "fp32": (1e-6, 20000, 1e-5, 1e-5),
     "mix_tf32": (1e-6, 1500, 2e-3, 5e-3),
+    "mix_bf16x3": (1e-6, 20000, 1e-5, 1e-5),
 }
 
 

@@ -12,7 +12,8 @@ Step-1 tolerances are fixed (cg_rtol) so that the step is comparable.
 Expected agreement:
 - FP64: CG error 1e-12 plus rounding;
 - FP32: CG rtol 1e-6 times tau ||B|| (about 1.5e-6) plus FP32 rounding;
-- TF32: a 2^-11 relative operand rounding in the Gram and update.
+- TF32: a 2^-11 relative operand rounding in the Gram and update;
+- BF16 x 3: as FP32 (three-piece operands to 2^-24).
 """
 import numpy as np
 import pytest
@@ -32,7 +33,8 @@ import paper_2511_06788_gb300 as pkg  # noqa: E402
 #  mix_tf32 6.7e-5 / 6.8e-4 / 8.6e-6)
 MODES = {"fp64": (1e-12, 1e-11, 1e-11, 1e-13),
          "fp32": (1e-6, 1e-5, 1e-5, 1e-6),
-         "mix_tf32": (1e-6, 5e-4, 5e-3, 1e-4)}
+         "mix_tf32": (1e-6, 5e-4, 5e-3, 1e-4),
+         "mix_bf16x3": (1e-6, 1e-5, 1e-5, 1e-6)}
 
 
 @pytest.fixture(scope="module")
