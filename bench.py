@@ -69,8 +69,9 @@ KERNEL_NAME = {("cg_apply", "fp32"): "k_cg_tma", ("cg_axpy", "fp32"): "k_cg_wr",
 # the TF32 mode runs the FP32 mode's kernels (one MMA per product in the Gram and update);
 # the BF16 x 3 mode its CG kernels and its own Gram and update
 KERNEL_NAME.update({(g, "mix_tf32"): k for (g, q), k in list(KERNEL_NAME.items()) if q == "fp32"})
-KERNEL_NAME.update({(g, "mix_bf16x3"): k for (g, q), k in list(KERNEL_NAME.items()) if q == "fp32"})
-KERNEL_NAME.update({("gram", "mix_bf16x3"): "k_gram_bf16", ("update", "mix_bf16x3"): "k_update_bf16"})
+for _m in ("mix_bf16x3", "mix_bf16"):
+    KERNEL_NAME.update({(g, _m): k for (g, q), k in list(KERNEL_NAME.items()) if q == "fp32"})
+    KERNEL_NAME.update({("gram", _m): "k_gram_bf16", ("update", _m): "k_update_bf16"})
 
 
 def algo_bytes(group, prec, n, p, s, launches, solves):
@@ -317,7 +318,7 @@ def run_ours(args):
     achieved = algo / avg_s / 1e9
     traffic = None
     # the CG, stencil and energy kernels of the TF32 and BF16 x 3 modes are the FP32 mode's
-    mixed = args.prec in ("mix_tf32", "mix_bf16x3")
+    mixed = args.prec in ("mix_tf32", "mix_bf16x3", "mix_bf16")
     key = (dom, "fp32" if mixed and dom.startswith(("cg_", "energy")) else args.prec)
     # (the W/R kernel's capture is of its Jacobi variant)
     if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_source_sha(dom, args.prec) and \
@@ -376,7 +377,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp64": "f64", "mix_tf32": "f32+tf32",
-                      "mix_bf16x3": "f32+bf16x3"}[args.prec],
+                      "mix_bf16x3": "f32+bf16x3", "mix_bf16": "f32+bf16"}[args.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "p": p, "precision": args.prec,
                        "cg_precond": args.precond, "seed_per_rank": "rank", "l2": "inputs larger than L2 (each n x p block "
@@ -821,7 +822,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "mix_tf32", "mix_bf16x3"])
+    ap.add_argument("--prec", default="fp32",
+                    choices=["fp32", "fp64", "mix_tf32", "mix_bf16x3", "mix_bf16"])
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "none"],
                     help="Step-1 CG preconditioner of the 3d_wells_64 workload")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

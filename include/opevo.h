@@ -61,9 +61,12 @@ typedef enum {
                             Gram chunk sums in FP64; Step 2-3 core in FP64           */
   OP_MIX_TF32 = 2,       /* as OP_FP32 but one TF32 MMA per product (operands rounded
                             to TF32, 10-bit mantissa); context-level API only        */
-  OP_MIX_BF16X3 = 3      /* as OP_FP32 but the Gram and update take BF16 operands split
+  OP_MIX_BF16X3 = 3,     /* as OP_FP32 but the Gram and update take BF16 operands split
                             in three (x = b0 + b1 + b2 to 2^-24) and six kind::f16 MMAs
                             per product (piece index sum <= 2), FP32 accumulation    */
+  OP_MIX_BF16 = 4        /* as OP_MIX_BF16X3 with one piece and one MMA per product
+                            (operands rounded to BF16, 8-bit mantissa); context-level
+                            API only                                                 */
 } op_prec;
 
 /* Solver of the source problems (H + sigma) w = u of Step 1 (the paper does not say how

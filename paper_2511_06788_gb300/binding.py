@@ -18,10 +18,11 @@ LIB_PATH = os.path.join(_HERE, "libopevo.so")
 
 OP_OK, OP_ERR_ARG, OP_ERR_CUDA, OP_ERR_NOTSPD, OP_ERR_DIVERGED, OP_ERR_TIMEOUT, OP_ERR_OOM, \
     OP_ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7
-OP_FP64, OP_FP32, OP_MIX_TF32, OP_MIX_BF16X3 = 0, 1, 2, 3
+OP_FP64, OP_FP32, OP_MIX_TF32, OP_MIX_BF16X3, OP_MIX_BF16 = 0, 1, 2, 3, 4
 OP_STOP_RESIDUAL, OP_STOP_ERR_E, OP_STOP_STEPS = 0, 1, 2
 OP_EIG_RITZ, OP_EIG_PAPER = 0, 1
-PRECS = {"fp64": OP_FP64, "fp32": OP_FP32, "mix_tf32": OP_MIX_TF32, "mix_bf16x3": OP_MIX_BF16X3}
+PRECS = {"fp64": OP_FP64, "fp32": OP_FP32, "mix_tf32": OP_MIX_TF32, "mix_bf16x3": OP_MIX_BF16X3,
+         "mix_bf16": OP_MIX_BF16}
 STATUS_NAMES = {0: "OP_OK", -1: "OP_ERR_ARG", -2: "OP_ERR_CUDA", -3: "OP_ERR_NOTSPD",
                 -4: "OP_ERR_DIVERGED", -5: "OP_ERR_TIMEOUT", -6: "OP_ERR_OOM",
                 -7: "OP_ERR_STATE"}

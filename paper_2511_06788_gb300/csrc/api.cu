@@ -118,7 +118,7 @@ op_status check_problem(const op_problem *pb) {
     return OP_ERR_ARG;
   }
   if (pb->prec != OP_FP64 && pb->prec != OP_FP32 && pb->prec != OP_MIX_TF32 &&
-      pb->prec != OP_MIX_BF16X3) {
+      pb->prec != OP_MIX_BF16X3 && pb->prec != OP_MIX_BF16) {
     set_error("unsupported precision mode %d", pb->prec);
     return OP_ERR_ARG;
   }
@@ -185,7 +185,11 @@ template <typename T>
 op_status gram_any(op_ctx *c, const T *U, const T *W, double *C, double *S, double *D) {
   if constexpr (std::is_same<T, float>::value)
     return gram_tc(c->n, c->p, c->ld, U, W, C, S, D, c->gram_ws, c->gram_bytes, c->dev_err,
-                   c->st, c->prec == OP_MIX_TF32 ? 0 : (c->prec == OP_MIX_BF16X3 ? 2 : 1));
+                   c->st,
+                   c->prec == OP_MIX_TF32     ? 0
+                   : c->prec == OP_MIX_BF16X3 ? 2
+                   : c->prec == OP_MIX_BF16   ? 3
+                                              : 1);
   else
     return gram<T>(c->n, c->p, c->ld, U, W, C, S, D, c->gram_ws, c->gram_bytes, c->st);
 }
@@ -226,11 +230,12 @@ template <typename T> op_status step_impl(op_ctx *c) {
   // Step 4
   prof_begin(&c->prof, PK_UPDATE, c->st);
   if constexpr (std::is_same<T, float>::value) {
-    if (c->prec == OP_MIX_BF16X3) {
+    if (c->prec == OP_MIX_BF16X3 || c->prec == OP_MIX_BF16) {
       // the three BF16 pieces of [KU - I; KW]^T take 12 ld^2 bytes of the 16 ld^2 of KT_hi|lo
       OP_TRY(launch_make_kt_bf16(c->ld, c->KU, c->KW, (uint16_t *)c->KT_hi, c->st));
       OP_TRY(update_bf16(c->n, c->ld, (const float *)c->U, (const float *)c->W,
-                         (const uint16_t *)c->KT_hi, (float *)c->U2, c->dev_err, c->st));
+                         (const uint16_t *)c->KT_hi, (float *)c->U2, c->dev_err, c->st,
+                         c->prec == OP_MIX_BF16X3));
     } else {
       OP_TRY(launch_make_kt(c->ld, c->KU, c->KW, c->KT_hi, c->KT_lo, c->st));
       OP_TRY(update_tc(c->n, c->ld, (const float *)c->U, (const float *)c->W, c->KT_hi,

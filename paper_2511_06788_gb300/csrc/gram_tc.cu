@@ -224,11 +224,11 @@ __device__ __forceinline__ void gram_tc_body(long long n, int ld, const float *_
   if (warp == 0) tc::tmem_dealloc(tmem, 2 * kTM);
 }
 
-// ---- BF16 x 3 variant --------------------------------------------------------------
+// ---- BF16 variants -------------------------------------------------------------------
 // The same tiling with BF16 operands: every value is split in three BF16 pieces
 // (x = b0 + b1 + b2 to 2^-24), and each product takes the six MMAs (kind::f16) whose
-// pieces have index sum <= 2; a slab is 64 grid points (one 128-byte row of BF16 K
-// values).  The staging patch is 8 grid points x 4 columns; the register buffer runs
+// pieces have index sum <= 2 (one piece and one MMA in the plain BF16 mode); a slab is
+// 64 grid points (one 128-byte row of BF16 K values).  The staging patch is 8 grid points x 4 columns; the register buffer runs
 // one slab ahead.
 constexpr int kKSb = 64;
 constexpr int kStageB16 = 6 * kPiece;  // A0 A1 A2 B0 B1 B2
@@ -249,7 +249,9 @@ __device__ __forceinline__ void load_patch8(const float *__restrict__ X, long lo
 }
 
 // operand row m = 4q + e gets the K-chunk kq (8 BF16 values) of each of the three pieces
-__device__ __forceinline__ void store_patch8(uint8_t *piece0, int q, int kq, const float (&v)[8][4]) {
+// (of the first piece, bf16(x), only, when three == false)
+__device__ __forceinline__ void store_patch8(uint8_t *piece0, int q, int kq, const float (&v)[8][4],
+                                             bool three) {
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     float col[8];
@@ -259,15 +261,18 @@ __device__ __forceinline__ void store_patch8(uint8_t *piece0, int q, int kq, con
     tc::split8_bf16x3(col, c0, c1, c2);
     const uint32_t off = tc::sw128_offset(4 * q + e, kq);
     *reinterpret_cast<uint4 *>(piece0 + off) = c0;
-    *reinterpret_cast<uint4 *>(piece0 + kPiece + off) = c1;
-    *reinterpret_cast<uint4 *>(piece0 + 2 * kPiece + off) = c2;
+    if (three) {
+      *reinterpret_cast<uint4 *>(piece0 + kPiece + off) = c1;
+      *reinterpret_cast<uint4 *>(piece0 + 2 * kPiece + off) = c2;
+    }
   }
 }
 
 __device__ __forceinline__ void gram_bf16_body(long long n, int ld, const float *__restrict__ U,
                                                const float *__restrict__ W, int prod, int ti,
                                                int tj, long long r0, long long r1,
-                                               double *__restrict__ dst_tile, int *err) {
+                                               double *__restrict__ dst_tile, int *err,
+                                               bool three) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_base_sh;
@@ -330,8 +335,8 @@ __device__ __forceinline__ void gram_bf16_body(long long n, int ld, const float 
     const int st = s & 1;
     uint8_t *stage = smem + st * kStageB16;
     // stage st was read by the MMAs of slab s-2, which the drain of slab s-2 waited for
-    store_patch8(stage, q, kq, va);
-    if (!same) store_patch8(stage + 3 * kPiece, q, kq, vb);
+    store_patch8(stage, q, kq, va, three);
+    if (!same) store_patch8(stage + 3 * kPiece, q, kq, vb, three);
     if (s + 1 < nslab) {
       const long long r = r0 + (long long)(s + 1) * kKSb + 8 * kq;
       load_patch8(A, r, r1, ca + 4 * q, ld, va);
@@ -354,11 +359,13 @@ __device__ __forceinline__ void gram_bf16_body(long long n, int ld, const float 
           b[r] = tc::desc_sw128(bbase + r * kPiece + kk * 32);
         }
         tc::mma_bf16(d, a[0], b[0], kIdescB16, kk > 0 ? 1u : 0u);
-        tc::mma_bf16(d, a[0], b[1], kIdescB16, 1u);
-        tc::mma_bf16(d, a[1], b[0], kIdescB16, 1u);
-        tc::mma_bf16(d, a[0], b[2], kIdescB16, 1u);
-        tc::mma_bf16(d, a[1], b[1], kIdescB16, 1u);
-        tc::mma_bf16(d, a[2], b[0], kIdescB16, 1u);
+        if (three) {
+          tc::mma_bf16(d, a[0], b[1], kIdescB16, 1u);
+          tc::mma_bf16(d, a[1], b[0], kIdescB16, 1u);
+          tc::mma_bf16(d, a[0], b[2], kIdescB16, 1u);
+          tc::mma_bf16(d, a[1], b[1], kIdescB16, 1u);
+          tc::mma_bf16(d, a[2], b[0], kIdescB16, 1u);
+        }
       }
       tc::mma_commit(&mbar[st]);
     }
@@ -381,12 +388,13 @@ __device__ __forceinline__ void gram_bf16_body(long long n, int ld, const float 
 __global__ void __launch_bounds__(256, 1)
     k_gram_bf16(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
                 int mask, int nt, int njobs, long long rows_per_split, double *__restrict__ part,
-                int *err) {
+                int *err, int three) {
   int prod, ti, tj;
   decode_job(blockIdx.x, mask, nt, &prod, &ti, &tj);
   const long long r0 = (long long)blockIdx.y * rows_per_split;
   gram_bf16_body(n, ld, U, W, prod, ti, tj, r0, r0 + rows_per_split,
-                 part + ((long long)blockIdx.y * njobs + blockIdx.x) * (kTM * kTM), err);
+                 part + ((long long)blockIdx.y * njobs + blockIdx.x) * (kTM * kTM), err,
+                 three != 0);
 }
 
 __global__ void __launch_bounds__(256, 1)
@@ -501,11 +509,11 @@ op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, do
     return OP_ERR_ARG;
   }
   double *part = (double *)ws;
-  if (split == 2) {  // BF16 x 3
+  if (split >= 2) {  // BF16: 2 three pieces, 3 one piece
     OP_CUDA(cudaFuncSetAttribute(k_gram_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemB16));
     k_gram_bf16<<<dim3(nj, nsplit), 256, kSmemB16, st>>>(n, ld, U, W, mask, nt, nj, rps, part,
-                                                          err);
+                                                          err, split == 2 ? 1 : 0);
     count_launch();
     OP_LAUNCH("k_gram_bf16");
   } else {

@@ -262,6 +262,6 @@ op_status launch_make_kt_bf16(int ld, const double *KU, const double *KW, uint16
 op_status launch_make_kt_bf16_f32(int ld, const float *KU, const float *KW, uint16_t *KT,
                                   cudaStream_t st);
 op_status update_bf16(long long n, int ld, const float *U, const float *W, const uint16_t *KT,
-                      float *Unew, int *err, cudaStream_t st);
+                      float *Unew, int *err, cudaStream_t st, bool three = true);
 
 }  // namespace opevo

@@ -463,9 +463,10 @@ __global__ void k_make_kt(int ld, const S *__restrict__ KU, const S *__restrict_
   }
 }
 
-// ---- BF16 x 3 variant (register-staged, one output tile per CTA) --------------------
+// ---- BF16 variants (register-staged, one output tile per CTA) -----------------------
 // Operands split in three BF16 pieces; six kind::f16 MMAs per 16-value K step (piece
-// index sum <= 2); a slab is 64 K values (one 128-byte row of BF16).  The B pieces
+// index sum <= 2; the plain BF16 mode: the first piece and one MMA); a slab is 64 K
+// values (one 128-byte row of BF16).  The B pieces
 // KT0..KT2 of [KU - I; KW]^T are formed once per step (k_make_kt_bf16).  Accumulation,
 // drain and epilogue are those of update_tc_body.
 constexpr int kKSb = 64;
@@ -495,7 +496,8 @@ __global__ void k_make_kt_bf16(int ld, const S *__restrict__ KU, const S *__rest
 
 __global__ void __launch_bounds__(256, 1)
     k_update_bf16(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
-                  const uint16_t *__restrict__ KT, float *__restrict__ Unew, int *err) {
+                  const uint16_t *__restrict__ KT, float *__restrict__ Unew, int *err,
+                  int three) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_base_sh;
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         vb[j][r] = make_uint4(0u, 0u, 0u, 0u);
-        if (col < ld && k < K)
+        if (col < ld && k < K && (three || r == 0))
           vb[j][r] = __ldg(reinterpret_cast<const uint4 *>(KT + r * ktot + (long long)col * K + k));
       }
     }
@@ -606,11 +608,13 @@ __global__ void __launch_bounds__(256, 1)
           b[r] = tc::desc_sw128(base + (3 + r) * kPieceA + kk * 32);
         }
         tc::mma_bf16(d, a[0], b[0], kIdescB16, kk > 0 ? 1u : 0u);
-        tc::mma_bf16(d, a[0], b[1], kIdescB16, 1u);
-        tc::mma_bf16(d, a[1], b[0], kIdescB16, 1u);
-        tc::mma_bf16(d, a[0], b[2], kIdescB16, 1u);
-        tc::mma_bf16(d, a[1], b[1], kIdescB16, 1u);
-        tc::mma_bf16(d, a[2], b[0], kIdescB16, 1u);
+        if (three) {
+          tc::mma_bf16(d, a[0], b[1], kIdescB16, 1u);
+          tc::mma_bf16(d, a[1], b[0], kIdescB16, 1u);
+          tc::mma_bf16(d, a[0], b[2], kIdescB16, 1u);
+          tc::mma_bf16(d, a[1], b[1], kIdescB16, 1u);
+          tc::mma_bf16(d, a[2], b[0], kIdescB16, 1u);
+        }
       }
       tc::mma_commit(&mbar[st]);
     }
@@ -718,7 +722,7 @@ op_status launch_make_kt_bf16_f32(int ld, const float *KU, const float *KW, uint
 }
 
 op_status update_bf16(long long n, int ld, const float *U, const float *W, const uint16_t *KT,
-                      float *Unew, int *err, cudaStream_t st) {
+                      float *Unew, int *err, cudaStream_t st, bool three) {
   if (ld % 8 != 0 || n < 1) {
     set_error("update_bf16: bad sizes n=%lld ld=%d", n, ld);
     return OP_ERR_ARG;
@@ -726,7 +730,7 @@ op_status update_bf16(long long n, int ld, const float *U, const float *W, const
   OP_CUDA(cudaFuncSetAttribute(k_update_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kSmemB16));
   const dim3 grid((unsigned)((n + kTM - 1) / kTM), (ld + kTN - 1) / kTN);
-  k_update_bf16<<<grid, 256, kSmemB16, st>>>(n, ld, U, W, KT, Unew, err);
+  k_update_bf16<<<grid, 256, kSmemB16, st>>>(n, ld, U, W, KT, Unew, err, three ? 1 : 0);
   count_launch();
   OP_LAUNCH("k_update_bf16");
   return OP_OK;

@@ -10,6 +10,8 @@ residual each mode reaches:
                                mode does not meet the 1e-5 target)
   OP_MIX_BF16X3 1e-5, 1e-5    (residual 1e-6; BF16 pieces x = b0 + b1 + b2 to 2^-24,
                                six MMAs per product, FP64 core)
+  OP_MIX_BF16  2e-2,  5e-2    (one BF16 MMA per product: operands rounded to 2^-9
+                               relative; stalls like TF32-only, earlier)
 """
 import numpy as np
 import pytest
@@ -29,6 +31,7 @@ MODES = {
     "fp32": (1e-6, 20000, 1e-5, 1e-5),
     "mix_tf32": (1e-6, 1500, 2e-3, 5e-3),
     "mix_bf16x3": (1e-6, 20000, 1e-5, 1e-5),
+    "mix_bf16": (1e-6, 1500, 2e-2, 5e-2),
 }
 
 
@@ -51,6 +54,6 @@ def test_precision_mode_accuracy(problem, prec):
     err = float(np.abs(ritz / lam[: P.p] - 1.0).max())
     orth = float(np.linalg.norm(U.T @ U - np.eye(P.p)))
     print(f"{prec}: steps {st['steps']} residual {st['residual']:.2e} eig {err:.2e} orth {orth:.2e}")
-    if prec != "mix_tf32":
+    if prec not in ("mix_tf32", "mix_bf16"):
         assert st["converged"]
     assert err <= eig_tol and orth <= orth_tol
