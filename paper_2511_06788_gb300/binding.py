@@ -190,7 +190,14 @@ def _stream_ptr(stream):
 
 
 class Solver:
-    """A solver context (op_init ... op_destroy) for one eigenproblem."""
+    """A solver context (op_init ... op_destroy) for one eigenproblem.
+
+    prec: "fp64", "fp32", "mix_tf32", "mix_bf16x3" or "mix_bf16" (op_prec).
+    precond: the Step-1 CG, "jacobi" (preconditioned with diag(H + sigma)) or "none".
+    flow: "g" (the paper's model, Step 1 solving W = (H + sigma)^-1 U) or "l2" (the L2
+    gradient flow W = -(H + sigma) U through the exact Cayley step; CFL-limited).
+    The remaining keywords are the op_problem fields of the same names.
+    """
 
     def __init__(self, shape, lo, hi, V, U0, p, *, prec="fp64", sigma=None, tau=None,
                  cg_rtol=0.0, cg_max_iter=0, check_every=0, adapt_every=0, precond="jacobi",
