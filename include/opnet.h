@@ -10,7 +10,7 @@
  *   Y = net(V)  (n x p)  ->  op_init / op_init_device orthonormalises Y once
  *   (Cholesky-QR, FP64)  ->  the plain scheme (op_step / op_solve).
  *
- * The scheme is unchanged and remains the judge of the result.
+ * The scheme is unchanged; its own steps decide the result.
  *
  * Network: a 3-level U-Net on an N^3 grid, N % 4 == 0.  Tensors are
  * channels-last [grid point][channel], with the point ordering of opevo.h.

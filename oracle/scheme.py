@@ -10,7 +10,7 @@ follows.  Notation follows the paper: ``<U, V>`` is the inner matrix
 (§2.1, ``<U,V>_ij = (u_i, v_j)``), ``G = (H + sigma)^-1`` the solution operator
 (§3.1), ``W = G U``.
 
-Discretisation (the paper uses finite elements in §5; this build uses finite
+Discretisation (the paper uses finite elements in §5; this oracle uses finite
 differences): ``H = -1/2 Delta_h + diag(V)`` with the standard 3-point second
 difference per axis and homogeneous Dirichlet values outside the interior
 grid.  The discrete inner product is the Euclidean one on R^n (the h^d weight

@@ -6,7 +6,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  The paper has no
 network; this is the learned-warm-start extension of the scheme.  The network
 only has to put U^0 in the basin of the scheme's fixed point.  The basin
 condition on the energy, E(U^0) below the excited-state level (§3), is what a
-good warm start buys; the scheme itself is unchanged and judges the result.
+good warm start buys; the scheme itself is unchanged and decides the result.
 
 Tensors are channels-last, [grid point][channel], on an N^3 grid (N % 4 == 0).
 Point (ix, iy, iz) has index ix + N (iy + N iz), the orbital-block ordering.
