@@ -212,30 +212,9 @@ constexpr int kSmemR = kRing * kStageR + 1024;
 constexpr uint64_t kWaitNs = 2000000000ull;  // every wait gives up after 2 s
 constexpr int kWarpsWS = 10;
 
-// Wait for the phase of `parity` of `bar`; false after kWaitNs or once *abort is set.
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
                                               volatile int *abort) {
-  const uint32_t a = tc::smem_u32(bar);
-  uint64_t t0 = 0;
-  for (;;) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (*abort) return false;
-    const uint64_t now = tma::global_ns();
-    if (t0 == 0) {
-      t0 = now;
-    } else if (now - t0 > kWaitNs) {
-      *abort = 1;
-      return false;
-    }
-  }
+  return tc::wait_or_abort(bar, parity, abort, kWaitNs);
 }
 
 __global__ void __launch_bounds__(kWarpsWS * 32, 1)
