@@ -224,173 +224,6 @@ __device__ __forceinline__ void gram_tc_body(long long n, int ld, const float *_
   if (warp == 0) tc::tmem_dealloc(tmem, 2 * kTM);
 }
 
-// ---- warp-specialised variant (one CTA per job and chunk, as k_gram_tc) --------------
-// The same staging, products, split and per-slab accumulation as gram_tc_body (so the
-// partial tiles are bit-identical), spread over two groups of 8 warps that meet at
-// mbarriers:
-//   warps 8..15  load 4 x 4 patches two slabs ahead in registers, split and store them
-//                into a ring of kRingG stages, then arrive on the stage's "full" barrier;
-//   warps 0..7   drain the accumulators into FP32 registers, kLagG slabs behind the
-//                MMAs, which lane 0 of warp 0 issues (into one of kAccG TMEM accumulators,
-//                committed to the accumulator's "done" and the stage's "empty" barrier).
-// Every wait is bounded in time; a role that gives up raises a flag the others poll.
-constexpr int kRingG = 3;
-constexpr int kAccG = 4;
-constexpr int kLagG = 2;  // kLagG + 2 <= kAccG: an accumulator is free again when reused
-constexpr int kSmemG = kRingG * kStage + 1024;
-constexpr uint64_t kWaitNsG = 2000000000ull;
-constexpr int kWarpsG = 16;
-
-__global__ void __launch_bounds__(kWarpsG * 32, 1)
-    k_gram_ws(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
-              int mask, int nt, int njobs, long long rows_per_split, double *__restrict__ part,
-              int *err, int split) {
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t full[kRingG], empty[kRingG], done[kAccG], freed[kAccG];
-  __shared__ uint32_t tmem_base_sh;
-  __shared__ int abort_sh;
-  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-
-  int prod, ti, tj;
-  decode_job(blockIdx.x, mask, nt, &prod, &ti, &tj);
-  const long long r0 = (long long)blockIdx.y * rows_per_split;
-  long long r1 = r0 + rows_per_split;
-  if (r1 > n) r1 = n;
-  double *dst_tile = part + ((long long)blockIdx.y * njobs + blockIdx.x) * (kTM * kTM);
-  const float *A = (prod == PROD_D) ? U : W;
-  const float *B = (prod == PROD_S) ? W : U;
-  const int ca = ti * kTM, cb = tj * kTM;
-  const bool same = (A == B) && (ca == cb);
-  const int nslab = r1 > r0 ? (int)((r1 - r0 + kKS - 1) / kKS) : 0;
-
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  if (warp == 0) tc::tmem_alloc(&tmem_base_sh, kAccG * kTM);
-  if (t == 0) {
-    for (int i = 0; i < kRingG; ++i) {
-      tc::mbar_init(&full[i], 256);
-      tc::mbar_init(&empty[i], 1);
-    }
-    for (int i = 0; i < kAccG; ++i) {
-      tc::mbar_init(&done[i], 1);
-      tc::mbar_init(&freed[i], 256);
-    }
-    tc::fence_mbar_init();
-    abort_sh = 0;
-  }
-  tc::tc_fence_before();
-  __syncthreads();
-  tc::tc_fence_after();
-  const uint32_t tmem = tmem_base_sh;
-  volatile int *abort = &abort_sh;
-
-  if (warp >= 8) {  // ---- loaders
-    const int ct = t - 256;
-    const int kq = ct & 7, q = ct >> 3;
-    float va0[4][4], vb0[4][4], va1[4][4], vb1[4][4];
-    if (nslab > 0) {
-      load_patch(A, r0 + 4 * kq, r1, ca + 4 * q, ld, va0);
-      if (!same) load_patch(B, r0 + 4 * kq, r1, cb + 4 * q, ld, vb0);
-    }
-    if (nslab > 1) {
-      load_patch(A, r0 + kKS + 4 * kq, r1, ca + 4 * q, ld, va1);
-      if (!same) load_patch(B, r0 + kKS + 4 * kq, r1, cb + 4 * q, ld, vb1);
-    }
-    auto put = [&](int s, float (&va)[4][4], float (&vb)[4][4]) -> bool {
-      const int st = s % kRingG;
-      // the stage's previous slab must have been read by its MMAs
-      if (s >= kRingG &&
-          !tc::wait_or_abort(&empty[st], (uint32_t)((s / kRingG - 1) & 1), abort, kWaitNsG))
-        return false;
-      uint8_t *stage = smem + st * kStage;
-      store_patch(stage, stage + kPiece, q, kq, va, split != 0);
-      if (!same) store_patch(stage + 2 * kPiece, stage + 3 * kPiece, q, kq, vb, split != 0);
-      tc::fence_async_smem();
-      tc::mbar_arrive(&full[st]);
-      if (s + 2 < nslab) {
-        const long long r = r0 + (long long)(s + 2) * kKS + 4 * kq;
-        load_patch(A, r, r1, ca + 4 * q, ld, va);
-        if (!same) load_patch(B, r, r1, cb + 4 * q, ld, vb);
-      }
-      return true;
-    };
-    for (int s = 0; s < nslab; s += 2) {
-      if (!put(s, va0, vb0)) break;
-      if (s + 1 < nslab && !put(s + 1, va1, vb1)) break;
-    }
-  } else {  // ---- MMA issue (warp 0, lane 0) and drain (TMEM lanes 32 (warp % 4) ..)
-    const int row = (warp & 3) * 32 + lane;
-    const int half = warp >> 2;
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    float acc[64];
-#pragma unroll
-    for (int i = 0; i < 64; ++i) acc[i] = 0.f;
-    int issued = 0;  // lane 0 of warp 0: slabs whose MMAs were committed
-    bool ok = true;
-    for (int s = 0; s < nslab + kLagG && ok; ++s) {
-      if (warp == 0 && lane == 0 && s < nslab) {
-        const int st = s % kRingG, a = s % kAccG;
-        bool go = tc::wait_or_abort(&full[st], (uint32_t)((s / kRingG) & 1), abort, kWaitNsG);
-        if (go && s >= kAccG)
-          go = tc::wait_or_abort(&freed[a], (uint32_t)((s / kAccG - 1) & 1), abort, kWaitNsG);
-        if (go) {
-          tc::tc_fence_after();
-          const uint32_t base = tc::smem_u32(smem + st * kStage);
-          const uint32_t bbase = same ? base : base + 2 * kPiece;
-          const uint32_t d = tmem + (uint32_t)(a * kTM);
-#pragma unroll
-          for (int kk = 0; kk < kKS / 8; ++kk) {
-            const uint64_t ah = tc::desc_sw128(base + kk * 32);
-            const uint64_t al = tc::desc_sw128(base + kPiece + kk * 32);
-            const uint64_t bh = tc::desc_sw128(bbase + kk * 32);
-            const uint64_t bl = tc::desc_sw128(bbase + kPiece + kk * 32);
-            tc::mma_tf32(d, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
-            if (split) {
-              tc::mma_tf32(d, ah, bl, kIdesc, 1u);
-              tc::mma_tf32(d, al, bh, kIdesc, 1u);
-              tc::mma_tf32(d, al, bl, kIdesc, 1u);
-            }
-          }
-          tc::mma_commit(&done[a]);
-          tc::mma_commit(&empty[st]);
-          issued = s + 1;
-        }
-      }
-      __syncwarp();
-      const int g = s - kLagG;  // the slab drained in this round
-      if (g < 0) continue;
-      const int a = g % kAccG;
-      if (!tc::wait_or_abort(&done[a], (uint32_t)((g / kAccG) & 1), abort, kWaitNsG)) {
-        ok = false;
-        break;
-      }
-      tc::tc_fence_after();
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        float v[32];
-        tc::tmem_ld32(tmem + lane_base + (uint32_t)(a * kTM + half * 64 + c * 32), v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) acc[c * 32 + i] += v[i];
-      }
-      tc::tc_fence_before();
-      tc::mbar_arrive(&freed[a]);
-    }
-    if (ok && !*abort) {
-      double *dst = dst_tile + row * kTM + half * 64;
-#pragma unroll
-      for (int i = 0; i < 64; ++i) dst[i] = (double)acc[i];
-    }
-    if (warp == 0 && lane == 0 && *abort && issued > 0) {
-      // MMAs issued but not drained: let them finish before the TMEM is freed
-      const int g = issued - 1;
-      (void)tc::mbar_wait(&done[g % kAccG], (uint32_t)((g / kAccG) & 1));
-    }
-  }
-  tc::tc_fence_before();
-  __syncthreads();
-  if (t == 0 && *abort) atomicExch(err, 1);
-  if (warp == 0) tc::tmem_dealloc(tmem, kAccG * kTM);
-}
-
 // ---- BF16 variants -------------------------------------------------------------------
 // The same tiling with BF16 operands: every value is split in three BF16 pieces
 // (x = b0 + b1 + b2 to 2^-24), and each product takes the six MMAs (kind::f16) whose
@@ -684,11 +517,11 @@ op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, do
     count_launch();
     OP_LAUNCH("k_gram_bf16");
   } else {
-    OP_CUDA(cudaFuncSetAttribute(k_gram_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemG));
-    k_gram_ws<<<dim3(nj, nsplit), kWarpsG * 32, kSmemG, st>>>(n, ld, U, W, mask, nt, nj, rps,
-                                                               part, err, split);
+    OP_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+    k_gram_tc<<<dim3(nj, nsplit), 256, kSmem, st>>>(n, ld, U, W, mask, nt, nj, rps, part, err,
+                                                     split);
     count_launch();
-    OP_LAUNCH("k_gram_ws");
+    OP_LAUNCH("k_gram_tc");
   }
   k_gram_tc_reduce<<<dim3(nj, kReduceSlices), 256, 0, st>>>(mask, nt, nj, nsplit, part, p, ld,
                                                              C, S, D);
