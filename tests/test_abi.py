@@ -62,7 +62,7 @@ def _init_status(pb, V, U0):
 
 
 @pytest.mark.parametrize("bad", ["dim", "p0", "shape", "box", "prec", "precond", "flow",
-                                 "l2_adapt", "null"])
+                                 "l2_adapt", "l2_wide", "null"])
 def test_init_rejects_bad_arguments_before_any_device_work(lib, bad):
     from paper_2511_06788_gb300 import binding as b
     pb = b.make_problem((4, 4), (0, 0), (1, 1), 2)
@@ -85,6 +85,11 @@ def test_init_rejects_bad_arguments_before_any_device_work(lib, bad):
         pb.flow = 2
     elif bad == "l2_adapt":
         pb.flow, pb.adapt_every = 1, 10
+    elif bad == "l2_wide":  # the exact Cayley step of the L2 flow takes p <= 256
+        pb = b.make_problem((20, 20), (0, 0), (1, 1), 257, flow="l2")
+        V, U0 = np.zeros(400), np.ones((400, 257))
+        Vp = V.ctypes.data_as(C.POINTER(C.c_double))
+        Up = U0.ctypes.data_as(C.POINTER(C.c_double))
     elif bad == "null":
         Vp = None
     s, ctx, msg = _init_status(pb, Vp, Up)
