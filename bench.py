@@ -582,7 +582,7 @@ def run_c3(args):
     gen = torch.Generator(device=dev)
     gen.manual_seed(rank)
     U0 = torch.randn(P.n, P.p, dtype=torch.float64, device=dev, generator=gen)
-    rtol = {"fp64": 1e-10, "fp32": 1e-6, "mix_tf32": 1e-6}
+    rtol = {"fp64": 1e-10, "fp32": 1e-6, "mix_tf32": 1e-6, "mix_bf16x3": 1e-6, "mix_bf16": 1e-6}
     rows, U64 = {}, None
     modes = args.c3_modes.split(",")
     for prec in modes:
