@@ -31,7 +31,7 @@
  *     stream).  Kernel-level calls only enqueue work; context-level calls
  *     synchronise the context's stream where they say so.
  *   - Inputs and outputs in FP64 unless stated; blocks of a context in
- *     OP_FP32 mode are stored in FP32 on the device.
+ *     OP_FP32 or a mixed mode are stored in FP32 on the device.
  */
 #ifndef OPEVO_H
 #define OPEVO_H
@@ -219,7 +219,6 @@ const char *op_profile_name(int kind);  /* static storage; "" for an unknown kin
 /* Total device time (ms) and number of timed launch groups of `kind` since enabling. */
 op_status op_profile_read(op_ctx *ctx, int kind, double *total_ms, long long *launches);
 
-/* Free the context's device memory. NULL is allowed. */
 /* Checkpoint / resume.  The paper has no counterpart; the scheme is a one-step map,
  * so a context restored from a checkpoint continues bit-identically: the state is
  * U, the Step-1 warm start W, sigma, tau and the step statistics.
@@ -228,6 +227,10 @@ op_status op_profile_read(op_ctx *ctx, int kind, double *total_ms, long long *la
  * op_restore: loads a state written by op_checkpoint into a context of the same
  *   problem size (n, p, ld) and precision (OP_ERR_ARG otherwise, or for a buffer
  *   that is not a checkpoint).  Both synchronise the context's stream. */
+size_t op_checkpoint_size(const op_ctx *ctx);
+op_status op_checkpoint(op_ctx *ctx, void *buf, size_t len);
+op_status op_restore(op_ctx *ctx, const void *buf, size_t len);
+
 /* Self-test of failure detection (the paper has no counterpart).  Every wait inside
  * this library's kernels is bounded: on expiry the kernel sets an error word and
  * the call returns OP_ERR_TIMEOUT instead of hanging.  This call makes one wait of
@@ -238,10 +241,7 @@ op_status op_profile_read(op_ctx *ctx, int kind, double *total_ms, long long *la
  * a second. */
 op_status op_selftest_bounded_waits(double *seconds, void *stream);
 
-size_t op_checkpoint_size(const op_ctx *ctx);
-op_status op_checkpoint(op_ctx *ctx, void *buf, size_t len);
-op_status op_restore(op_ctx *ctx, const void *buf, size_t len);
-
+/* Free the context's device memory. NULL is allowed. */
 void op_destroy(op_ctx *ctx);
 
 /* ---------------------------------------------------------------------------
@@ -255,7 +255,8 @@ void op_destroy(op_ctx *ctx);
  * ------------------------------------------------------------------------- */
 typedef struct op_batch op_batch;
 
-/* Group `count` contexts (each OP_FP32, p <= 128; not copied, still owned by the
+/* Group `count` contexts (each OP_FP32 of the G flow, p <= 128, plain or Jacobi CG; not
+ * copied, still owned by the
  * caller) into a batch.  The batch captures and replays its graphs on a stream of
  * its own; `stream` and the contexts' streams are synchronised at creation, and
  * every batch call that returns results synchronises the batch stream.  While the batch exists the
