@@ -255,9 +255,8 @@ void op_destroy(op_ctx *ctx);
  * ------------------------------------------------------------------------- */
 typedef struct op_batch op_batch;
 
-/* Group `count` contexts (each OP_FP32 of the G flow, p <= 128, plain or Jacobi CG; not
- * copied, still owned by the
- * caller) into a batch.  The batch captures and replays its graphs on a stream of
+/* Group `count` contexts (each OP_FP32 of the G flow, p <= 128, plain or Jacobi CG;
+ * not copied, still owned by the caller) into a batch.  The batch captures and replays its graphs on a stream of
  * its own; `stream` and the contexts' streams are synchronised at creation, and
  * every batch call that returns results synchronises the batch stream.  While the batch exists the
  * contexts must not be stepped on their own (they may be read: op_get_U,
