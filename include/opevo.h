@@ -256,11 +256,12 @@ void op_destroy(op_ctx *ctx);
 typedef struct op_batch op_batch;
 
 /* Group `count` contexts (each OP_FP32 of the G flow, p <= 128, plain or Jacobi CG;
- * not copied, still owned by the caller) into a batch.  The batch captures and replays its graphs on a stream of
- * its own; `stream` and the contexts' streams are synchronised at creation, and
- * every batch call that returns results synchronises the batch stream.  While the batch exists the
- * contexts must not be stepped on their own (they may be read: op_get_U,
- * op_eigenvalues, op_residual, op_get_stats).  Destroy the batch before the contexts. */
+ * not copied, still owned by the caller) into a batch.  The batch captures and
+ * replays its graphs on a stream of its own; `stream` and the contexts' streams are
+ * synchronised at creation, and every batch call that returns results synchronises
+ * the batch stream.  While the batch exists the contexts must not be stepped on
+ * their own (they may be read: op_get_U, op_eigenvalues, op_residual,
+ * op_get_stats).  Destroy the batch before the contexts. */
 op_status op_batch_create(op_batch **b, op_ctx *const *ctxs, int count, int cg_iters,
                           void *stream);
 /* Work-list granularity: grid points per stencil/CG/energy item (>= 32) and per Gram
