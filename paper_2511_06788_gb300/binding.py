@@ -429,6 +429,10 @@ def apply_H(shape, lo, hi, V_t, sigma, X, Y=None, stream=None):
 
 def cg_solve(shape, lo, hi, V_t, sigma, U, W, p, rtol, max_iter=5000, stream=None,
              precond="none"):
+    """Step 1 alone (op_cg_solve): W <- (H + sigma)^-1 U by block CG warm-started from
+    W, each column to ||u - (H + sigma) w|| <= rtol ||u||.  precond: "none" (plain CG,
+    the kernel-level default) or "jacobi" (the Solver default).  Returns the number of
+    iterations."""
     import torch
     n, ld = U.shape
     prec = _prec_of(U)
