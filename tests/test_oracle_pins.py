@@ -210,6 +210,22 @@ def test_jacobi_pcg_iterate_minimises_the_energy_error_over_the_krylov_space():
         np.testing.assert_allclose(Xk[:, 0], x_best, rtol=0, atol=1e-9 * np.abs(xs).max())
 
 
+def test_jacobi_pcg_stops_on_the_unpreconditioned_residual():
+    # the stop test is ||b - A x_k|| <= rtol ||b|| per column, at the first such k
+    import scipy.sparse as sp
+    shape, lo, hi, V, H, sigma, U = random_problem(41, (6, 5, 4), 3)
+    A = (H + sigma * sp.identity(H.shape[0])).tocsr()
+    rtol = 1e-6
+    _, k = o.block_pcg_jacobi(A, U, rtol=rtol)
+    for j in range(k + 1):
+        X, _ = o.block_pcg_jacobi(A, U, rtol=0.0, max_iter=j)
+        res = np.linalg.norm(U - A @ X, axis=0) / np.linalg.norm(U, axis=0)
+        if j < k:
+            assert np.any(res > rtol * (1 + 1e-9))
+        else:
+            assert np.all(res <= rtol * (1 + 1e-9))
+
+
 def test_jacobi_pcg_converges_to_the_direct_solution():
     import scipy.sparse as sp
     shape, lo, hi, V, H, sigma, U = random_problem(1, (6, 5, 4), 5)
