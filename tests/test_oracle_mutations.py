@@ -124,3 +124,53 @@ def test_pcg_mutant_copy_is_faithful_without_mistake(monkeypatch):
         test_jacobi_pcg_iterate_minimises_the_energy_error_over_the_krylov_space as pin
     monkeypatch.setattr(o, "block_pcg_jacobi", _pcg_mutant("none"))
     pin()
+
+
+def _residuals_no_sqrt_p(H, U, hnorm):
+    HU = H @ U
+    R = HU - U @ (U.T @ HU)
+    nr = float(np.linalg.norm(R))
+    lam, Y = np.linalg.eigh(U.T @ HU)
+    ri = np.linalg.norm(H @ (U @ Y) - (U @ Y) * lam, axis=0)
+    return nr / hnorm, nr / float(np.linalg.norm(U.T @ HU)), ri     # dropped sqrt(p)
+
+
+def _residuals_theta_norm(H, U, hnorm):
+    HU = H @ U
+    Th = U.T @ HU
+    nr = float(np.linalg.norm(HU - U @ Th))
+    lam, Y = np.linalg.eigh(Th)
+    ri = np.linalg.norm(H @ (U @ Y) - (U @ Y) * lam, axis=0)
+    return nr / float(np.linalg.norm(Th)), nr / float(np.linalg.norm(Th)), ri  # wrong normaliser
+
+
+def _residuals_diagonal_theta(H, U, hnorm):
+    HU = H @ U
+    Th = U.T @ HU
+    R = HU - U * np.diag(Th)                               # Theta replaced by its diagonal
+    nr = float(np.linalg.norm(R))
+    lam, Y = np.linalg.eigh(Th)
+    ri = np.linalg.norm(H @ (U @ Y) - (U @ Y) * lam, axis=0)
+    return nr / (hnorm * np.sqrt(U.shape[1])), nr / float(np.linalg.norm(Th)), ri
+
+
+@pytest.mark.parametrize("mutant", [_residuals_no_sqrt_p, _residuals_theta_norm,
+                                    _residuals_diagonal_theta])
+def test_residual_mutants_break_the_closed_form_pin(monkeypatch, mutant):
+    from tests.test_oracle_pins import test_residuals_closed_form_for_two_rotated_directions as pin
+    monkeypatch.setattr(o, "residuals", mutant)
+    with pytest.raises(AssertionError):
+        pin()
+
+
+def test_gershgorin_diagonal_only_mutant_breaks_the_row_sum_pin(monkeypatch):
+    from tests.test_oracle_pins import \
+        test_gershgorin_norm_is_the_max_row_sum_of_the_pointwise_stencil as pin
+
+    def diag_only(shape, lo, hi, V, sigma):
+        h = o.grid_spacing(shape, lo, hi)
+        return sum(1.0 / (hd * hd) for hd in h) + float(np.max(np.abs(np.asarray(V) + sigma)))
+
+    monkeypatch.setattr(o, "gershgorin_norm", diag_only)
+    with pytest.raises(AssertionError):
+        pin()

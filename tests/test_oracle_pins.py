@@ -544,3 +544,101 @@ def test_l2_flow_is_cfl_limited_and_the_g_flow_is_not():
     assert big[0] is None and not big[1], big
     g = [run(N, "g")[0] for N in (7, 15)]
     assert None not in g and g[1] <= 1.5 * g[0] + 2, g
+
+
+# ----------------------------------------------------------------------------
+# The residual of Algorithm 1's stop rule and its normalisation
+# ----------------------------------------------------------------------------
+def _max_abs_row_sum(A):
+    return float(np.max(np.sum(np.abs(A), axis=1)))
+
+
+def test_gershgorin_norm_is_the_max_row_sum_of_the_pointwise_stencil():
+    # For V + sigma >= 0 with its maximum at a point whose 2 dim neighbours are all
+    # inside the grid, the largest absolute row sum of H + sigma (built point by point)
+    # is exactly 2 sum_d 1/h_d^2 + max(V + sigma).
+    shape, lo, hi = (5, 6, 4), (-1.0, 0.0, 0.5), (1.3, 2.0, 1.1)
+    n = int(np.prod(shape))
+    V = np.random.default_rng(21).uniform(0.0, 2.0, n)
+    V[2 + 5 * (3 + 6 * 2)] = 7.5            # interior point (2, 3, 2)
+    sigma = 0.25
+    Hd = dense_stencil(shape, lo, hi, V) + sigma * np.eye(n)
+    assert o.gershgorin_norm(shape, lo, hi, V, sigma) == pytest.approx(_max_abs_row_sum(Hd),
+                                                                       rel=1e-14)
+
+
+def test_gershgorin_norm_bounds_the_spectral_norm_2d_and_3d():
+    # In general it is an upper bound of ||H + sigma||_inf >= ||H + sigma||_2, also for
+    # a potential of both signs whose extreme sits on the boundary layer.
+    for shape, lo, hi in (((7, 5), (0.0, -1.0), (1.0, 2.0)),
+                          ((4, 5, 3), (-1.0, -1.0, -1.0), (1.0, 0.5, 2.0))):
+        n = int(np.prod(shape))
+        V = np.random.default_rng(5).uniform(-3.0, 3.0, n)
+        V[0] = -9.0                          # a corner point
+        sigma = 0.5
+        Hd = dense_stencil(shape, lo, hi, V) + sigma * np.eye(n)
+        g = o.gershgorin_norm(shape, lo, hi, V, sigma)
+        assert g >= _max_abs_row_sum(Hd) - 1e-12
+        assert g >= np.max(np.abs(np.linalg.eigvalsh(Hd))) - 1e-12
+        # and it is not loose by more than the boundary effect of the corner point
+        h = [(b - a) / (m + 1) for a, b, m in zip(lo, hi, shape)]
+        assert g - _max_abs_row_sum(Hd) <= sum(0.5 / hd ** 2 for hd in h) + 1e-12
+
+
+def _eigen_setup(seed=9):
+    shape, lo, hi = (5, 4, 3), (-1.0, -1.0, -1.0), (1.2, 0.9, 1.1)
+    V = np.random.default_rng(seed).uniform(-1.0, 2.0, 60)
+    Hd = dense_stencil(shape, lo, hi, V)
+    lam, X = np.linalg.eigh(Hd)
+    return shape, lo, hi, V, Hd, lam, X
+
+
+def test_residuals_vanish_on_an_exact_rotated_eigenbasis():
+    shape, lo, hi, V, Hd, lam, X = _eigen_setup()
+    p = 6
+    Q, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((p, p)))
+    U = X[:, :p] @ Q
+    r, r_theta, ri = o.residuals(o.hamiltonian(shape, lo, hi, V), U, 10.0)
+    assert r < 1e-14 and r_theta < 1e-14 and np.max(ri) < 1e-12
+
+
+def test_residuals_closed_form_for_two_rotated_directions():
+    # U = [c1 x_1 + s1 x_k, c2 x_2 + s2 x_m, x_3, .., x_p] Q with k, m > p distinct:
+    # Theta = diag(c1^2 l1 + s1^2 lk, c2^2 l2 + s2^2 lm, l3, ..) rotated by Q, and
+    # H U - U Theta has Frobenius norm sqrt((c1 s1 (lk - l1))^2 + (c2 s2 (lm - l2))^2)
+    # whatever the rotation Q.  r divides it by hnorm sqrt(p); r_theta by ||Theta||_F;
+    # the Ritz residuals r_i are |c1 s1 (lk - l1)|, |c2 s2 (lm - l2)| and zeros.
+    shape, lo, hi, V, Hd, lam, X = _eigen_setup()
+    p, k, m = 5, 11, 17
+    t1, t2 = 0.3, 1.1
+    c1, s1, c2, s2 = math.cos(t1), math.sin(t1), math.cos(t2), math.sin(t2)
+    U = X[:, :p].copy()
+    U[:, 0] = c1 * X[:, 0] + s1 * X[:, k]
+    U[:, 1] = c2 * X[:, 1] + s2 * X[:, m]
+    Q, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((p, p)))
+    U = U @ Q
+    e1, e2 = c1 * s1 * (lam[k] - lam[0]), c2 * s2 * (lam[m] - lam[1])
+    nR = math.hypot(e1, e2)
+    theta = np.array([c1 * c1 * lam[0] + s1 * s1 * lam[k], c2 * c2 * lam[1] + s2 * s2 * lam[m],
+                      *lam[2:p]])
+    hnorm = 37.0
+    r, r_theta, ri = o.residuals(o.hamiltonian(shape, lo, hi, V), U, hnorm)
+    assert r == pytest.approx(nR / (hnorm * math.sqrt(p)), rel=1e-12)
+    assert r_theta == pytest.approx(nR / float(np.linalg.norm(theta)), rel=1e-12)
+    np.testing.assert_allclose(np.sort(ri), np.sort([0.0, 0.0, 0.0, abs(e1), abs(e2)]),
+                               rtol=1e-10, atol=1e-12)
+
+
+def test_residual_of_a_run_uses_the_gershgorin_normalisation():
+    # The run's recorded residual of U^0 is ||H U - U Theta||_F / (hnorm sqrt(p)) with
+    # hnorm = 2 sum_d 1/h_d^2 + max |V + sigma|, computed here from the dense stencil.
+    shape, lo, hi, V, Hd, lam, X = _eigen_setup(4)
+    p = 4
+    U0 = np.random.default_rng(3).standard_normal((60, p))
+    res = o.run(shape, lo, hi, V, U0, max_steps=0, stop="steps")
+    U = o.householder_orthonormalize(U0)
+    HU = Hd @ U
+    nR = float(np.linalg.norm(HU - U @ (U.T @ HU)))
+    h = [(b - a) / (m + 1) for a, b, m in zip(lo, hi, shape)]
+    hn = 2.0 * sum(1.0 / hd ** 2 for hd in h) + float(np.max(np.abs(V + res.sigma)))
+    assert res.resid[0] == pytest.approx(nR / (hn * math.sqrt(p)), rel=1e-12)
