@@ -55,7 +55,8 @@ typedef enum {
 } op_status;
 
 typedef enum {
-  OP_FP64 = 0,           /* blocks, stencil, CG, Gram and update in FP64           */
+  OP_FP64 = 0,           /* blocks, stencil, CG, Gram and update in FP64 (the Gram and
+                            update by op_problem.fp64_gemm)                          */
   OP_FP32 = 1,           /* blocks, stencil and CG in FP32; Gram and update on the
                             tensor cores with a TF32 hi/lo split (FP32-class accuracy),
                             Gram chunk sums in FP64; Step 2-3 core in FP64           */
@@ -89,6 +90,20 @@ typedef enum {
   OP_FLOW_G = 0,
   OP_FLOW_L2 = 1
 } op_flow;
+
+/* How FP64 contexts form their FP64 products of n x p blocks (the Grams of §2.1 and the
+ * Step-4 update, also the set-up Cholesky-QR of every mode).  OP_GEMM_TC: every FP64
+ * operand is written exactly as seven balanced base-256 integer digits (one power-of-two
+ * exponent per row of the contraction), the 28 digit products with digit index sum <= 6
+ * run on the tensor cores (tcgen05 kind::f16) with exact integer level sums over runs of
+ * 256 terms, added in int64 and scaled back in FP64: each product term is exact up to
+ * 2^-53.4 |a| |b| and the result carries an FP64 rounding error relative to the largest
+ * |a| |b| of the run (the error class of an FP64 dot product).  OP_GEMM_FMA: FP64 FMA on
+ * the FP64 pipe (about 2 per clock per SM on GB300). */
+typedef enum {
+  OP_GEMM_TC = 0,
+  OP_GEMM_FMA = 1
+} op_fp64_gemm;
 
 typedef enum {
   OP_STOP_RESIDUAL = 0,  /* r <= tol, r = ||H U - U Theta||_F / (||H+sigma||_G sqrt(p)) */
@@ -135,6 +150,8 @@ typedef struct {
   int cg_precond;        /* op_precond of the Step-1 CG                              */
   int flow;              /* op_flow (contexts; the batched solver and the adaptive
                             shift take OP_FLOW_G only)                               */
+  int fp64_gemm;         /* op_fp64_gemm: FP64 Gram and update of OP_FP64 contexts and
+                            the set-up Cholesky-QR of every context                  */
 } op_problem;
 
 /* Per-context statistics, filled by op_step / op_solve. */
@@ -174,6 +191,15 @@ long long op_kernel_launches(void);
  * On error *ctx is NULL. */
 op_status op_init(op_ctx **ctx, const op_problem *pb, const double *V, const double *U0,
                   void *stream);
+
+/* As op_init, with the raw initial block drawn on the device from `seed` instead of read
+ * from the caller (§5 starts from random data): U0[i][j] is standard normal number
+ * k = i p + j of the SplitMix64 counter stream key = seed ^ 0xD1B54A32D192ED03 (output m of
+ * the stream is mix64(key + (m + 1) 0x9E3779B97F4A7C15); uniform m is ((output m >> 11) +
+ * 0.5) 2^-53; normal k is sqrt(-2 ln u_2k) cos(2 pi u_2k+1), Box-Muller).  V is n FP64
+ * values in host memory.  Allocates and frees a temporary n x p FP64 block. */
+op_status op_init_seeded(op_ctx **ctx, const op_problem *pb, const double *V,
+                         unsigned long long seed, void *stream);
 
 /* As op_init, but V (n FP64) and U0 (n x p FP64, ld = p) are device pointers. */
 op_status op_init_device(op_ctx **ctx, const op_problem *pb, const double *V_dev,
@@ -241,6 +267,20 @@ op_status op_restore(op_ctx *ctx, const void *buf, size_t len);
  * a second. */
 op_status op_selftest_bounded_waits(double *seconds, void *stream);
 
+/* Peak-rate microbenchmarks (the paper has no counterpart): the roofline denominators of
+ * the units the kernels are bound by, measured by this library on the current device
+ * without reading or changing any GPU setting.  OP_PEAK_FP64_FMA: FP64 FMA on the CUDA
+ * cores (independent chains, 2 flops per FMA); OP_PEAK_TF32_MMA / OP_PEAK_BF16_MMA:
+ * tcgen05.mma kind::tf32 / kind::f16 (BF16) at M = 128, N = 256 from operands resident in
+ * shared memory, one CTA per SM.  *tflops receives flops / s / 1e12 of the third of three
+ * launches timed with CUDA events on `stream`.  Allocates and frees a few KB; synchronises. */
+typedef enum {
+  OP_PEAK_FP64_FMA = 0,
+  OP_PEAK_TF32_MMA = 1,
+  OP_PEAK_BF16_MMA = 2
+} op_peak_kind;
+op_status op_peak_rate(int kind, double *tflops, void *stream);
+
 /* Free the context's device memory. NULL is allowed. */
 void op_destroy(op_ctx *ctx);
 
@@ -250,8 +290,9 @@ void op_destroy(op_ctx *ctx);
  * (work lists over (problem, grid-point range), (problem, Gram chunk),
  * (problem, update tile), one CTA per problem for the FP64 core); Step 1 runs a
  * fixed number `cg_iters` of CG iterations per step whose kernels return at once
- * for problems whose CG has converged.  The CG tolerance, the energy, err_E and
- * the freeze of converged problems are computed on the device.
+ * for problems whose CG has converged.  The CG tolerance (a context's cg_rtol when it
+ * is positive, else the adaptive rule of op_problem.cg_rtol with the FP32 floor), the
+ * energy, err_E and the freeze of converged problems are computed on the device.
  * ------------------------------------------------------------------------- */
 typedef struct op_batch op_batch;
 
@@ -263,7 +304,7 @@ typedef struct op_batch op_batch;
  * their own (they may be read: op_get_U, op_eigenvalues, op_residual,
  * op_get_stats).  Destroy the batch before the contexts. */
 op_status op_batch_create(op_batch **b, op_ctx *const *ctxs, int count, int cg_iters,
-                          void *stream);
+                          void *stream);   /* 1 <= cg_iters <= 200 */
 /* Work-list granularity: grid points per stencil/CG/energy item (>= 32) and per Gram
  * chunk (>= 256, multiple of 32).  Rebuilds the graphs.  Synchronises. */
 op_status op_batch_set_tiles(op_batch *b, int rows_per_item, int gram_rows);
@@ -327,15 +368,23 @@ size_t op_gram_workspace(int prec, long long n, int ld);
 /* op_gram without any device allocation (no counterpart in the paper: a service for
  * callers that cannot allocate device memory or hand over a workspace, e.g. because
  * another allocator with a hard budget owns all device memory, or because the calling
- * loop may not enter the driver's allocator).  Same arguments and results as op_gram
- * minus the workspace: the reduction partials live in one library-owned device array
- * of 16 MiB (held on every GPU that loads the library until the process exits).
- * - Limit: the partials of one chunk per output tile must fit, i.e. with all three
- *   products ld <= 896 (OP_FP32, 128 x 128 tiles) or ld <= 960 (OP_FP64, 64 x 64
- *   tiles); larger sizes return OP_ERR_ARG with a message.  Smaller scratch means
- *   fewer, longer grid-point chunks than op_gram uses.
- * - The first call on a device looks up the array's device address (with that
- *   device current); make that first call before any stream capture.
+ * loop may not enter the driver's allocator).  Arguments and results as op_gram minus the
+ * workspace, for prec OP_FP64 or OP_FP32 only (OP_MIX_BF16X3 returns OP_ERR_ARG).  The
+ * reduction partials live in one library-owned device array of 16 MiB.
+ * - Memory: the array belongs to the library's module; with CUDA's default lazy module
+ *   loading the driver reserves it on the first call on each device (16 MiB inside the
+ *   caller's device-memory budget, held until the process exits), so a caller with a fixed
+ *   budget should make that first call during its set-up.
+ * - Limit: one 128 x 128 (OP_FP32) or 64 x 64 (OP_FP64) FP64 tile per output tile must
+ *   fit, i.e. with all three products ld <= 896 (OP_FP32) or ld <= 960 (OP_FP64); larger
+ *   sizes return OP_ERR_ARG with a message.
+ * - Accuracy: OP_FP32 splits the grid points into the same chunks as op_gram and adds the
+ *   FP64 chunk partials into one tile per output tile with atomics (so the FP64 chunk sums
+ *   are taken in a run-dependent order; the FP32 rounding bound is op_gram's).  OP_FP64
+ *   uses fewer, longer chunks than op_gram when the array is small (FP64 register sums).
+ * - The first call on a device looks up the array's device address (with that device
+ *   current) and keeps it; make that first call before any stream capture, and do not
+ *   call this after cudaDeviceReset() on that device (the module and the address go away).
  * - Every call uses the same array: calls that overlap on the GPU (other streams,
  *   other host threads) race and corrupt each other's results.
  * - Synchronises `stream` before returning (it reads back the bounded-wait flag:
@@ -346,6 +395,23 @@ op_status op_gram_noalloc(int prec, long long n, int p, int ld, const void *U, c
 /* Synchronises `stream`; OP_ERR_TIMEOUT if the last op_gram / op_update on ws reported a
  * bounded device wait that gave up, else OP_OK. */
 op_status op_ws_status(void *ws, void *stream);
+
+/* FP64-accurate Gram and update on the tensor cores (the OP_GEMM_TC arithmetic of
+ * op_fp64_gemm) on caller-owned FP64 blocks (n x ld, ld a multiple of 8, 16-byte aligned).
+ * ws: device scratch of at least op_fp64tc_workspace(n, ld) bytes (about 14 bytes per
+ * element of [U W] for up to 8 GiB of digit planes, plus 2 ld x 2 ld FP64); its first int
+ * is set when a bounded device wait gave up (op_ws_status).  Enqueue only.
+ * op_gram_fp64tc: C = <W,U>, S = <W,W>, D = <U,U> as op_gram (ld x ld FP64, zero outside
+ *   p x p; any may be NULL; W may be NULL when only D is wanted).
+ * op_update_fp64tc: Unew = U KU + W KW (computed as U + [U W][KU - I; KW]; W and KW may
+ *   be NULL for Unew = U KU); KU, KW: ld x ld FP64; Unew must not alias U or W. */
+size_t op_fp64tc_workspace(long long n, int ld);
+op_status op_gram_fp64tc(long long n, int p, int ld, const double *U, const double *W,
+                         double *C, double *S, double *D, void *ws, size_t ws_bytes,
+                         void *stream);
+op_status op_update_fp64tc(long long n, int p, int ld, const double *U, const double *W,
+                           const double *KU, const double *KW, double *Unew, void *ws,
+                           size_t ws_bytes, void *stream);
 
 /* Steps 2-3 of §4.1 in FP64: from C = <W,U>, S = <W,W> (ld x ld device, FP64) form
  * M = I + tau/2 (C - C^T) + tau^2/4 (S - C C^T), B = M^-1 (p <= 128: FP32 Gauss-Jordan

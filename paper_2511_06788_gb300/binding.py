@@ -33,7 +33,7 @@ class OpProblem(C.Structure):
                 ("hi", C.c_double * 3), ("p", C.c_int), ("sigma", C.c_double),
                 ("tau", C.c_double), ("prec", C.c_int), ("cg_rtol", C.c_double),
                 ("cg_max_iter", C.c_int), ("check_every", C.c_int), ("adapt_every", C.c_int),
-                ("cg_precond", C.c_int), ("flow", C.c_int)]
+                ("cg_precond", C.c_int), ("flow", C.c_int), ("fp64_gemm", C.c_int)]
 
 
 class OpStats(C.Structure):
@@ -77,6 +77,7 @@ def lib():
         "op_kernel_launches": (C.c_longlong, []),
         "op_init": (i32, [P(vp), P(OpProblem), P(f64), P(f64), vp]),
         "op_init_device": (i32, [P(vp), P(OpProblem), vp, vp, vp]),
+        "op_init_seeded": (i32, [P(vp), P(OpProblem), P(f64), C.c_ulonglong, vp]),
         "op_step": (i32, [vp, i32, P(OpStats)]),
         "op_solve": (i32, [vp, f64, i32, i32, P(OpStats)]),
         "op_energy": (i32, [vp, P(f64)]),
@@ -109,9 +110,13 @@ def lib():
         "op_core_status": (i32, [vp, vp]),
         "op_update": (i32, [i32, C.c_longlong, i32, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
         "op_update_workspace": (sz, [i32, i32]),
+        "op_fp64tc_workspace": (sz, [C.c_longlong, i32]),
+        "op_gram_fp64tc": (i32, [C.c_longlong, i32, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
+        "op_update_fp64tc": (i32, [C.c_longlong, i32, i32, vp, vp, vp, vp, vp, vp, sz, vp]),
         "op_ws_status": (i32, [vp, vp]),
         "op_get_U_device": (i32, [vp, vp, i32]),
         "op_selftest_bounded_waits": (i32, [P(f64), vp]),
+        "op_peak_rate": (i32, [i32, P(f64), vp]),
         "op_checkpoint_size": (sz, [vp]),
         "op_checkpoint": (i32, [vp, vp, sz]),
         "op_restore": (i32, [vp, vp, sz]),
@@ -145,11 +150,12 @@ def last_error() -> str:
 
 PRECONDS = {"none": 0, "jacobi": 1}
 FLOWS = {"g": 0, "l2": 1}
+FP64_GEMMS = {"tc": 0, "fma": 1}
 
 
 def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol=0.0,
                  cg_max_iter=0, check_every=0, adapt_every=0, precond="jacobi",
-                 flow="g") -> OpProblem:
+                 flow="g", fp64_gemm="tc") -> OpProblem:
     pb = OpProblem()
     dim = len(shape)
     pb.dim = dim
@@ -167,6 +173,7 @@ def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol
     pb.adapt_every = int(adapt_every)
     pb.cg_precond = PRECONDS[precond] if isinstance(precond, str) else int(precond)
     pb.flow = FLOWS[flow] if isinstance(flow, str) else int(flow)
+    pb.fp64_gemm = FP64_GEMMS[fp64_gemm] if isinstance(fp64_gemm, str) else int(fp64_gemm)
     return pb
 
 
@@ -196,21 +203,32 @@ class Solver:
     precond: the Step-1 CG, "jacobi" (preconditioned with diag(H + sigma)) or "none".
     flow: "g" (the paper's model, Step 1 solving W = (H + sigma)^-1 U) or "l2" (the L2
     gradient flow W = -(H + sigma) U through the exact Cayley step; CFL-limited).
+    fp64_gemm: "tc" (FP64 Gram and update as exact digit products on the tensor cores) or
+    "fma" (FP64 FMA) for FP64 contexts and every context's set-up (op_fp64_gemm).
+    U0 None: the raw initial block is drawn on the device from `seed` (op_init_seeded,
+    the stream of synthetic.gaussian_block(seed, n, p)).
     The remaining keywords are the op_problem fields of the same names.
     """
 
     def __init__(self, shape, lo, hi, V, U0, p, *, prec="fp64", sigma=None, tau=None,
                  cg_rtol=0.0, cg_max_iter=0, check_every=0, adapt_every=0, precond="jacobi",
-                 flow="g", stream=None, device=False):
+                 flow="g", stream=None, device=False, seed=0, fp64_gemm="tc"):
         self.pb = make_problem(shape, lo, hi, p, prec=prec, sigma=sigma, tau=tau,
                                cg_rtol=cg_rtol, cg_max_iter=cg_max_iter, check_every=check_every,
-                               adapt_every=adapt_every, precond=precond, flow=flow)
+                               adapt_every=adapt_every, precond=precond, flow=flow,
+                               fp64_gemm=fp64_gemm)
         self.n = int(np.prod(shape))
         self.p = int(p)
         self._ctx = C.c_void_p()
         L = lib()
         st = _stream_ptr(stream)
-        if device:
+        if U0 is None:
+            # the raw initial block is drawn on the device from `seed` (op_init_seeded)
+            V = np.ascontiguousarray(V, dtype=np.float64)
+            assert V.shape == (self.n,)
+            check(L.op_init_seeded(C.byref(self._ctx), C.byref(self.pb), _dptr(V),
+                                   C.c_ulonglong(int(seed) & 0xFFFFFFFFFFFFFFFF), st))
+        elif device:
             # V, U0: torch CUDA tensors (float64, contiguous)
             check(L.op_init_device(C.byref(self._ctx), C.byref(self.pb),
                                    C.c_void_p(V.data_ptr()), C.c_void_p(U0.data_ptr()), st))
@@ -510,6 +528,37 @@ def update(U, W, KU_t, KW_t, p, out=None, stream=None, prec=None):
     return out
 
 
+def gram_fp64tc(U, W, p, want=("C", "S", "D"), stream=None):
+    """(C, S, D) as gram() for float64 blocks through op_gram_fp64tc (exact digit products
+    on the tensor cores).  W may be None when only D is wanted."""
+    import torch
+    n, ld = U.shape
+    out = {k: (torch.empty(ld, ld, dtype=torch.float64, device=U.device) if k in want else None)
+           for k in ("C", "S", "D")}
+    nbytes = lib().op_fp64tc_workspace(n, ld)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=U.device)
+    st = _stream_ptr(stream)
+    check(lib().op_gram_fp64tc(n, p, ld, _tptr(U), _tptr(W), _tptr(out["C"]), _tptr(out["S"]),
+                               _tptr(out["D"]), _tptr(ws), nbytes, st))
+    check(lib().op_ws_status(_tptr(ws), st))
+    return out["C"], out["S"], out["D"]
+
+
+def update_fp64tc(U, W, KU, KW, p, out=None, stream=None):
+    """Unew = U KU + W KW for float64 blocks through op_update_fp64tc (W, KW may be None)."""
+    import torch
+    n, ld = U.shape
+    if out is None:
+        out = torch.empty_like(U)
+    nbytes = lib().op_fp64tc_workspace(n, ld)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=U.device)
+    st = _stream_ptr(stream)
+    check(lib().op_update_fp64tc(n, p, ld, _tptr(U), _tptr(W), _tptr(KU), _tptr(KW), _tptr(out),
+                                 _tptr(ws), nbytes, st))
+    check(lib().op_ws_status(_tptr(ws), st))
+    return out
+
+
 class Net:
     """The learned warm start (include/opnet.h): a 3-level conv U-Net V -> Y (n x p).
 
@@ -596,6 +645,16 @@ class Net:
                                      C.c_void_p(Ustar.data_ptr()), float(gamma), float(lr),
                                      float(beta1), float(beta2), float(eps), C.byref(loss)))
         return loss.value
+
+
+PEAKS = {"fp64_fma": 0, "tf32_mma": 1, "bf16_mma": 2}
+
+
+def peak_rate(kind, stream=None) -> float:
+    """TFLOP/s of the library's own microbenchmark of `kind` (PEAKS) on this device."""
+    v = C.c_double()
+    check(lib().op_peak_rate(PEAKS[kind], C.byref(v), _stream_ptr(stream)))
+    return v.value
 
 
 def selftest_bounded_waits(stream=None):

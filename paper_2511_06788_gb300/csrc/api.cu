@@ -22,6 +22,23 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches_so_far() { return g_launches.load(); }
 
+int num_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    v = 152;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 void set_error(const char *fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -130,6 +147,10 @@ op_status check_problem(const op_problem *pb) {
     set_error("unsupported flow %d", pb->flow);
     return OP_ERR_ARG;
   }
+  if (pb->fp64_gemm != OP_GEMM_TC && pb->fp64_gemm != OP_GEMM_FMA) {
+    set_error("unsupported fp64_gemm %d", pb->fp64_gemm);
+    return OP_ERR_ARG;
+  }
   if (pb->flow == OP_FLOW_L2 && pb->adapt_every > 0) {
     set_error("the adaptive shift re-tunes the step of the G flow only (flow %d)", pb->flow);
     return OP_ERR_ARG;
@@ -190,8 +211,21 @@ op_status gram_any(op_ctx *c, const T *U, const T *W, double *C, double *S, doub
                    : c->prec == OP_MIX_BF16X3 ? 2
                    : c->prec == OP_MIX_BF16   ? 3
                                               : 1);
+  else if (c->tc_ws)
+    return gram_fp64tc(c->n, c->p, c->ld, U, W, C, S, D, c->tc_ws, c->tc_bytes, c->dev_err,
+                       c->st);
   else
     return gram<T>(c->n, c->p, c->ld, U, W, C, S, D, c->gram_ws, c->gram_bytes, c->st);
+}
+
+// Step 4 of an FP64 context: U+ = U + [U W][KU - I; KW] on the tensor cores, or
+// [U W][KU; KW] by FP64 FMA.
+op_status update_fp64(op_ctx *c, const double *U, const double *W, const double *KU,
+                      const double *KW, double *Unew) {
+  if (c->tc_ws)
+    return update_fp64tc(c->n, c->ld, U, W, KU, KW, true, Unew, c->tc_ws, c->tc_bytes, c->dev_err,
+                         c->st);
+  return update<double>(c->n, c->ld, U, W, KU, KW, Unew, c->st);
 }
 
 template <typename T> op_status step_impl(op_ctx *c) {
@@ -243,8 +277,8 @@ template <typename T> op_status step_impl(op_ctx *c) {
                        c->prec == OP_MIX_TF32 ? 0 : 1));
     }
   } else {
-    OP_TRY(update<T>(c->n, c->ld, (const T *)c->U, (const T *)c->W, (const T *)c->KU_t,
-                     (const T *)c->KW_t, (T *)c->U2, c->st));
+    OP_TRY(update_fp64(c, (const double *)c->U, (const double *)c->W, c->KU, c->KW,
+                       (double *)c->U2));
   }
   prof_end(&c->prof, c->st);
   void *tmp = c->U;
@@ -292,8 +326,19 @@ template <typename T> op_status residual_impl(op_ctx *c, double *r) {
   OP_TRY(launch_apply<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, Y, c->ld, c->st));
   OP_TRY(gram_any<T>(c, (const T *)c->U, Y, c->Th, nullptr, nullptr));
   OP_TRY(launch_resid_coeff<T>(c->p, c->ld, c->Th, (T *)c->KU_t, (T *)c->KW_t, c->st));
-  OP_TRY(update<T>(c->n, c->ld, (const T *)c->U, Y, (const T *)c->KU_t, (const T *)c->KW_t, Z,
-                   c->st));
+  bool done = false;
+  if constexpr (std::is_same<T, double>::value) {
+    if (c->tc_ws) {
+      // R = [U HU][-Theta; I] (no delta form: the coefficients are not near the identity)
+      OP_TRY(update_fp64tc(c->n, c->ld, (const double *)c->U, Y, (const double *)c->KU_t,
+                           (const double *)c->KW_t, false, Z, c->tc_ws, c->tc_bytes, c->dev_err,
+                           c->st));
+      done = true;
+    }
+  }
+  if (!done)
+    OP_TRY(update<T>(c->n, c->ld, (const T *)c->U, Y, (const T *)c->KU_t, (const T *)c->KW_t, Z,
+                     c->st));
   OP_TRY(launch_sumsq<T>(c->n, c->ld, Z, c->part, c->dsc + 6, c->st));
   prof_end(&c->prof, c->st);
   OP_CUDA(cudaMemcpyAsync(c->hsc + 6, c->dsc + 6, sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -329,7 +374,13 @@ template <typename T> op_status eig_impl(op_ctx *c, double *lam, int kind) {
 // not positive definite.
 op_status cholqr_check(op_ctx *c) {
   OP_CUDA(cudaMemcpyAsync(c->hpin_int, c->core_ws, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  OP_CUDA(cudaMemcpyAsync(c->hpin_int + 1, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost,
+                          c->st));
   OP_CUDA(cudaStreamSynchronize(c->st));
+  if (c->hpin_int[1]) {
+    set_error("a kernel of the set-up gave up a bounded device wait");
+    return OP_ERR_TIMEOUT;
+  }
   if (c->hpin_int[0]) {
     set_error("Cholesky-QR of U0 failed: U0^T U0 is not positive definite");
     return OP_ERR_NOTSPD;
@@ -345,9 +396,9 @@ op_status cholqr_check(op_ctx *c) {
 template <typename T> op_status orthonormalise_impl(op_ctx *c, const double *U0_dev) {
   const size_t blk = (size_t)c->n * c->ld * sizeof(double);
   const size_t gbytes = gram_workspace_bytes(c->n, c->ld, 8);
-  void *A64 = nullptr, *Q64 = nullptr, *gws = nullptr;
+  void *A64 = nullptr, *Q64 = nullptr, *gws = nullptr, *tc_tmp = nullptr;
   auto release = [&]() {
-    for (void *p : {A64, Q64, gws}) {
+    for (void *p : {A64, Q64, gws, tc_tmp}) {
       if (!p) continue;
       cudaFree(p);
       for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
@@ -361,6 +412,11 @@ template <typename T> op_status orthonormalise_impl(op_ctx *c, const double *U0_
   void *ws = c->gram_ws;
   size_t wsb = c->gram_bytes;
   op_status s = OP_OK;
+  // the FP64 products of the set-up: on the tensor cores (digit products) unless the
+  // problem asks for FP64 FMA; FP32 contexts borrow a scratch for it during the set-up
+  const bool use_tc = c->pb.fp64_gemm == OP_GEMM_TC;
+  void *tcw = c->tc_ws;
+  size_t tcb = c->tc_bytes;
   if constexpr (std::is_same<T, double>::value) {
     A = (double *)c->U2;  // FP64 contexts: the context's own blocks are the scratch
     Q = (double *)c->U;
@@ -372,7 +428,15 @@ template <typename T> op_status orthonormalise_impl(op_ctx *c, const double *U0_
     A = (double *)A64;
     Q = (double *)Q64;
   }
-  if (wsb < gbytes) {
+  if (use_tc && !tcw) {
+    tcb = fp64tc_workspace_bytes(c->n, c->ld);
+    if ((s = dev_alloc(c, &tc_tmp, tcb))) {
+      release();
+      return s;
+    }
+    tcw = tc_tmp;
+  }
+  if (!use_tc && wsb < gbytes) {
     if ((s = dev_alloc(c, &gws, gbytes))) {
       release();
       return s;
@@ -381,9 +445,14 @@ template <typename T> op_status orthonormalise_impl(op_ctx *c, const double *U0_
     wsb = gbytes;
   }
   if ((s = launch_pad_copy<double>(c->n, c->p, c->ld, U0_dev, A, c->st)) ||
-      (s = gram<double>(c->n, c->p, c->ld, A, A, nullptr, nullptr, c->D, ws, wsb, c->st)) ||
+      (s = use_tc ? gram_fp64tc(c->n, c->p, c->ld, A, nullptr, nullptr, nullptr, c->D, tcw, tcb,
+                                c->dev_err, c->st)
+                  : gram<double>(c->n, c->p, c->ld, A, A, nullptr, nullptr, c->D, ws, wsb,
+                                 c->st)) ||
       (s = cholqr_coeff(c->p, c->ld, c->D, c->KU, c->core_ws, c->st)) ||
-      (s = update<double>(c->n, c->ld, A, nullptr, c->KU, nullptr, Q, c->st))) {
+      (s = use_tc ? update_fp64tc(c->n, c->ld, A, nullptr, c->KU, nullptr, false, Q, tcw, tcb,
+                                  c->dev_err, c->st)
+                  : update<double>(c->n, c->ld, A, nullptr, c->KU, nullptr, Q, c->st))) {
     release();
     return s;
   }
@@ -472,6 +541,12 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
     c->KT_lo = c->KT_hi + (size_t)ld * 2 * ld;
   }
   OP_TRY(dev_alloc(c, &c->gram_ws, c->gram_bytes));
+  c->tc_ws = nullptr;
+  c->tc_bytes = 0;
+  if (sizeof(T) == 8 && c->pb.fp64_gemm == OP_GEMM_TC) {
+    c->tc_bytes = fp64tc_workspace_bytes(n, ld);
+    OP_TRY(dev_alloc(c, &c->tc_ws, c->tc_bytes));
+  }
   OP_TRY(dev_alloc(c, &p, 256));
   c->dev_err = (int *)p;
   OP_CUDA(cudaMemsetAsync(c->dev_err, 0, 256, c->st));
@@ -557,6 +632,67 @@ op_status init_common(op_ctx **out, const op_problem *pb, const double *V, const
   return OP_OK;
 }
 
+// Raw initial block from a seed: normal k of the SplitMix64 counter stream
+// key = seed ^ (1 * 0xD1B54A32D192ED03) (stream tag 1), drawn by the Box-Muller transform
+// from uniforms 2k and 2k+1 (output j of the stream is mix64(key + (j + 1) * golden
+// gamma); a uniform is ((z >> 11) + 0.5) 2^-53).  SplitMix64: Steele, Lea and Flood,
+// "Fast splittable pseudorandom number generators" (OOPSLA 2014).
+__device__ __forceinline__ unsigned long long splitmix_mix(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_gaussian_block(long long count, unsigned long long key, double *__restrict__ out) {
+  const unsigned long long gamma = 0x9E3779B97F4A7C15ull;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+       k += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long z1 = splitmix_mix(key + (unsigned long long)(2 * k + 1) * gamma);
+    const unsigned long long z2 = splitmix_mix(key + (unsigned long long)(2 * k + 2) * gamma);
+    const double u1 = ((double)(z1 >> 11) + 0.5) * 0x1p-53;
+    const double u2 = ((double)(z2 >> 11) + 0.5) * 0x1p-53;
+    out[k] = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+  }
+}
+
+op_status init_seeded(op_ctx **out, const op_problem *pb, const double *V,
+                      unsigned long long seed, void *stream) {
+  if (!out) {
+    set_error("null ctx pointer");
+    return OP_ERR_ARG;
+  }
+  *out = nullptr;
+  OP_TRY(check_problem(pb));
+  if (!V) {
+    set_error("V must be non-null");
+    return OP_ERR_ARG;
+  }
+  Geom g;
+  OP_TRY(make_geom(pb, &g));
+  cudaStream_t st = (cudaStream_t)stream;
+  double *Vd = nullptr, *U0d = nullptr;
+  const size_t ubytes = (size_t)g.n * pb->p * sizeof(double);
+  cudaError_t e = cudaMalloc((void **)&Vd, g.n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&U0d, ubytes);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Vd, V, g.n * sizeof(double), cudaMemcpyHostToDevice, st);
+  op_status s = OP_OK;
+  if (e == cudaSuccess) {
+    const unsigned long long key = seed ^ (1ull * 0xD1B54A32D192ED03ull);
+    k_gaussian_block<<<num_sms() * 8, 256, 0, st>>>(g.n * pb->p, key, U0d);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess)
+    s = cuda_status(e, "op_init_seeded");
+  else
+    s = init_common(out, pb, Vd, U0d, stream, true);
+  cudaStreamSynchronize(st);
+  if (Vd) cudaFree(Vd);
+  if (U0d) cudaFree(U0d);
+  return s;
+}
+
 }  // namespace
 
 // Adaptive shift (op_problem.adapt_every): from the Ritz values lambda_1 <= .. <=
@@ -594,6 +730,12 @@ op_status op_init(op_ctx **ctx, const op_problem *pb, const double *V, const dou
                   void *stream) {
   g_err[0] = 0;
   return init_common(ctx, pb, V, U0, stream, false);
+}
+
+op_status op_init_seeded(op_ctx **ctx, const op_problem *pb, const double *V,
+                         unsigned long long seed, void *stream) {
+  g_err[0] = 0;
+  return init_seeded(ctx, pb, V, seed, stream);
 }
 
 op_status op_init_device(op_ctx **ctx, const op_problem *pb, const double *V_dev,
@@ -1039,6 +1181,42 @@ op_status op_update(int prec, long long n, int p, int ld, const void *U, const v
   OP_TRY(launch_make_kt_f32(ld, (const float *)KU_t, (const float *)KW_t, KT_hi, KT_lo, st));
   return update_tc(n, ld, (const float *)U, (const float *)W, KT_hi, KT_lo, (float *)Unew,
                    (int *)ws, st);
+}
+
+size_t op_fp64tc_workspace(long long n, int ld) {
+  if (n < 1 || ld < 8) return 0;
+  return kWsHeader + fp64tc_workspace_bytes(n, ld);
+}
+
+op_status op_gram_fp64tc(long long n, int p, int ld, const double *U, const double *W, double *C,
+                         double *S, double *D, void *ws, size_t ws_bytes, void *stream) {
+  if (n < 1 || p < 1 || ld < p || ld % 8 || !U || ((uintptr_t)U & 15) ||
+      (W && ((uintptr_t)W & 15)) || (!W && (C || S)) || !ws ||
+      ws_bytes < op_fp64tc_workspace(n, ld)) {
+    set_error("op_gram_fp64tc: bad arguments (n=%lld p=%d ld=%d; C and S need W; ws >= "
+              "op_fp64tc_workspace())", n, p, ld);
+    return OP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  OP_CUDA(cudaMemsetAsync(ws, 0, sizeof(int), st));
+  return gram_fp64tc(n, p, ld, U, W, C, S, D, (char *)ws + kWsHeader, ws_bytes - kWsHeader,
+                     (int *)ws, st);
+}
+
+op_status op_update_fp64tc(long long n, int p, int ld, const double *U, const double *W,
+                           const double *KU, const double *KW, double *Unew, void *ws,
+                           size_t ws_bytes, void *stream) {
+  if (n < 1 || p < 1 || ld < p || ld % 8 || !U || !KU || !Unew || (W && !KW) ||
+      ((uintptr_t)U & 15) || (W && ((uintptr_t)W & 15)) || ((uintptr_t)Unew & 15) ||
+      Unew == U || Unew == W || !ws || ws_bytes < op_fp64tc_workspace(n, ld)) {
+    set_error("op_update_fp64tc: bad arguments (n=%lld p=%d ld=%d; outputs must not alias "
+              "inputs; ws >= op_fp64tc_workspace())", n, p, ld);
+    return OP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  OP_CUDA(cudaMemsetAsync(ws, 0, sizeof(int), st));
+  return update_fp64tc(n, ld, U, W, KU, W ? KW : nullptr, true, Unew, (char *)ws + kWsHeader,
+                       ws_bytes - kWsHeader, (int *)ws, st);
 }
 
 }  // extern "C"

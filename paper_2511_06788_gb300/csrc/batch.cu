@@ -40,12 +40,17 @@ struct BatchCtl {
   double cg_cap;  // upper bound of the adaptive CG tolerance
 };
 
-// Adaptive CG tolerance of each problem for the coming step (device side):
-// rtol = max(1e-6, min(1e-2, 0.1 g, cap)), g = relative G-residual of the last step.
+// CG tolerance of each problem for the coming step (device side): the context's cg_rtol
+// when positive, else the adaptive rule rtol = max(1e-6, min(1e-2, 0.1 g, cap)),
+// g = relative G-residual of the last step.
 __global__ void k_b_set_tol(const BatchProb *__restrict__ B, const double *__restrict__ stats,
                             const BatchCtl *__restrict__ ctl, int nprob) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nprob) return;
+  if (B[b].fixed_rtol > 0.0) {
+    *B[b].cg_rtol2 = B[b].fixed_rtol * B[b].fixed_rtol;
+    return;
+  }
   const double *s = stats + (long long)b * BS_FIELDS;
   double g = (s[BS_TRS] > 0.0 && s[BS_G2] > 0.0) ? sqrt(s[BS_G2] / s[BS_TRS]) : 1.0;
   double r = 0.1 * g;
@@ -161,6 +166,7 @@ op_status build_lists(op_batch *b) {
     pb.active = c->cgw.active;
     pb.ctl = c->cgw.ctl;
     pb.cg_rtol2 = b->d_rtol2 + i;
+    pb.fixed_rtol = c->pb.cg_rtol > 0.0 ? c->pb.cg_rtol : 0.0;
     pb.C = c->C;
     pb.S = c->S;
     pb.D = c->D;
@@ -334,7 +340,8 @@ extern "C" {
 op_status op_batch_create(op_batch **out, op_ctx *const *ctxs, int count, int cg_iters,
                           void *stream) {
   if (!out || !ctxs || count < 1 || cg_iters < 1 || cg_iters > 200) {
-    set_error("op_batch_create: bad arguments");
+    set_error("op_batch_create: bad arguments (need contexts, count >= 1 and 1 <= cg_iters <= "
+              "200; got count=%d cg_iters=%d)", count, cg_iters);
     return OP_ERR_ARG;
   }
   *out = nullptr;

@@ -119,7 +119,10 @@ inline RowShape row_shape(int ld, int vec) {
   return s;
 }
 
-constexpr int kNumSMs = 152;
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, looked
+// up once per device; 152 on GB300, also the answer when no device can be queried).  Sizes
+// grids and split counts, and with them the workspace sizes derived from it.
+int num_sms();
 
 // NVTX range over a host scope (the enqueue of one phase); profilers that record
 // NVTX attribute the phase's kernels to it.  Costs a few ns when no tool is attached.

@@ -26,6 +26,8 @@ struct op_ctx {
   int *dev_err;          // set by a tensor-core kernel whose bounded wait gave up
   void *cg_ws, *gram_ws, *core_ws;
   void *cayley_ws;       // OP_FLOW_L2: the 2p x 3p system of the exact Cayley step
+  void *tc_ws;           // FP64 contexts with fp64_gemm = OP_GEMM_TC: digit planes etc.
+  size_t tc_bytes;
   size_t gram_bytes;
   CGWork cgw;
   Prof prof;

@@ -166,7 +166,7 @@ GramPlan plan_gram(long long n, int ld, int nprod, int kc) {
   const int nt = (ld + kTile - 1) / kTile;
   GramPlan g;
   g.njobs = nprod * nt * nt;  // upper bound (symmetric products use fewer)
-  const int want = 4 * kNumSMs;
+  const int want = 4 * num_sms();
   long long ns = (want + g.njobs - 1) / g.njobs;
   long long maxs = (n + 255) / 256;
   if (ns > maxs) ns = maxs;
@@ -200,7 +200,7 @@ op_status gram(long long n, int p, int ld, const T *U, const T *W, double *C, do
   GramPlan g = plan_gram(n, ld, 3, GramCfg<T>::KC);
   // recompute the split for the actual job count (more splits when fewer jobs)
   {
-    const int want = 4 * kNumSMs;
+    const int want = 4 * num_sms();
     long long ns = (want + nj - 1) / nj;
     long long maxs = (n + 255) / 256;
     if (ns > maxs) ns = maxs;
@@ -250,7 +250,7 @@ op_status gram_fixed_scratch(long long n, int p, int ld, const T *U, const T *W,
               nj, (size_t)nj * tile_bytes, part_bytes);
     return OP_ERR_ARG;
   }
-  long long ns = (4 * kNumSMs + nj - 1) / nj;
+  long long ns = (4 * num_sms() + nj - 1) / nj;
   const long long maxs = (n + 255) / 256;
   if (ns > maxs) ns = maxs;
   if (ns > fit) ns = fit;

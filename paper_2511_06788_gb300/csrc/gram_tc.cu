@@ -101,7 +101,8 @@ __device__ __forceinline__ void store_patch(uint8_t *hi, uint8_t *lo, int q, int
 __device__ __forceinline__ void gram_tc_body(long long n, int ld, const float *__restrict__ U,
                                              const float *__restrict__ W, int prod, int ti,
                                              int tj, long long r0, long long r1,
-                                             double *__restrict__ dst_tile, int *err, int split) {
+                                             double *__restrict__ dst_tile, int *err, int split,
+                                             bool atomic_out = false) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t mbar[2];  // one per TMEM accumulator
   __shared__ uint32_t tmem_base_sh;
@@ -216,8 +217,14 @@ __device__ __forceinline__ void gram_tc_body(long long n, int ld, const float *_
     if (t == 0) atomicExch(err, 1);
   } else {
     double *dst = dst_tile + row * kTM + half * 64;
+    if (atomic_out) {
+      // the chunk partials of a tile meet in one FP64 tile (fixed-scratch entry point)
 #pragma unroll
-    for (int i = 0; i < 64; ++i) dst[i] = (double)acc[i];
+      for (int i = 0; i < 64; ++i) atomicAdd(dst + i, (double)acc[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 64; ++i) dst[i] = (double)acc[i];
+    }
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -400,12 +407,13 @@ __global__ void __launch_bounds__(256, 1)
 __global__ void __launch_bounds__(256, 1)
     k_gram_tc(long long n, int ld, const float *__restrict__ U, const float *__restrict__ W,
               int mask, int nt, int njobs, long long rows_per_split, double *__restrict__ part,
-              int *err, int split) {
+              int *err, int split, int atomic_out) {
   int prod, ti, tj;
   decode_job(blockIdx.x, mask, nt, &prod, &ti, &tj);
   const long long r0 = (long long)blockIdx.y * rows_per_split;
+  const long long slot = atomic_out ? 0 : (long long)blockIdx.y;
   gram_tc_body(n, ld, U, W, prod, ti, tj, r0, r0 + rows_per_split,
-               part + ((long long)blockIdx.y * njobs + blockIdx.x) * (kTM * kTM), err, split);
+               part + (slot * njobs + blockIdx.x) * (kTM * kTM), err, split, atomic_out != 0);
 }
 
 // Batched: one CTA per GramItem (problem, job, grid-point chunk); all three products.
@@ -473,7 +481,7 @@ int tc_jobs(int nt, int mask) {
 
 // Splits: about three CTAs per SM over all jobs, at least 512 grid points each.
 static void plan_tc(long long n, int njobs, int *nsplit, long long *rps) {
-  long long ns = (3 * kNumSMs + njobs - 1) / njobs;
+  long long ns = (3 * num_sms() + njobs - 1) / njobs;
   const long long maxs = (n + 511) / 512;
   if (ns > maxs) ns = maxs;
   if (ns < 1) ns = 1;
@@ -485,9 +493,9 @@ static void plan_tc(long long n, int njobs, int *nsplit, long long *rps) {
 
 size_t gram_tc_workspace_bytes(long long n, int ld) {
   (void)n;
-  // plan_tc gives nj * nsplit <= 3 * kNumSMs + nj for every subset of the products
+  // plan_tc gives nj * nsplit <= 3 * num_sms() + nj for every subset of the products
   const int nt = (ld + kTM - 1) / kTM;
-  return (size_t)(3 * kNumSMs + tc_jobs(nt, 7)) * kTM * kTM * sizeof(double) + 256;
+  return (size_t)(3 * num_sms() + tc_jobs(nt, 7)) * kTM * kTM * sizeof(double) + 256;
 }
 
 op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, double *C, double *S,
@@ -519,7 +527,7 @@ op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, do
   } else {
     OP_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
     k_gram_tc<<<dim3(nj, nsplit), 256, kSmem, st>>>(n, ld, U, W, mask, nt, nj, rps, part, err,
-                                                     split);
+                                                     split, 0);
     count_launch();
     OP_LAUNCH("k_gram_tc");
   }
@@ -530,7 +538,10 @@ op_status gram_tc(long long n, int p, int ld, const float *U, const float *W, do
   return OP_OK;
 }
 
-// As gram_tc(), but the chunk split is chosen so that the partials fit in part_bytes.
+// As gram_tc() (the same chunks of grid points, so the same FP32 runs and rounding
+// bound), but the chunk partials of each output tile are added into one FP64 tile with
+// atomics: part_bytes must hold one 128 x 128 FP64 tile per output tile.  The FP64
+// chunk sums are taken in whatever order the CTAs finish.
 op_status gram_tc_fixed_scratch(long long n, int p, int ld, const float *U, const float *W,
                                 double *C, double *S, double *D, void *part, size_t part_bytes,
                                 int *err, cudaStream_t st) {
@@ -543,8 +554,7 @@ op_status gram_tc_fixed_scratch(long long n, int p, int ld, const float *U, cons
   const int nj = tc_jobs(nt, mask);
   if (nj == 0) return OP_OK;
   const size_t tile_bytes = (size_t)kTM * kTM * sizeof(double);
-  const long long fit = (long long)(part_bytes / ((size_t)nj * tile_bytes));
-  if (fit < 1) {
+  if (part_bytes < (size_t)nj * tile_bytes) {
     set_error("gram_tc: %d output tiles need %zu bytes of partials, the fixed scratch holds %zu",
               nj, (size_t)nj * tile_bytes, part_bytes);
     return OP_ERR_ARG;
@@ -552,18 +562,14 @@ op_status gram_tc_fixed_scratch(long long n, int p, int ld, const float *U, cons
   int nsplit;
   long long rps;
   plan_tc(n, nj, &nsplit, &rps);
-  if (nsplit > fit) {
-    rps = (n + fit - 1) / fit;
-    rps = (rps + kKS - 1) / kKS * kKS;
-    nsplit = (int)((n + rps - 1) / rps);
-  }
+  OP_CUDA(cudaMemsetAsync(part, 0, (size_t)nj * tile_bytes, st));
   OP_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
   k_gram_tc<<<dim3(nj, nsplit), 256, kSmem, st>>>(n, ld, U, W, mask, nt, nj, rps, (double *)part,
-                                                   err, 1);
+                                                   err, 1, 1);
   count_launch();
   OP_LAUNCH("k_gram_tc");
-  k_gram_tc_reduce<<<dim3(nj, kReduceSlices), 256, 0, st>>>(mask, nt, nj, nsplit,
-                                                             (const double *)part, p, ld, C, S, D);
+  k_gram_tc_reduce<<<dim3(nj, kReduceSlices), 256, 0, st>>>(mask, nt, nj, 1, (const double *)part,
+                                                             p, ld, C, S, D);
   count_launch();
   OP_LAUNCH("k_gram_tc_reduce");
   return OP_OK;

@@ -58,6 +58,7 @@ struct BatchProb {
   double *state;           // CG state [6][ld]
   int *active, *ctl;       // CG control (ctl[0..1] active counts, ctl[2] iterations)
   double *cg_rtol2;        // squared relative CG tolerance of the current step
+  double fixed_rtol;       // the context's cg_rtol when positive (else the adaptive rule)
   double *C, *S, *D, *KU, *KW;
   float *KT_hi, *KT_lo;
   int *core_status;
@@ -221,6 +222,17 @@ op_status core_cayley(int p, int ld, double tau, const double *C, const double *
                       void *ws, cudaStream_t st);
 // Cholesky-QR coefficients: from D = U0^T U0, KU = R^-1 with R = chol(D)^T, written
 // as an ld x ld FP64 matrix (zero outside p x p). Status word as in core().
+// FP64-accurate Gram and update on the tensor cores (exact BF16 digit products, fp64tc.cu).
+// gram_fp64tc: C = <W,U>, S = <W,W>, D = <U,U> (W may be null when only D is wanted).
+// update_fp64tc: Unew = U + [U W][KU - I; KW] (delta) or [U W][KU; KW]; W, KW may be null.
+// ws: fp64tc_workspace_bytes(n, ld) bytes; err: set when a bounded wait gave up.
+size_t fp64tc_workspace_bytes(long long n, int ld);
+op_status gram_fp64tc(long long n, int p, int ld, const double *U, const double *W, double *C,
+                      double *S, double *D, void *ws, size_t ws_bytes, int *err, cudaStream_t st);
+op_status update_fp64tc(long long n, int ld, const double *U, const double *W, const double *KU,
+                        const double *KW, bool delta, double *Unew, void *ws, size_t ws_bytes,
+                        int *err, cudaStream_t st);
+
 op_status cholqr_coeff(int p, int ld, const double *D, double *KU, void *ws, cudaStream_t st);
 // Eigenvalues (ascending) of the symmetric part of the p x p matrix A (stride ld)
 // by cyclic Jacobi on the device; `work` holds 2 p*p doubles; lam receives p values.

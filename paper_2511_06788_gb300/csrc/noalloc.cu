@@ -9,10 +9,17 @@
 // reduction then live in one fixed device array that this file defines; the
 // caller still provides U, W and the output matrices.
 //
-// The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (16 MiB) until the process exits.  Host code may not use
-// its name as a device address, so the address is looked up once per device
-// with cudaGetSymbolAddress, with that device current, on the first call.
+// The array is a file-scope __device__ variable: it belongs to the library's
+// module, so each GPU on which the module is loaded holds it (16 MiB) until the
+// process exits; under CUDA's default lazy module loading that happens on the
+// first call on the device.  Host code may not use its name as a device
+// address, so the address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, on the first call, and kept
+// (a cudaDeviceReset() unloads the module and invalidates it).
+//
+// FP32 blocks use the chunks of op_gram and add each chunk's FP64 partial tile
+// into one tile per output tile with atomics, so one tile per output tile
+// (not one per chunk) has to fit in the array.
 #include <mutex>
 
 #include "common.cuh"

@@ -434,7 +434,7 @@ __global__ void k_unpad_to(long long n, int p, int ld, const S *__restrict__ src
 
 int ew_blocks(long long count) {
   long long b = (count + 255) / 256;
-  const long long cap = (long long)kNumSMs * 16;
+  const long long cap = (long long)num_sms() * 16;
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 

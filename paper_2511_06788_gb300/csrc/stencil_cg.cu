@@ -525,7 +525,7 @@ __global__ void k_unpad_copy(long long n, int p, int ld, const T *__restrict__ s
 // CTAs of a row kernel: four 256-thread CTAs per SM, fewer for small n.
 int grid_blocks(long long n, int rows) {
   long long want = (n + rows - 1) / rows;
-  long long cap = (long long)kNumSMs * 4;
+  long long cap = (long long)num_sms() * 4;
   if (want > cap) want = cap;
   if (want < 1) want = 1;
   return (int)want;
@@ -533,13 +533,13 @@ int grid_blocks(long long n, int rows) {
 
 int warp_blocks(int warps) { return (warps * 32 + 255) / 256; }
 
-// The CTA partials buffer holds up to kNumSMs*8 x 2 x ld doubles; per-column sums follow.
-double *colsum_area(double *part, int ld) { return part + (size_t)kNumSMs * 8 * 2 * ld; }
+// The CTA partials buffer holds up to num_sms()*8 x 2 x ld doubles; per-column sums follow.
+double *colsum_area(double *part, int ld) { return part + (size_t)num_sms() * 8 * 2 * ld; }
 
 }  // namespace
 
 size_t part_bytes(int ld) {
-  return ((size_t)kNumSMs * 8 * 2 * ld + 2 * (size_t)ld) * sizeof(double);
+  return ((size_t)num_sms() * 8 * 2 * ld + 2 * (size_t)ld) * sizeof(double);
 }
 
 // ---------------------------------------------------------------------------
@@ -612,7 +612,7 @@ void cg_carve(void *ws, long long n, int ld, int elem, CGWork *w) {
   p += blk;
   w->Q = p;
   p += blk;
-  w->max_blocks = kNumSMs * 8;
+  w->max_blocks = num_sms() * 8;
   w->part = (double *)p;
   p += (part_bytes(ld) + 255) / 256 * 256;
   w->state = (double *)p;
@@ -766,7 +766,7 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
 
 template <typename T>
 op_status launch_pad_copy(long long n, int p, int ld, const double *src, T *dst, cudaStream_t st) {
-  k_pad_copy<T><<<kNumSMs * 8, 256, 0, st>>>(n, p, ld, src, dst);
+  k_pad_copy<T><<<num_sms() * 8, 256, 0, st>>>(n, p, ld, src, dst);
   count_launch();
   OP_LAUNCH("k_pad_copy");
   return OP_OK;
@@ -775,7 +775,7 @@ op_status launch_pad_copy(long long n, int p, int ld, const double *src, T *dst,
 template <typename T>
 op_status launch_unpad_copy(long long n, int p, int ld, const T *src, double *dst,
                             cudaStream_t st) {
-  k_unpad_copy<T><<<kNumSMs * 8, 256, 0, st>>>(n, p, ld, src, dst);
+  k_unpad_copy<T><<<num_sms() * 8, 256, 0, st>>>(n, p, ld, src, dst);
   count_launch();
   OP_LAUNCH("k_unpad_copy");
   return OP_OK;

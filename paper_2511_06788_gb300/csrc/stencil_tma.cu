@@ -363,7 +363,7 @@ void plan_geometry(const Geom &g, double sigma, int ld, CgTmaGeom *tg, int *grid
   int per_sm = resident_ctas<M_P>();
   const int others[2] = {resident_ctas<M_P_FIRST>(), resident_ctas<M_QUAD>()};
   for (int o : others) per_sm = o < per_sm ? o : per_sm;
-  const long long cap = (long long)kNumSMs * per_sm;
+  const long long cap = (long long)num_sms() * per_sm;
   const long long ncols = (long long)tg->nch * tg->ntx * tg->nty;
   long long S = ncols < cap ? cap / ncols : 1;
   if (S > g.nz) S = g.nz;
@@ -488,6 +488,31 @@ op_status tma_map_2d_f32_sw128(CUtensorMap *map, const void *base, uint64_t inne
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), gd, gs, bx,
                   es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    return OP_ERR_CUDA;
+  }
+  return OP_OK;
+}
+
+op_status tma_map_3d_bf16_sw64(CUtensorMap *map, const void *base, uint64_t inner,
+                               uint64_t rows, uint64_t planes, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return OP_ERR_CUDA;
+  }
+  if (((uintptr_t)base & 15) != 0 || (inner * 2) % 16 != 0 || box_rows < 1 || box_rows > 256) {
+    set_error("tensor map: base or row pitch not 16-byte aligned, or bad box");
+    return OP_ERR_ARG;
+  }
+  cuuint64_t gd[3] = {inner, rows, planes};
+  cuuint64_t gs[2] = {inner * 2, inner * rows * 2};
+  cuuint32_t bx[3] = {32, box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), gd, gs, bx,
+                  es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);

@@ -30,6 +30,14 @@ op_status tma_map_4d_f32(CUtensorMap *map, const void *base, const uint64_t dims
 op_status tma_map_2d_f32_sw128(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
                                uint32_t box_outer);
 
+// 3-D BF16 tensor map over [planes][rows][inner] (inner contiguous, a multiple of 8
+// elements) with a box of 32 x box_rows x 1 elements landing in the 64-byte-swizzled
+// K-major layout (rows of 64 bytes, 16-byte chunk c of row r at chunk c ^ ((r / 2) % 4)
+// within each 512-byte group of 8 rows).  Destinations must be 1024-byte aligned and
+// every inner coordinate a multiple of 8.
+op_status tma_map_3d_bf16_sw64(CUtensorMap *map, const void *base, uint64_t inner,
+                               uint64_t rows, uint64_t planes, uint32_t box_rows);
+
 namespace tma {
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -102,6 +110,15 @@ __device__ __forceinline__ void load_4d(void *dst, const CUtensorMap *map, int c
       "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
       "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                        uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
       : "memory");
 }
 

@@ -34,8 +34,11 @@ __global__ void __launch_bounds__(256) k_update(long long n, int ld, const T *__
   __shared__ __align__(16) T As[KC][kRows + 1];
   __shared__ __align__(16) T Bs[KC][kCols + N];
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 16 + tx;
-  const long long r0 = (long long)blockIdx.y * kRows;
-  const int c0 = blockIdx.x * kCols;
+  // linear block index, column tiles fastest (the CTAs that share a row slab of [U W]
+  // run together); grid.x is not limited to 65535 like grid.y
+  const int nct = (ld + kCols - 1) / kCols;
+  const long long r0 = (long long)(blockIdx.x / nct) * kRows;
+  const int c0 = (int)(blockIdx.x % nct) * kCols;
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -99,8 +102,13 @@ __global__ void __launch_bounds__(256) k_update(long long n, int ld, const T *__
 template <typename T>
 op_status update(long long n, int ld, const T *U, const T *W, const T *KU, const T *KW, T *Unew,
                  cudaStream_t st) {
-  const dim3 grid((ld + kCols - 1) / kCols, (unsigned)((n + kRows - 1) / kRows));
-  k_update<T><<<grid, dim3(16, 16), 0, st>>>(n, ld, U, W, KU, KW, Unew); count_launch();
+  const long long tiles = (long long)((ld + kCols - 1) / kCols) * ((n + kRows - 1) / kRows);
+  if (tiles > 0x7fffffffll) {
+    set_error("update: %lld tiles exceed the launch limit", tiles);
+    return OP_ERR_ARG;
+  }
+  k_update<T><<<(unsigned)tiles, dim3(16, 16), 0, st>>>(n, ld, U, W, KU, KW, Unew);
+  count_launch();
   OP_LAUNCH("k_update");
   return OP_OK;
 }

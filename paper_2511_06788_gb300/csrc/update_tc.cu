@@ -665,7 +665,7 @@ op_status update_tc(long long n, int ld, const float *U, const float *W, const f
     OP_TRY(tma_map_2d_f32_sw128(&mKh, KT_hi, 2 * ld, ld, kTN));
     OP_TRY(tma_map_2d_f32_sw128(&mKl, KT_lo, 2 * ld, ld, kTN));
     const long long ntiles = (n + kTM - 1) / kTM * ((ld + kTN - 1) / kTN);
-    const int grid = (int)std::min<long long>(ntiles, kNumSMs);
+    const int grid = (int)std::min<long long>(ntiles, num_sms());
     OP_CUDA(cudaFuncSetAttribute(k_update_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemR));
     k_update_ws<<<grid, kWarpsWS * 32, kSmemR, st>>>(mU, mW, mKh, mKl, n, ld, U, Unew, err,

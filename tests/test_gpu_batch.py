@@ -137,3 +137,41 @@ def test_batch_solve_with_adaptive_shift():
     assert sum(steps["adapt"]) <= sum(steps["fixed"])
     for s in fixed + adapt:
         s.close()
+
+
+# Five problems of the 64-problem workload (synthetic.batch_problems(0)): a 48^3 grid,
+# p = 96, and three more between 26^3 and 46^3 with p from 22 to 69.
+C4_PICK = (43, 46, 0, 1, 37)
+
+
+def test_batch_step_matches_oracle_at_the_batch_workload_sizes():
+    """One batched step against the oracle's step with an exact Step 1 (§4.1, Steps 1-4),
+    problem by problem, from the same U (the FP32 values each context holds).  The batch
+    solves Step 1 to the FP32 floor (cg_rtol 1e-6, enough iterations to converge); the
+    expected agreement is that of one FP32 step at p = 1024: CG rtol 1e-6 times tau ||B||
+    plus FP32 rounding, max|dU| / max|U| <= 1e-5, ||U^T U - I||_F <= 1e-5 and
+    |dE| / |E| <= 1e-6."""
+    allp = syn.batch_problems(0, 64)
+    probs = [allp[i] for i in C4_PICK]
+    assert max(P.shape[0] for P in probs) == 48 and max(P.p for P in probs) == 96
+    solvers = [pkg.Solver(P.shape, P.lo, P.hi, P.V, syn.gaussian_block(100 + i, P.n, P.p), P.p,
+                          prec="fp32", cg_rtol=1e-6) for i, P in zip(C4_PICK, probs)]
+    U0 = [s.get_U() for s in solvers]
+    with pkg.Batch(solvers, cg_iters=200) as b:
+        b.step(1)
+        out = [(s.get_U(), b.stats(i)) for i, s in enumerate(solvers)]
+    for (U, st), Ua, P in zip(out, U0, probs):
+        assert st["steps"] == 1 and st["last_cg_iters"] < 200  # converged before the cap
+        H = o.hamiltonian(P.shape, P.lo, P.hi, P.V.astype(np.float32).astype(np.float64))
+        W = o.SourceSolver(H, st["sigma"], cg_rtol=1e-11).solve(Ua)
+        U1 = o.scheme_step(Ua, W, st["tau"])
+        E1 = o.energy(H, U1)
+        du = np.abs(U - U1).max() / np.abs(U1).max()
+        orth = np.linalg.norm(U.T @ U - np.eye(P.p))
+        print(f"{P.name}: max|dU|/max|U| {du:.2e} orth {orth:.2e} "
+              f"dE/E {abs(st['energy'] - E1) / abs(E1):.2e} cg {st['last_cg_iters']}")
+        assert du <= 1e-5
+        assert orth <= 1e-5
+        assert st["energy"] == pytest.approx(E1, rel=1e-6)
+    for s in solvers:
+        s.close()

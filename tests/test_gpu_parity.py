@@ -525,3 +525,17 @@ def test_full_size_3d_wells_steps(c2, prec):
     assert np.all(np.diff(E) < 0)
     assert np.linalg.norm(U.T @ U - np.eye(p)) < (1e-12 if prec == "fp64" else 1e-4)
     assert math.isfinite(st["g_residual"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_seeded_init_draws_the_synthetic_gaussian_block(prec):
+    """op_init_seeded draws U0 on the device from the same SplitMix64 / Box-Muller stream as
+    synthetic.gaussian_block(seed): both contexts hold the same orthonormal U (the device's
+    log and cos may differ from the host's by an ulp)."""
+    P = syn.wells_3d(12, 9, 3, 2)
+    with pkg.Solver(P.shape, P.lo, P.hi, P.V, None, P.p, prec=prec, seed=77) as a, \
+            pkg.Solver(P.shape, P.lo, P.hi, P.V, syn.gaussian_block(77, P.n, P.p), P.p,
+                       prec=prec) as b:
+        Ua, Ub = a.get_U(), b.get_U()
+    assert np.abs(Ua - Ub).max() <= (1e-12 if prec == "fp64" else 1e-6)
+    assert np.linalg.norm(Ua.T @ Ua - np.eye(P.p)) < (1e-13 if prec == "fp64" else 1e-5)

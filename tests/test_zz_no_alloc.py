@@ -72,3 +72,55 @@ def test_noalloc_gram_rejects_sizes_beyond_its_scratch():
         pkg.binding.gram_noalloc(U, U, p)
     assert e.value.status == pkg.binding.OP_ERR_ARG
     assert "fixed scratch" in str(e.value)
+
+
+def test_noalloc_gram_allocates_nothing():
+    # after a first call (which may load the library's module and its array), a further
+    # call leaves the device's free memory unchanged
+    n, p, ld = 20011, 64, 64
+    U, W = _blocks(5, n, p, ld, torch.float32)
+    pkg.binding.gram_noalloc(U, W, p)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    pkg.binding.gram_noalloc(U, W, p)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_gram_fp64_size_limit():
+    # FP64: 64 x 64 tiles; with all three products ld = 960 fits the array, 968 does not
+    n = 300
+    U = torch.zeros(n, 960, dtype=torch.float64, device=DEV)
+    U[:, :960] = torch.randn(n, 960, dtype=torch.float64, device=DEV)
+    C, S, D = pkg.binding.gram_noalloc(U, U, 960)
+    Uh = U.cpu().numpy()
+    assert np.abs(D.cpu().numpy() - Uh.T @ Uh).max() <= 1e-12 * n
+    V = torch.zeros(n, 968, dtype=torch.float64, device=DEV)
+    with pytest.raises(pkg.OpError) as e:
+        pkg.binding.gram_noalloc(V, V, 968)
+    assert e.value.status == pkg.binding.OP_ERR_ARG
+
+
+def test_noalloc_gram_fp32_widest_blocks_over_a_million_points():
+    """ld = 896 (the widest FP32 blocks that fit) over n > 10^6 grid points: the chunks
+    are op_gram's (here 5 chunks of 200032 points per output tile), so every entry is
+    within the FP32 rounding bound of that run length, (64 + 200032 / 32) 2^-24 sum |x y|
+    (a 32-point slab on the tensor cores, then one FP32 addition per slab), checked
+    against FP64 sums on sampled entries, and equal to op_gram's up to the order of the
+    FP64 chunk sums."""
+    n, p, ld = 1_000_003, 896, 896
+    U, W = _blocks(21, n, p, ld, torch.float32)
+    got = pkg.binding.gram_noalloc(U, W, p)
+    ref = pkg.gram(U, W, p)
+    run = 200032 // 32
+    bound_scale = (64 + run) * 2.0 ** -24
+    rng = np.random.default_rng(3)
+    for M, R, (X, Y) in zip(got, ref, ((W, U), (W, W), (U, U))):
+        Mh, Rh = M.cpu().numpy(), R.cpu().numpy()
+        assert np.abs(Mh - Rh).max() <= 1e-9 * np.abs(Rh).max()
+        for i, j in rng.integers(0, p, (48, 2)):
+            x, y = X[:, i].double(), Y[:, j].double()
+            exact = float((x * y).sum())
+            mag = float((x.abs() * y.abs()).sum())
+            assert abs(Mh[i, j] - exact) <= bound_scale * mag, (i, j, Mh[i, j], exact)
