@@ -1,13 +1,16 @@
 """Throughput of the orthogonality-preserving scheme on one GB300 (per rank).
 
-One bench "step" is one time step of the scheme (Steps 1-4 of §4.1 plus the
-energy of Algorithm 1) on the 3D workload: 64^3 interior grid on [-8, 8]^3,
-V = |x|^2/2 plus 8 seeded Gaussian wells (depth U[1,5], width U[0.5,1.5]),
-p = 128 orbitals.  value = n * p * steps / second (orbital-updates/s), summed
-over ranks (each rank advances its own seeded instance: weak scaling).
+One bench "step" is one time step of the scheme (Steps 1-4 of §4.1 plus the energy of
+Algorithm 1).  The default workload is the largest configuration that fits one GPU:
+a 128^3 interior grid on [-8, 8]^3, V = |x|^2/2 plus 32 seeded Gaussian wells (depth
+U[1,5], width U[0.5,1.5]), p = 1024 orbitals, in the paper's arithmetic (FP64; the FP64
+Gram and update run as exact integer-digit products on the tensor cores).  value =
+n * p * steps / second (orbital-updates/s), summed over ranks (each rank advances its
+own seeded instance: weak scaling).  Legs of the same workload report the FP32 and
+BF16 x 3 modes and FP64 with FP64-FMA products against it.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64]
-                       [--impl ours|reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload c3|3d_wells_64|...]
 Under torchrun (N > 1) every rank runs; rank 0 prints one JSON line.
 """
 from __future__ import annotations
@@ -31,6 +34,7 @@ import numpy as np  # noqa: E402
 import synthetic as syn  # noqa: E402
 
 WORKLOAD = "3d_wells_64^3_p128"
+HEADLINE = "3d_wells_128^3_p1024"
 METRIC = "n*p orbital-updates/s"
 UNIT = "orbital-updates/s"
 
@@ -61,6 +65,24 @@ ALGO_BYTES = {
 # full, S and D one triangle each; the update [U W] [KU; KW] is n x 2p x p)
 FP64_FLOPS = {"gram": lambda n, p: 4 * n * p * p, "update": lambda n, p: 4 * n * p * p}
 FP64_TFLOPS = 1.25  # GB300 nominal FP64 (non-tensor) rate
+# FP64 CG kernels (three-kernel iteration, Jacobi variant): algorithmic FP64 flops per
+# element of the n x p block (FMA = 2): the 7-point apply is 3 pair sums, the diagonal
+# product and three scaled subtractions (10); p.q adds 2.  axpy: w += a p, z -= a q / d,
+# rk = d z and two sums (10); dir: p = z + b p (2); init: apply, u - Aw, / d, three sums (18).
+FP64_CG_FLOPS = {"cg_apply": 12, "cg_axpy": 10, "cg_dir": 2, "cg_init": 18, "energy": 14}
+# digit-product kernels: 28 BF16 MMAs per digit pair set, 2 flops per multiply-add
+
+
+def digit_flops(group, n, ld):
+    """BF16 tensor flops one step's FP64 Gram / update issues on the tensor cores."""
+    if group == "gram":
+        nc = 2 * ld
+        nI, nJ = (nc + 127) // 128, (nc + 63) // 64
+        tiles = sum(max(0, nJ - 2 * i) for i in range(nI))
+        return 28 * 2 * tiles * 128 * 64 * n
+    if group == "update":
+        return 28 * 2 * ((n + 127) // 128 * 128) * ((ld + 63) // 64 * 64) * 2 * ld
+    return 0
 KERNEL_NAME = {("cg_apply", "fp32"): "k_cg_tma", ("cg_axpy", "fp32"): "k_cg_wr",
                ("cg_apply", "fp64"): "k_cg_apply", ("cg_axpy", "fp64"): "k_cg_axpy",
                ("cg_dir", "fp64"): "k_cg_dir", ("gram", "fp32"): "k_gram_tc",
@@ -230,23 +252,53 @@ def oracle_sample(P, U0, p_sample, steps, warmup=0):
     return P.n * p_sample * steps / secs, secs, desc
 
 
+def headline_problem(rank):
+    """The default workload: 128^3 grid, harmonic trap plus 32 wells, p = 1024 (seed = rank)."""
+    return syn.wells_3d(128, 1024, 32, seed=rank)
+
+
+def oracle_headline_sample(P, seed, p_sample, steps, warmup=0):
+    """The oracle as it stands on the headline workload restricted to its first p_sample
+    orbitals (Step 1 is p independent solves), the raw U0 columns drawn from the same
+    seeded stream as the device's.  Returns (orbital-updates/s, seconds, description)."""
+    import oracle as o
+    U0 = syn.gaussian_columns(seed, P.n, P.p, np.arange(p_sample))
+    times = []
+    t_last = [time.perf_counter()]
+
+    def cb(n, U, W):
+        now = time.perf_counter()
+        times.append(now - t_last[0])
+        t_last[0] = now
+
+    t_last[0] = time.perf_counter()
+    o.run(P.shape, P.lo, P.hi, P.V, U0, stop="steps", max_steps=warmup + steps,
+          track_residual=False, callback=cb)
+    timed = times[warmup:]
+    secs = float(sum(timed))
+    desc = (f"{steps} time step(s) after {warmup} warm-up step(s) of the {HEADLINE} problem "
+            f"restricted to its first {p_sample} of {P.p} orbitals (FP64 oracle: Step 1 by CG "
+            f"to 1e-13 warm-started from the previous step's W; numpy/scipy on one thread: "
+            f"scipy's sparse products are single-threaded and the dense algebra of a "
+            f"{p_sample}-orbital sample is negligible)")
+    return P.n * p_sample * steps / secs, secs, desc
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    P = syn.config_3d_wells(0)
-    U0 = syn.gaussian_block(0, P.n, P.p)
-    p_sample = 8
-    v, secs, desc = oracle_sample(P, U0, p_sample, args.steps, args.warmup)
-    cores = os.cpu_count()
+    P = headline_problem(0)
+    p_sample = 1
+    v, secs, desc = oracle_headline_sample(P, 0, p_sample, args.steps, args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": P.n, "p": P.p, "p_sample": p_sample,
+        "config": {"workload": HEADLINE, "n": P.n, "p": P.p, "p_sample": p_sample,
                    "precision": "fp64", "seed": 0},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -392,6 +444,196 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_headline(args):
+    """The default workload (128^3 x 1024, FP64) timed on the device, with the FP64-FMA,
+    FP32 and BF16 x 3 legs, the roofline of the dominant kernel group, the end-to-end run
+    through op_init with host buffers and the oracle timed on a host sample."""
+    import torch
+
+    import paper_2511_06788_gb300 as pkg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    P = headline_problem(rank)
+    n, p, ld = P.n, P.p, (P.p + 7) // 8 * 8
+    # roofline denominators measured by the library's own microbenchmarks, before the run
+    peaks = {k: pkg.binding.peak_rate(k, stream) for k in ("fp64_fma", "tf32_mma", "bf16_mma")}
+    hbm, _, peak_kind = load_peaks()
+    bf16_sust = _sustained_bf16()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # inputs resident in HBM: V and the raw U0 (the seeded stream of op_init_seeded)
+    V_d = torch.from_numpy(P.V).to(dev)
+    U0_d = pkg.binding.gaussian_block(rank, n, p, device=dev, stream=stream)
+    barrier()
+    t0 = time.perf_counter()
+    solver = pkg.Solver(P.shape, P.lo, P.hi, V_d, U0_d, p, prec="fp64", stream=stream,
+                        device=True, precond="jacobi")
+    barrier()
+    setup_s = time.perf_counter() - t0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    U2, E2, step2_ms = None, None, None
+    for k in range(args.warmup):
+        if k == 1:
+            ev[0].record(stream)
+        st = solver.step(1)
+        if k == 1:
+            ev[1].record(stream)
+            barrier()
+            step2_ms = ev[0].elapsed_time(ev[1])
+            U2, E2 = solver.get_U_device(torch.float64), st["energy"]
+    solver.profile(True)
+    launches0 = pkg.lib().op_kernel_launches()
+    st0 = solver.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        solver.step(1)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = pkg.lib().op_kernel_launches() - launches0
+    st1 = solver.stats()
+    prof = solver.profile_read()
+    solver.profile(False)
+    solver.close()
+    ms = max_over_ranks(ms, dev, ws)
+    value = job_value(n * p, args.steps, ws, ms)
+
+    # rooflines of every timed group; the dominant one (most device time) is the headline's
+    groups = {k: v for k, v in prof.items() if v[1] > 0}
+    rooflines = {}
+    for g, (tot_ms, cnt) in groups.items():
+        avg_s = tot_ms * 1e-3 / cnt
+        if g in ("gram", "update"):
+            fl = digit_flops(g, n, ld)
+            a = fl / avg_s / 1e12
+            rooflines[g] = {"bound": "tensor", "kernel": "k_fp64tc (with its digit split)",
+                            "achieved": a, "peak": bf16_sust, "unit": "TFLOP/s",
+                            "frac": a / bf16_sust, "traffic": None,
+                            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained "
+                                           "(cuBLAS BF16, seconds-long loop)",
+                            "algo_flops_per_launch": fl, "avg_launch_ms": 1e3 * avg_s,
+                            "share_of_step_time": tot_ms / ms}
+        elif g in FP64_CG_FLOPS:
+            fl = FP64_CG_FLOPS[g] * n * p
+            a = fl / avg_s / 1e12
+            by = algo_bytes(g, "fp64", n, p, 8, cnt, args.steps) if g != "energy" else \
+                n * 8 * (p + 1)
+            rooflines[g] = {"bound": "alu", "kernel": KERNEL_NAME.get((g, "fp64"), g),
+                            "achieved": a, "peak": peaks["fp64_fma"], "unit": "TFLOP/s",
+                            "frac": a / peaks["fp64_fma"], "traffic": None,
+                            "peak_source": "measured by op_peak_rate(OP_PEAK_FP64_FMA) in "
+                                           "this run",
+                            "algo_flops_per_launch": fl, "avg_launch_ms": 1e3 * avg_s,
+                            "hbm_frac": by / avg_s / 1e9 / hbm,
+                            "share_of_step_time": tot_ms / ms}
+    dom = max(rooflines, key=lambda g: rooflines[g]["share_of_step_time"])
+    roofline = dict(rooflines[dom], group=dom)
+    kernel_times = {k: {"ms": round(v[0], 3), "groups": v[1]} for k, v in groups.items()}
+
+    # legs: two steps of each mode from the same U0; the second step timed, U and E after
+    # it compared with the FP64 run's
+    legs = {}
+    for leg in [x for x in args.legs.split(",") if x and x != "none"] if rank == 0 else []:
+        prec, gemm = ("fp64", "fma") if leg == "fp64_fma" else (leg, "tc")
+        s = pkg.Solver(P.shape, P.lo, P.hi, V_d, U0_d, p, prec=prec, stream=stream, device=True,
+                       precond="jacobi", fp64_gemm=gemm)
+        s.step(1)
+        ev[0].record(stream)
+        st = s.step(1)
+        ev[1].record(stream)
+        barrier()
+        leg_ms = ev[0].elapsed_time(ev[1])
+        U = s.get_U_device(torch.float64)
+        s.close()
+        legs[leg] = {"ms_step2": leg_ms, "fp64_ms_step2": step2_ms,
+                     "step_time_vs_fp64": leg_ms / step2_ms,
+                     "max_dU_rel_vs_fp64": float((U - U2).abs().max() / U2.abs().max()),
+                     "dE_rel_vs_fp64": abs(st["energy"] - E2) / abs(E2),
+                     "orth": st["orth"], "cg_iters_step2": st["last_cg_iters"]}
+        del U
+        torch.cuda.empty_cache()
+    del U2
+    torch.cuda.empty_cache()
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    e2e = None
+    if rank == 0 or ws > 1:
+        Vh = torch.from_numpy(P.V).pin_memory()
+        Uh = torch.empty(n, p, dtype=torch.float64).pin_memory()
+        Uh.copy_(U0_d)
+        del U0_d
+        torch.cuda.empty_cache()
+        Uout = torch.empty(n, p, dtype=torch.float64).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        s2 = pkg.Solver(P.shape, P.lo, P.hi, Vh.numpy(), Uh.numpy(), p, prec="fp64",
+                        stream=stream, precond="jacobi")
+        s2.step(args.steps)
+        s2.get_U(out=Uout.numpy())
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t0
+        s2.close()
+        e2e = {"value": n * p * args.steps * ws / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": (n + n * p) * 8 / args.steps,
+               "d2h_bytes_per_step": n * p * 8 / args.steps,
+               "includes": "op_init (upload V, U0 from pinned host memory; FP64 Cholesky-QR) "
+                           "+ K steps from U0 + op_get_U into pinned host memory; op_destroy "
+                           "after the clock stops"}
+        del Uh, Uout
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, secs, desc = oracle_headline_sample(P, rank, 2, 1, 1)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": secs}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": HEADLINE, "n": n, "p": p, "precision": "fp64",
+                       "fp64_products": "Gram and update as exact integer-digit products on "
+                                        "the tensor cores (op_fp64_gemm OP_GEMM_TC)",
+                       "cg_precond": "jacobi", "seed_per_rank": "rank",
+                       "l2": f"inputs larger than L2 (each n x p block {n * p * 8 / 1e9:.1f} GB)",
+                       "cg_iters_per_step": (st1["cg_iters"] - st0["cg_iters"]) / args.steps,
+                       "setup_s": setup_s},
+            "roofline": roofline, "rooflines": rooflines, "kernel_ms": kernel_times,
+            "measured_peaks_tflops": peaks, "legs": legs, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+            "stats": {"energy": st1["energy"], "orth": st1["orth"], "err_E": st1["err_E"]},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _sustained_bf16():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("bf16_tflops_sustained", d.get("bf16_tflops", 1700.0))
+    return 1700.0
 
 
 def run_batch(args):
@@ -828,9 +1070,11 @@ def main():
                     help="Step-1 CG preconditioner of the 3d_wells_64 workload")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="3d_wells_64",
-                    choices=["3d_wells_64", "batch64", "warmstart48", "ttr64", "batch64-ttr",
-                             "c3"])
+    ap.add_argument("--workload", default="c3fp64",
+                    choices=["c3fp64", "3d_wells_64", "batch64", "warmstart48", "ttr64",
+                             "batch64-ttr", "c3"])
+    ap.add_argument("--legs", default="fp32,mix_bf16x3,fp64_fma",
+                    help="modes timed beside the default workload (comma list or none)")
     ap.add_argument("--bttr-tol", type=float, default=1e-6)
     ap.add_argument("--bttr-cap", type=int, default=3000)
     ap.add_argument("--ttr-fp64-count", type=int, default=8)
@@ -863,7 +1107,9 @@ def main():
         return run_batch_ttr(args)
     if args.workload == "c3":
         return run_c3(args)
-    return run_ours(args)
+    if args.workload == "3d_wells_64":
+        return run_ours(args)
+    return run_headline(args)
 
 
 if __name__ == "__main__":

@@ -201,6 +201,11 @@ op_status op_init(op_ctx **ctx, const op_problem *pb, const double *V, const dou
 op_status op_init_seeded(op_ctx **ctx, const op_problem *pb, const double *V,
                          unsigned long long seed, void *stream);
 
+/* The raw initial block of op_init_seeded, drawn into caller-owned device memory U0
+ * (n x p FP64, ld = p) on `stream` (enqueue only). */
+op_status op_gaussian_block(unsigned long long seed, long long n, int p, double *U0,
+                            void *stream);
+
 /* As op_init, but V (n FP64) and U0 (n x p FP64, ld = p) are device pointers. */
 op_status op_init_device(op_ctx **ctx, const op_problem *pb, const double *V_dev,
                          const double *U0_dev, void *stream);

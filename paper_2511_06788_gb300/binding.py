@@ -78,6 +78,7 @@ def lib():
         "op_init": (i32, [P(vp), P(OpProblem), P(f64), P(f64), vp]),
         "op_init_device": (i32, [P(vp), P(OpProblem), vp, vp, vp]),
         "op_init_seeded": (i32, [P(vp), P(OpProblem), P(f64), C.c_ulonglong, vp]),
+        "op_gaussian_block": (i32, [C.c_ulonglong, C.c_longlong, i32, vp, vp]),
         "op_step": (i32, [vp, i32, P(OpStats)]),
         "op_solve": (i32, [vp, f64, i32, i32, P(OpStats)]),
         "op_energy": (i32, [vp, P(f64)]),
@@ -645,6 +646,16 @@ class Net:
                                      C.c_void_p(Ustar.data_ptr()), float(gamma), float(lr),
                                      float(beta1), float(beta2), float(eps), C.byref(loss)))
         return loss.value
+
+
+def gaussian_block(seed, n, p, device=None, stream=None):
+    """The raw initial block of op_init_seeded (synthetic.gaussian_block's stream) drawn on
+    the device: an n x p float64 CUDA tensor."""
+    import torch
+    out = torch.empty(n, p, dtype=torch.float64, device=device or "cuda")
+    check(lib().op_gaussian_block(C.c_ulonglong(int(seed) & 0xFFFFFFFFFFFFFFFF), int(n), int(p),
+                                  _tptr(out), _stream_ptr(stream)))
+    return out
 
 
 PEAKS = {"fp64_fma": 0, "tf32_mma": 1, "bf16_mma": 2}

@@ -655,6 +655,15 @@ __global__ void k_gaussian_block(long long count, unsigned long long key, double
   }
 }
 
+op_status launch_gaussian_block(unsigned long long seed, long long count, double *out,
+                                cudaStream_t st) {
+  const unsigned long long key = seed ^ (1ull * 0xD1B54A32D192ED03ull);
+  k_gaussian_block<<<num_sms() * 8, 256, 0, st>>>(count, key, out);
+  count_launch();
+  OP_LAUNCH("k_gaussian_block");
+  return OP_OK;
+}
+
 op_status init_seeded(op_ctx **out, const op_problem *pb, const double *V,
                       unsigned long long seed, void *stream) {
   if (!out) {
@@ -678,10 +687,13 @@ op_status init_seeded(op_ctx **out, const op_problem *pb, const double *V,
     e = cudaMemcpyAsync(Vd, V, g.n * sizeof(double), cudaMemcpyHostToDevice, st);
   op_status s = OP_OK;
   if (e == cudaSuccess) {
-    const unsigned long long key = seed ^ (1ull * 0xD1B54A32D192ED03ull);
-    k_gaussian_block<<<num_sms() * 8, 256, 0, st>>>(g.n * pb->p, key, U0d);
-    count_launch();
-    e = cudaGetLastError();
+    const op_status gs = launch_gaussian_block(seed, g.n * pb->p, U0d, st);
+    if (gs != OP_OK) {
+      cudaStreamSynchronize(st);
+      cudaFree(Vd);
+      cudaFree(U0d);
+      return gs;
+    }
   }
   if (e != cudaSuccess)
     s = cuda_status(e, "op_init_seeded");
@@ -1181,6 +1193,15 @@ op_status op_update(int prec, long long n, int p, int ld, const void *U, const v
   OP_TRY(launch_make_kt_f32(ld, (const float *)KU_t, (const float *)KW_t, KT_hi, KT_lo, st));
   return update_tc(n, ld, (const float *)U, (const float *)W, KT_hi, KT_lo, (float *)Unew,
                    (int *)ws, st);
+}
+
+op_status op_gaussian_block(unsigned long long seed, long long n, int p, double *U0,
+                            void *stream) {
+  if (n < 1 || p < 1 || !U0) {
+    set_error("op_gaussian_block: need n >= 1, p >= 1 and an output block");
+    return OP_ERR_ARG;
+  }
+  return launch_gaussian_block(seed, n * p, U0, (cudaStream_t)stream);
 }
 
 size_t op_fp64tc_workspace(long long n, int ld) {

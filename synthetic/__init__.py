@@ -75,6 +75,24 @@ def gaussian_block(seed: int, n: int, p: int) -> np.ndarray:
     return gaussian(stream_key(seed, STREAM_U0), 0, n * p).reshape(n, p)
 
 
+def gaussian_at(key: np.uint64, idx: np.ndarray) -> np.ndarray:
+    """Normals number idx (any indices) of the stream `key` (as gaussian())."""
+    k = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z1 = _mix64(key + (np.uint64(2) * k + np.uint64(1)) * GAMMA)
+        z2 = _mix64(key + (np.uint64(2) * k + np.uint64(2)) * GAMMA)
+    u1 = ((z1 >> np.uint64(11)).astype(np.float64) + 0.5) * (2.0 ** -53)
+    u2 = ((z2 >> np.uint64(11)).astype(np.float64) + 0.5) * (2.0 ** -53)
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+def gaussian_columns(seed: int, n: int, p: int, cols) -> np.ndarray:
+    """Columns `cols` of gaussian_block(seed, n, p) without drawing the whole block."""
+    cols = np.asarray(cols, dtype=np.int64)
+    idx = np.arange(n, dtype=np.int64)[:, None] * p + cols[None, :]
+    return gaussian_at(stream_key(seed, STREAM_U0), idx)
+
+
 # ----------------------------------------------------------------------------
 # Problems
 # ----------------------------------------------------------------------------

@@ -21,7 +21,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["metric"] == "n*p orbital-updates/s" and d["unit"] == "orbital-updates/s"
     assert d["higher_is_better"] is True and d["value"] > 0
     assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
-    assert d["config"]["workload"] == "3d_wells_64^3_p128"
+    assert d["config"]["workload"] == "3d_wells_128^3_p1024"
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     cb = d["cpu_baseline"]

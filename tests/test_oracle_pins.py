@@ -85,6 +85,11 @@ def test_splitmix64_published_vector():
     assert int(syn.splitmix64(np.uint64(0), 0, 1)[0]) == 0xE220A8397B1DCDAF
 
 
+def test_gaussian_columns_equal_the_block_columns():
+    B = syn.gaussian_block(11, 40, 9)
+    np.testing.assert_array_equal(syn.gaussian_columns(11, 40, 9, [0, 3, 8]), B[:, [0, 3, 8]])
+
+
 def test_gaussian_moments():
     g = syn.gaussian(syn.stream_key(7, syn.STREAM_U0), 0, 400000)
     assert abs(g.mean()) < 5e-3 and abs(g.std() - 1.0) < 5e-3
