@@ -105,6 +105,17 @@ typedef enum {
   OP_GEMM_FMA = 1
 } op_fp64_gemm;
 
+/* Solver of Step 1 in a context.  OP_STEP1_CG: conjugate gradients in the block precision.
+ * OP_STEP1_REFINE (FP64 contexts): iterative refinement in FP64 around an FP32 CG; every
+ * cycle forms the FP64 residual, stops when each column meets the FP64 residual test of
+ * cg_rtol, and otherwise adds the FP32 CG's solution of the scaled residual equation.
+ * OP_STEP1_AUTO: OP_STEP1_REFINE for FP64 contexts with fp64_gemm = OP_GEMM_TC, else CG. */
+typedef enum {
+  OP_STEP1_AUTO = 0,
+  OP_STEP1_CG = 1,
+  OP_STEP1_REFINE = 2
+} op_step1;
+
 typedef enum {
   OP_STOP_RESIDUAL = 0,  /* r <= tol, r = ||H U - U Theta||_F / (||H+sigma||_G sqrt(p)) */
   OP_STOP_ERR_E = 1,     /* Algorithm 1: |E(U^{n+1}) - E(U^n)| / |E(U^n)| <= tol   */
@@ -152,6 +163,7 @@ typedef struct {
                             shift take OP_FLOW_G only)                               */
   int fp64_gemm;         /* op_fp64_gemm: FP64 Gram and update of OP_FP64 contexts and
                             the set-up Cholesky-QR of every context                  */
+  int step1;             /* op_step1: the Step-1 solver of a context (G flow)        */
 } op_problem;
 
 /* Per-context statistics, filled by op_step / op_solve. */

@@ -33,7 +33,8 @@ class OpProblem(C.Structure):
                 ("hi", C.c_double * 3), ("p", C.c_int), ("sigma", C.c_double),
                 ("tau", C.c_double), ("prec", C.c_int), ("cg_rtol", C.c_double),
                 ("cg_max_iter", C.c_int), ("check_every", C.c_int), ("adapt_every", C.c_int),
-                ("cg_precond", C.c_int), ("flow", C.c_int), ("fp64_gemm", C.c_int)]
+                ("cg_precond", C.c_int), ("flow", C.c_int), ("fp64_gemm", C.c_int),
+                ("step1", C.c_int)]
 
 
 class OpStats(C.Structure):
@@ -152,11 +153,12 @@ def last_error() -> str:
 PRECONDS = {"none": 0, "jacobi": 1}
 FLOWS = {"g": 0, "l2": 1}
 FP64_GEMMS = {"tc": 0, "fma": 1}
+STEP1 = {"auto": 0, "cg": 1, "refine": 2}
 
 
 def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol=0.0,
                  cg_max_iter=0, check_every=0, adapt_every=0, precond="jacobi",
-                 flow="g", fp64_gemm="tc") -> OpProblem:
+                 flow="g", fp64_gemm="tc", step1="auto") -> OpProblem:
     pb = OpProblem()
     dim = len(shape)
     pb.dim = dim
@@ -175,6 +177,7 @@ def make_problem(shape, lo, hi, p, *, prec="fp64", sigma=None, tau=None, cg_rtol
     pb.cg_precond = PRECONDS[precond] if isinstance(precond, str) else int(precond)
     pb.flow = FLOWS[flow] if isinstance(flow, str) else int(flow)
     pb.fp64_gemm = FP64_GEMMS[fp64_gemm] if isinstance(fp64_gemm, str) else int(fp64_gemm)
+    pb.step1 = STEP1[step1] if isinstance(step1, str) else int(step1)
     return pb
 
 
@@ -206,6 +209,7 @@ class Solver:
     gradient flow W = -(H + sigma) U through the exact Cayley step; CFL-limited).
     fp64_gemm: "tc" (FP64 Gram and update as exact digit products on the tensor cores) or
     "fma" (FP64 FMA) for FP64 contexts and every context's set-up (op_fp64_gemm).
+    step1: "auto", "cg" or "refine" (FP64 iterative refinement around an FP32 CG; op_step1).
     U0 None: the raw initial block is drawn on the device from `seed` (op_init_seeded,
     the stream of synthetic.gaussian_block(seed, n, p)).
     The remaining keywords are the op_problem fields of the same names.
@@ -213,11 +217,11 @@ class Solver:
 
     def __init__(self, shape, lo, hi, V, U0, p, *, prec="fp64", sigma=None, tau=None,
                  cg_rtol=0.0, cg_max_iter=0, check_every=0, adapt_every=0, precond="jacobi",
-                 flow="g", stream=None, device=False, seed=0, fp64_gemm="tc"):
+                 flow="g", stream=None, device=False, seed=0, fp64_gemm="tc", step1="auto"):
         self.pb = make_problem(shape, lo, hi, p, prec=prec, sigma=sigma, tau=tau,
                                cg_rtol=cg_rtol, cg_max_iter=cg_max_iter, check_every=check_every,
                                adapt_every=adapt_every, precond=precond, flow=flow,
-                               fp64_gemm=fp64_gemm)
+                               fp64_gemm=fp64_gemm, step1=step1)
         self.n = int(np.prod(shape))
         self.p = int(p)
         self._ctx = C.c_void_p()

@@ -147,6 +147,14 @@ op_status check_problem(const op_problem *pb) {
     set_error("unsupported flow %d", pb->flow);
     return OP_ERR_ARG;
   }
+  if (pb->step1 != OP_STEP1_AUTO && pb->step1 != OP_STEP1_CG && pb->step1 != OP_STEP1_REFINE) {
+    set_error("unsupported step1 solver %d", pb->step1);
+    return OP_ERR_ARG;
+  }
+  if (pb->step1 == OP_STEP1_REFINE && pb->prec != OP_FP64) {
+    set_error("the mixed-precision Step 1 refines FP64 blocks (prec %d)", pb->prec);
+    return OP_ERR_ARG;
+  }
   if (pb->fp64_gemm != OP_GEMM_TC && pb->fp64_gemm != OP_GEMM_FMA) {
     set_error("unsupported fp64_gemm %d", pb->fp64_gemm);
     return OP_ERR_ARG;
@@ -228,6 +236,24 @@ op_status update_fp64(op_ctx *c, const double *U, const double *W, const double 
   return update<double>(c->n, c->ld, U, W, KU, KW, Unew, c->st);
 }
 
+// Step 1 for the context: CG in the block precision, or (FP64 contexts) iterative
+// refinement around an FP32 CG.
+template <typename T>
+op_status solve_step1(op_ctx *c, const T *U, T *W, double rtol, int max_iter, int *iters) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (c->refine) {
+      c->cgw32.Q = c->U2;  // the update's output block is free during Step 1
+      int cycles = 0;
+      return cg_refine(c->g, (const double *)c->Vt, c->Vt32, c->sigma, U, W, c->p, c->ld, rtol,
+                       max_iter, c->cgw, c->cgw32, (float *)c->cgw.P,
+                       (float *)c->cgw.P + (size_t)c->n * c->ld, c->ref_scale, iters, &cycles,
+                       c->st);
+    }
+  }
+  return cg_solve<T>(c->g, (const T *)c->Vt, c->sigma, U, W, c->p, c->ld, rtol, max_iter, c->cgw,
+                     iters, c->st);
+}
+
 template <typename T> op_status step_impl(op_ctx *c) {
   NvtxRange step_range("opevo step");
   int iters = 0;
@@ -241,8 +267,8 @@ template <typename T> op_status step_impl(op_ctx *c) {
   } else {
     // Step 1: W = (H + sigma)^-1 U, warm-started from the previous W
     NvtxRange r("step 1: CG");
-    OP_TRY(cg_solve<T>(c->g, (const T *)c->Vt, c->sigma, (const T *)c->U, (T *)c->W, c->p,
-                       c->ld, cg_rtol_for(c), cg_max_iter(c), c->cgw, &iters, c->st));
+    OP_TRY(solve_step1<T>(c, (const T *)c->U, (T *)c->W, cg_rtol_for(c), cg_max_iter(c),
+                          &iters));
   }
   NvtxRange r_rest("Grams, core, update, energy");
   // inner matrices <W,U>, <W,W>, <U,U>
@@ -259,7 +285,8 @@ template <typename T> op_status step_impl(op_ctx *c) {
                           (T *)c->KW_t, c->cayley_ws, c->core_ws, c->st));
   else
     OP_TRY(core<T>(c->p, c->ld, c->tau, c->C, c->S, c->KU, c->KW, (T *)c->KU_t, (T *)c->KW_t,
-                   c->core_ws, c->st));
+                   c->core_ws, c->st, c->tc_ws ? c->tc_ws : c->core_tc_ws,
+                   c->tc_ws ? c->tc_bytes : c->core_tc_bytes, c->dev_err));
   prof_end(&c->prof, c->st);
   // Step 4
   prof_begin(&c->prof, PK_UPDATE, c->st);
@@ -358,8 +385,7 @@ template <typename T> op_status eig_impl(op_ctx *c, double *lam, int kind) {
   } else {
     int iters = 0;
     const double tight = c->prec == OP_FP64 ? 1e-13 : 1e-6;
-    OP_TRY(cg_solve<T>(c->g, (const T *)c->Vt, c->sigma, (const T *)c->U, (T *)c->W, c->p, c->ld,
-                       tight, 20000, c->cgw, &iters, c->st));
+    OP_TRY(solve_step1<T>(c, (const T *)c->U, (T *)c->W, tight, 20000, &iters));
     OP_TRY(gram_any<T>(c, (const T *)c->U, (const T *)c->W, c->Th, nullptr, nullptr));
     OP_TRY(sym_eigvals(c->p, c->ld, c->Th, c->eig_work, c->eig_work + (size_t)c->p * c->p,
                        c->st));
@@ -532,6 +558,35 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
   cg_carve(c->cg_ws, n, ld, sizeof(T), &c->cgw);
   c->cgw.prof = &c->prof;
   c->cgw.jacobi = c->pb.cg_precond == OP_PRECOND_JACOBI;
+  c->refine = sizeof(T) == 8 && c->pb.flow == OP_FLOW_G &&
+              (c->pb.step1 == OP_STEP1_REFINE ||
+               (c->pb.step1 == OP_STEP1_AUTO && c->pb.fp64_gemm == OP_GEMM_TC));
+  c->Vt32 = nullptr;
+  c->ref_scale = nullptr;
+  if (c->refine) {
+    // the FP32 CG's blocks: R, P in the FP64 block Q, its direction buffer Q in U2 (set per
+    // call); the rhs and solution in the FP64 block P; its reductions of its own
+    const size_t b32 = (size_t)n * ld * sizeof(float);
+    memset(&c->cgw32, 0, sizeof(c->cgw32));
+    c->cgw32.R = c->cgw.Q;
+    c->cgw32.P = (char *)c->cgw.Q + b32;
+    c->cgw32.Q = nullptr;
+    c->cgw32.max_blocks = c->cgw.max_blocks;
+    const size_t pb = (part_bytes(ld) + 255) / 256 * 256;
+    const size_t sb = ((size_t)6 * ld * sizeof(double) + 255) / 256 * 256;
+    const size_t ab = ((size_t)ld * sizeof(int) + 255) / 256 * 256;
+    OP_TRY(dev_alloc(c, &p, pb + sb + ab + 256 + (size_t)ld * sizeof(double)));
+    c->cgw32.part = (double *)p;
+    c->cgw32.state = (double *)((char *)p + pb);
+    c->cgw32.active = (int *)((char *)p + pb + sb);
+    c->cgw32.ctl = (int *)((char *)p + pb + sb + ab);
+    c->ref_scale = (double *)((char *)p + pb + sb + ab + 256);
+    c->cgw32.jacobi = c->cgw.jacobi;
+    c->cgw32.prof = &c->prof;
+    c->cgw32.expect_iters = 0;
+    OP_TRY(dev_alloc(c, &p, (size_t)n * sizeof(float)));
+    c->Vt32 = (float *)p;
+  }
   c->gram_bytes = gram_workspace_bytes(n, ld, sizeof(T));
   if (sizeof(T) == 4) {
     const size_t tcb = gram_tc_workspace_bytes(n, ld);
@@ -547,6 +602,12 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
     c->tc_bytes = fp64tc_workspace_bytes(n, ld);
     OP_TRY(dev_alloc(c, &c->tc_ws, c->tc_bytes));
   }
+  c->core_tc_ws = nullptr;
+  c->core_tc_bytes = 0;
+  if (!c->tc_ws && c->p > 128 && c->pb.fp64_gemm == OP_GEMM_TC) {
+    c->core_tc_bytes = fp64tc_workspace_bytes(c->p, ld);
+    OP_TRY(dev_alloc(c, &c->core_tc_ws, c->core_tc_bytes));
+  }
   OP_TRY(dev_alloc(c, &p, 256));
   c->dev_err = (int *)p;
   OP_CUDA(cudaMemsetAsync(c->dev_err, 0, 256, c->st));
@@ -560,6 +621,7 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
   OP_CUDA(cudaMallocHost((void **)&c->hsc, 64 * sizeof(double)));
   OP_CUDA(cudaMallocHost((void **)&c->hpin_int, 16 * sizeof(int)));
   c->cgw.host_ctl = c->hpin_int + 4;
+  c->cgw32.host_ctl = c->hpin_int + 8;
   OP_CUDA(cudaMemsetAsync(c->W, 0, blk, c->st));
   OP_CUDA(cudaMemsetAsync(c->U2, 0, blk, c->st));
 
@@ -570,6 +632,7 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
                           n * sizeof(double),
                           device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
   OP_TRY(launch_convert<T>((int)n, (const double *)V64, (T *)c->Vt, c->st));
+  if (c->Vt32) OP_TRY(launch_convert<float>((int)n, (const double *)V64, c->Vt32, c->st));
   // raw U0 (n x p FP64) on the device (a device U0 is read in place)
   void *U0d = nullptr;
   if (!device) {

@@ -28,6 +28,14 @@ struct op_ctx {
   void *cayley_ws;       // OP_FLOW_L2: the 2p x 3p system of the exact Cayley step
   void *tc_ws;           // FP64 contexts with fp64_gemm = OP_GEMM_TC: digit planes etc.
   size_t tc_bytes;
+  void *core_tc_ws;      // p > 128 with OP_GEMM_TC: the core's Newton-Schulz products (the
+  size_t core_tc_bytes;  // FP64 contexts use tc_ws)
+  // FP64 contexts with the mixed-precision Step 1: V in FP32, the FP32 CG's scratch (its
+  // blocks alias the FP64 CG blocks Q and U2, its rhs and solution the FP64 block P)
+  bool refine;
+  float *Vt32;
+  CGWork cgw32;
+  double *ref_scale;
   size_t gram_bytes;
   CGWork cgw;
   Prof prof;

@@ -14,6 +14,8 @@
 
 #include <type_traits>
 
+#include <string.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -84,7 +86,11 @@ __global__ void k_small_gemm(int p, int ld, double alpha, const double *__restri
 // for the Step-2 matrix, whose symmetric part is >= I (Lemma 3.1), so every
 // leading block is nonsingular.  status <- 1 on a zero or non-finite pivot.
 __global__ void __launch_bounds__(1024) k_lu(int p, int ld, const double *__restrict__ M,
-                                             double *__restrict__ LU, int *status) {
+                                             double *__restrict__ LU, int *status,
+                                             const double *gate = nullptr,
+                                             double gate_tol = 0.0) {
+  // gate (optional): skip when a faster inverse already met its residual test
+  if (gate && *gate <= gate_tol) return;
   __shared__ double piv;
   __shared__ int bad;
   const int t = threadIdx.x, nt = blockDim.x;
@@ -166,10 +172,12 @@ __global__ void __launch_bounds__(1024) k_chol(int p, int ld, const double *__re
 //   mode 1: F = L^T    (column j of R^-1 for R = L^T)
 //   mode 2: F = L U    (unit-lower L below the diagonal, U on and above; k_lu)
 __global__ void k_tri_cols(int p, int ld, const double *__restrict__ L, int mode,
-                           double *__restrict__ out, const int *__restrict__ status) {
+                           double *__restrict__ out, const int *__restrict__ status,
+                           const double *gate = nullptr, double gate_tol = 0.0) {
   extern __shared__ double y[];  // p values
   const int j = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
   if (j >= ld) return;
+  if (gate && *gate <= gate_tol) return;  // a faster inverse already met its residual test
   if (*status || j >= p) {
     for (int i = t; i < ld; i += nt) out[(long long)i * ld + j] = (i == j && j < p) ? 1.0 : 0.0;
     return;
@@ -713,6 +721,68 @@ __global__ void k_cayley_coeff(int p, int ld, double tau, const double *__restri
   }
 }
 
+// ---- Newton-Schulz inverse of the Step-2 matrix ---------------------------------------
+// X0 = alpha I_p with alpha = 2 / (1 + ||M||_inf): for M whose symmetric part is >= I
+// (Lemma 3.1) and whose skew part is small, the spectrum of I - alpha M lies inside the
+// unit disc, and X <- X (2I - M X) squares the residual I - M X every step.  One CTA.
+__global__ void __launch_bounds__(1024) k_ns_seed(int p, int ld, const double *__restrict__ M,
+                                                  double *__restrict__ X) {
+  __shared__ double sh[32];
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    double r = 0.0;
+    for (int j = 0; j < p; ++j) r += fabs(M[(long long)i * ld + j]);
+    mx = fmax(mx, r);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) sh[0] = v;
+  }
+  __syncthreads();
+  const double alpha = 2.0 / (1.0 + sh[0]);
+  for (long long e = threadIdx.x; e < (long long)ld * ld; e += blockDim.x) {
+    const int i = (int)(e / ld), j = (int)(e % ld);
+    X[e] = (i == j && i < p) ? alpha : 0.0;
+  }
+}
+
+// E = 2 I - T on the p x p block (zero elsewhere), *err_bits = max |(I - T)_ij| (the bits of a
+// non-negative double order like the double: atomicMax on them is a max).
+__global__ void k_ns_resid(int p, int ld, const double *__restrict__ T, double *__restrict__ E,
+                           unsigned long long *err_bits) {
+  double mx = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)ld * ld;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ld), j = (int)(e % ld);
+    double v = 0.0;
+    if (i < p && j < p) {
+      const double r = (i == j ? 1.0 : 0.0) - T[e];
+      mx = fmax(mx, fabs(r));
+      v = (i == j ? 1.0 : 0.0) + r;
+    }
+    E[e] = v;
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0)
+    atomicMax(err_bits, (unsigned long long)__double_as_longlong(mx));
+}
+
+// *err_bits = max |(I - M X)_ij| over the p x p block (p <= 128 path; R = I - M X given).
+__global__ void k_maxabs(int p, int ld, const double *__restrict__ R,
+                         unsigned long long *err_bits) {
+  double mx = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)p * p;
+       e += (long long)gridDim.x * blockDim.x)
+    mx = fmax(mx, fabs(R[(e / p) * ld + e % p]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0)
+    atomicMax(err_bits, (unsigned long long)__double_as_longlong(mx));
+}
+
 }  // namespace
 
 size_t cayley_workspace_bytes(int p) { return (size_t)6 * p * p * sizeof(double); }
@@ -741,17 +811,29 @@ op_status core_cayley(int p, int ld, double tau, const double *C, const double *
 
 size_t core_workspace_bytes(int p, int ld) {
   (void)p;
-  return 256 + 4 * (size_t)ld * ld * sizeof(double);
+  return 256 + 5 * (size_t)ld * ld * sizeof(double);
 }
+
+static double __longlong_as_double_host(unsigned long long b) {
+  double d;
+  memcpy(&d, &b, sizeof(d));
+  return d;
+}
+
+// Residual threshold of the fast inverses: max |I - M B| above this falls back to LU.
+constexpr double kInvTol = 1e-12;
 
 template <typename T>
 op_status core(int p, int ld, double tau, const double *C, const double *S, double *KU,
-               double *KW, T *KU_t, T *KW_t, void *ws, cudaStream_t st) {
+               double *KW, T *KU_t, T *KW_t, void *ws, cudaStream_t st, void *tcws, size_t tcb,
+               int *err) {
   int *status = (int *)ws;
+  unsigned long long *err_bits = (unsigned long long *)((char *)ws + 64);
   double *M = (double *)((char *)ws + 256);
   double *L = M + (size_t)ld * ld;
   double *B = L + (size_t)ld * ld;
   double *R = B + (size_t)ld * ld;
+  double *E = R + (size_t)ld * ld;
   const dim3 tb(kT, kT), tg((ld + kT - 1) / kT, (ld + kT - 1) / kT);
   const double q = 0.25 * tau * tau;
   OP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
@@ -782,12 +864,62 @@ op_status core(int p, int ld, double tau, const double *C, const double *S, doub
     }
     if (X != B)
       OP_CUDA(cudaMemcpyAsync(B, X, (size_t)ld * ld * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // guard: max |I - M B| > kInvTol (a badly conditioned M) replaces B by the FP64 LU
+    // inverse; both fallback kernels return at once when the residual test holds
+    k_small_gemm<double><<<tg, tb, 0, st>>>(p, ld, -1.0, M, 0, B, 0, 0.0, (const double *)nullptr,
+                                            0.0, 0.0, (const double *)nullptr, 1.0, R,
+                                            (double *)nullptr, (const int *)nullptr);
+    count_launch();
+    OP_CUDA(cudaMemsetAsync(err_bits, 0, sizeof(unsigned long long), st));
+    k_maxabs<<<8, 256, 0, st>>>(p, ld, R, err_bits);
+    count_launch();
+    // FP64 contexts refine twice (residual ~1e-15); FP32 contexts once (their blocks carry
+    // 6e-8 anyway): fall back beyond 1e-12 and 1e-6 respectively
+    const double tol = std::is_same<T, double>::value ? kInvTol : 1e-6;
+    k_lu<<<1, 1024, 0, st>>>(p, ld, M, L, status, (const double *)err_bits, tol);
+    count_launch();
+    k_tri_cols<<<ld, 256, p * sizeof(double), st>>>(p, ld, L, 2, B, status,
+                                                   (const double *)err_bits, tol);
+    count_launch();
   } else {
-    // larger cores: FP64 LU on one CTA, then the inverse by substitution
-    k_lu<<<1, 1024, 0, st>>>(p, ld, M, L, status);
-    count_launch();
-    k_tri_cols<<<ld, 256, p * sizeof(double), st>>>(p, ld, L, 2, B, status);
-    count_launch();
+    bool done = false;
+    if (tcws) {
+      // Newton-Schulz X <- X (2I - M X) with the tensor-core FP64 products, converged when
+      // max |I - M X| <= 1e-9 before the last step (after it the residual is ~ p 1e-18)
+      k_ns_seed<<<1, 1024, 0, st>>>(p, ld, M, L);
+      count_launch();
+      // the products write rows < p only: rows p..ld-1 of both iterates stay zero
+      OP_CUDA(cudaMemsetAsync(B, 0, (size_t)ld * ld * sizeof(double), st));
+      double *X = L, *Xn = B;
+      for (int it = 0; it < 60 && !done; ++it) {
+        OP_TRY(update_fp64tc(p, ld, M, nullptr, X, nullptr, false, R, tcws, tcb, err, st));
+        OP_CUDA(cudaMemsetAsync(err_bits, 0, sizeof(unsigned long long), st));
+        k_ns_resid<<<(ld * ld + 255) / 256 < 4096 ? (ld * ld + 255) / 256 : 4096, 256, 0, st>>>(
+            p, ld, R, E, err_bits);
+        count_launch();
+        OP_LAUNCH("k_ns_resid");
+        OP_TRY(update_fp64tc(p, ld, X, nullptr, E, nullptr, false, Xn, tcws, tcb, err, st));
+        unsigned long long h = 0;
+        OP_CUDA(cudaMemcpyAsync(&h, err_bits, sizeof(h), cudaMemcpyDeviceToHost, st));
+        OP_CUDA(cudaStreamSynchronize(st));
+        const double r = __longlong_as_double_host(h);
+        double *tmp = X;
+        X = Xn;
+        Xn = tmp;
+        if (r <= 1e-9) done = true;
+        else if (!(r < 1e3) || (it >= 12 && r > 0.5)) break;  // diverging or stalled: LU
+      }
+      if (done && X != B)
+        OP_CUDA(cudaMemcpyAsync(B, X, (size_t)ld * ld * sizeof(double), cudaMemcpyDeviceToDevice,
+                                st));
+    }
+    if (!done) {
+      // FP64 LU on one CTA, then the inverse by substitution
+      k_lu<<<1, 1024, 0, st>>>(p, ld, M, L, status);
+      count_launch();
+      k_tri_cols<<<ld, 256, p * sizeof(double), st>>>(p, ld, L, 2, B, status);
+      count_launch();
+    }
   }
   // Step 3 folded into Step 4: KU = I - tau A = 2B - I - tau C^T B; KW = tau B
   k_small_gemm<T><<<tg, tb, 0, st>>>(p, ld, -tau, C, 1, B, 0, 2.0, B, 0.0, 0.0,
@@ -870,9 +1002,11 @@ template op_status launch_resid_coeff<float>(int, int, const double *, float *, 
 template op_status launch_resid_coeff<double>(int, int, const double *, double *, double *,
                                               cudaStream_t);
 template op_status core<float>(int, int, double, const double *, const double *, double *,
-                               double *, float *, float *, void *, cudaStream_t);
+                               double *, float *, float *, void *, cudaStream_t, void *, size_t,
+                               int *);
 template op_status core<double>(int, int, double, const double *, const double *, double *,
-                                double *, double *, double *, void *, cudaStream_t);
+                                double *, double *, double *, void *, cudaStream_t, void *,
+                                size_t, int *);
 template op_status core_cayley<float>(int, int, double, const double *, const double *,
                                       const double *, double *, double *, float *, float *,
                                       void *, void *, cudaStream_t);

@@ -20,6 +20,7 @@ enum ProfKind {
   PK_UPDATE,
   PK_ENERGY,
   PK_RESIDUAL,
+  PK_REFINE,   // FP64 residual, scaling and correction of the mixed-precision Step 1
   PK_COUNT
 };
 struct Prof {
@@ -144,6 +145,18 @@ template <typename T>
 op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, int p, int ld,
                    double rtol, int max_iter, CGWork &w, int *iters, cudaStream_t st);
 
+// Step 1 in FP64 by iterative refinement around an FP32 CG: each cycle forms the FP64
+// residual R = U - (H + sigma) W and its column norms (w64: FP64 scratch, its R block and
+// reductions), stops when every column meets ||r_j|| <= rtol ||u_j||, else solves
+// (H + sigma) d = r_j / ||r_j|| by the FP32 CG of w32 (V in FP32: Vt32; rhs r32, solution
+// d32: n x ld FP32 blocks) to a relative tolerance that the cycle needs, and adds
+// ||r_j|| d_j to W in FP64.  scale: ld doubles of device scratch.  *iters: FP32 CG
+// iterations of all cycles; *cycles: FP64 residual evaluations.
+op_status cg_refine(const Geom &g, const double *Vt, const float *Vt32, double sigma,
+                    const double *U, double *W, int p, int ld, double rtol, int max_iter,
+                    CGWork &w64, CGWork &w32, float *r32, float *d32, double *scale, int *iters,
+                    int *cycles, cudaStream_t st);
+
 // FP32 CG direction kernel on 3-D grids with TMA-staged stencil planes (stencil_tma.cu).
 struct CgTmaGeom {
   int nx, ny, nz, ld;
@@ -208,9 +221,13 @@ op_status gram_tc_fixed_scratch(long long n, int p, int ld, const float *U, cons
 // ---- dense FP64 p x p algebra (dense.cu) --------------------------------------
 size_t core_workspace_bytes(int p, int ld);
 // ws layout begins with an int status word (0 ok, 1 not SPD).
+// tcws (may be null): an fp64tc scratch of fp64tc_workspace_bytes(p, ld) or more; with it,
+// p > 128 inverts the Step-2 matrix by Newton-Schulz on the tensor-core FP64 products
+// (host-checked convergence, FP64 LU when it does not converge), else by FP64 LU.
 template <typename T>
 op_status core(int p, int ld, double tau, const double *C, const double *S, double *KU,
-               double *KW, T *KU_t, T *KW_t, void *ws, cudaStream_t st);
+               double *KW, T *KU_t, T *KW_t, void *ws, cudaStream_t st, void *tcws = nullptr,
+               size_t tcb = 0, int *err = nullptr);
 // The midpoint step as an exact Cayley transform for any <U, U> (2p x 2p solve with the
 // joint Gram of [U W], Gauss-Jordan with partial pivoting): KU, KW (FP64 and T copies)
 // with U+ = U KU + W KW.  aug: cayley_workspace_bytes(p) of device scratch; status word

@@ -16,7 +16,9 @@
 // number of still-active columns; every kernel of an iteration returns at once
 // when the previous iteration left no active column, so the host can queue
 // several iterations between convergence checks.
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -65,16 +67,19 @@ __device__ __forceinline__ Pack<T> stencil_at(const Geom &g, const T *__restrict
   const long long base = i * (long long)ld + col;
   const Coord c = coord_of(g, i);
   Pack<T> xc = Pack<T>::load(X + base);
-  Pack<T> sx = Pack<T>::zero(), sy = Pack<T>::zero(), sz = Pack<T>::zero();
-  if (c.ix > 0) add_pack(sx, Pack<T>::load(X + base - ld));
-  if (c.ix < g.nx - 1) add_pack(sx, Pack<T>::load(X + base + ld));
+  // each axis: one addition of the two neighbours (a missing neighbour reads as zero),
+  // so the apply costs 3 additions and 4 multiply-adds per element
+  const Pack<T> z = Pack<T>::zero();
+  Pack<T> sx = c.ix > 0 ? Pack<T>::load(X + base - ld) : z;
+  add_pack(sx, c.ix < g.nx - 1 ? Pack<T>::load(X + base + ld) : z);
   const long long sty = (long long)g.nx * ld;
-  if (c.iy > 0) add_pack(sy, Pack<T>::load(X + base - sty));
-  if (c.iy < g.ny - 1) add_pack(sy, Pack<T>::load(X + base + sty));
+  Pack<T> sy = c.iy > 0 ? Pack<T>::load(X + base - sty) : z;
+  add_pack(sy, c.iy < g.ny - 1 ? Pack<T>::load(X + base + sty) : z);
+  Pack<T> sz = z;
   if (g.dim == 3) {
     const long long stz = (long long)g.nx * g.ny * ld;
-    if (c.iz > 0) add_pack(sz, Pack<T>::load(X + base - stz));
-    if (c.iz < g.nz - 1) add_pack(sz, Pack<T>::load(X + base + stz));
+    sz = c.iz > 0 ? Pack<T>::load(X + base - stz) : z;
+    add_pack(sz, c.iz < g.nz - 1 ? Pack<T>::load(X + base + stz) : z);
   }
   if (center) *center = xc;
   return combine(g, __ldg(Vt + i) + shift, xc, sx, sy, sz);
@@ -764,6 +769,119 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
   return OP_OK;
 }
 
+// ---- mixed-precision Step 1 (FP64 iterative refinement around an FP32 CG) -------------
+namespace {
+
+// scale[j] = ||r_j|| for the active columns (0 otherwise), from the init finaliser's state.
+__global__ void k_ref_scale(int ld, const double *__restrict__ state, const int *__restrict__ active,
+                            double *__restrict__ scale) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < ld) scale[j] = active[j] ? sqrt(state[j]) : 0.0;
+}
+
+// r32 = R / scale (column-wise; zero for inactive columns); four elements per thread.
+__global__ void k_ref_rhs(long long total, int ld, const double *__restrict__ R,
+                          const double *__restrict__ scale, float *__restrict__ r32) {
+  for (long long e = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x); e < total;
+       e += 4 * (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % ld);
+    const double2 a = *reinterpret_cast<const double2 *>(R + e);
+    const double2 b = *reinterpret_cast<const double2 *>(R + e + 2);
+    float4 o;
+    const double s0 = scale[j], s1 = scale[j + 1], s2 = scale[j + 2], s3 = scale[j + 3];
+    o.x = s0 > 0.0 ? (float)(a.x / s0) : 0.f;
+    o.y = s1 > 0.0 ? (float)(a.y / s1) : 0.f;
+    o.z = s2 > 0.0 ? (float)(b.x / s2) : 0.f;
+    o.w = s3 > 0.0 ? (float)(b.y / s3) : 0.f;
+    *reinterpret_cast<float4 *>(r32 + e) = o;
+  }
+}
+
+// W += scale_j d_j in FP64.
+__global__ void k_ref_correct(long long total, int ld, const float *__restrict__ d32,
+                              const double *__restrict__ scale, double *__restrict__ W) {
+  for (long long e = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x); e < total;
+       e += 4 * (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % ld);
+    const float4 d = *reinterpret_cast<const float4 *>(d32 + e);
+    double2 a = *reinterpret_cast<double2 *>(W + e);
+    double2 b = *reinterpret_cast<double2 *>(W + e + 2);
+    a.x += scale[j] * (double)d.x;
+    a.y += scale[j + 1] * (double)d.y;
+    b.x += scale[j + 2] * (double)d.z;
+    b.y += scale[j + 3] * (double)d.w;
+    *reinterpret_cast<double2 *>(W + e) = a;
+    *reinterpret_cast<double2 *>(W + e + 2) = b;
+  }
+}
+
+}  // namespace
+
+op_status cg_refine(const Geom &g, const double *Vt, const float *Vt32, double sigma,
+                    const double *U, double *W, int p, int ld, double rtol, int max_iter,
+                    CGWork &w64, CGWork &w32, float *r32, float *d32, double *scale, int *iters,
+                    int *cycles, cudaStream_t st) {
+  RowShape s = row_shape(ld, Pack<double>::N);
+  const int nb = grid_blocks(g.n, s.rows);
+  const dim3 grid(nb, s.gy);
+  const int fb = warp_blocks(ld);
+  const double sg = g.cdiag + sigma;
+  const long long total = g.n * ld;
+  const int eb = (int)std::min<long long>((total / 4 + 255) / 256, (long long)num_sms() * 32);
+  double *R = (double *)w64.R;
+  std::vector<double> hs(2 * (size_t)ld);
+  int inner = 0, cyc = 0;
+  *iters = 0;
+  *cycles = 0;
+  for (; cyc < 12; ++cyc) {
+    prof_begin(w64.prof, PK_REFINE, st);
+    // R = U - (H + sigma) W and the column norms; active columns: ||r_j|| > rtol ||u_j||
+    k_cg_init<double, false, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, nullptr, ld,
+                                                             w64.part, w64.ctl);
+    count_launch();
+    k_cg_fin_init<<<fb, 256, 0, st>>>(w64.part, nb, 2, ld, p, rtol * rtol, w64.state, w64.active,
+                                      w64.ctl);
+    count_launch();
+    prof_end(w64.prof, st);
+    OP_LAUNCH("cg_refine residual");
+    OP_CUDA(cudaMemcpyAsync(w64.host_ctl, w64.ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    OP_CUDA(cudaMemcpyAsync(hs.data(), w64.state, (size_t)ld * sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+    OP_CUDA(cudaMemcpyAsync(hs.data() + ld, w64.state + 4 * (size_t)ld, (size_t)ld * sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+    OP_CUDA(cudaStreamSynchronize(st));
+    prof_harvest(w64.prof);
+    if (w64.host_ctl[1] == 0 || inner >= max_iter) break;
+    // the inner tolerance the worst active column needs, with a margin, not below what an
+    // FP32 solve reaches
+    double rho = 0.0;
+    for (int j = 0; j < p; ++j)
+      if (hs[ld + j] > 0.0 && hs[j] > rtol * rtol * hs[ld + j])
+        rho = std::max(rho, sqrt(hs[j] / hs[ld + j]));
+    double eta = rho > 0.0 ? 0.3 * rtol / rho : 0.5;
+    eta = std::min(0.5, std::max(eta, 2e-6));
+    prof_begin(w64.prof, PK_REFINE, st);
+    k_ref_scale<<<(ld + 255) / 256, 256, 0, st>>>(ld, w64.state, w64.active, scale);
+    count_launch();
+    k_ref_rhs<<<eb, 256, 0, st>>>(total, ld, R, scale, r32);
+    count_launch();
+    OP_CUDA(cudaMemsetAsync(d32, 0, (size_t)total * sizeof(float), st));
+    prof_end(w64.prof, st);
+    OP_LAUNCH("cg_refine rhs");
+    int it = 0;
+    OP_TRY(cg_solve<float>(g, Vt32, sigma, r32, d32, p, ld, eta, max_iter - inner, w32, &it, st));
+    inner += it;
+    prof_begin(w64.prof, PK_REFINE, st);
+    k_ref_correct<<<eb, 256, 0, st>>>(total, ld, d32, scale, W);
+    count_launch();
+    prof_end(w64.prof, st);
+    OP_LAUNCH("cg_refine correction");
+  }
+  *iters = inner;
+  *cycles = cyc + 1;
+  return OP_OK;
+}
+
 template <typename T>
 op_status launch_pad_copy(long long n, int p, int ld, const double *src, T *dst, cudaStream_t st) {
   k_pad_copy<T><<<num_sms() * 8, 256, 0, st>>>(n, p, ld, src, dst);
@@ -1112,7 +1230,7 @@ op_status launch_b_energy(const BatchProb *B, const RowItem *items, int nitems, 
 const char *prof_name(int kind) {
   static const char *names[PK_COUNT] = {"cg_init", "cg_apply", "cg_axpy", "cg_dir",
                                         "cg_finalize", "gram", "core", "update", "energy",
-                                        "residual"};
+                                        "residual", "cg_refine"};
   return (kind >= 0 && kind < PK_COUNT) ? names[kind] : "";
 }
 
