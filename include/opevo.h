@@ -92,14 +92,16 @@ typedef enum {
 } op_flow;
 
 /* How FP64 contexts form their FP64 products of n x p blocks (the Grams of §2.1 and the
- * Step-4 update, also the set-up Cholesky-QR of every mode).  OP_GEMM_TC: every FP64
- * operand is written exactly as seven balanced base-256 integer digits (one power-of-two
- * exponent per row of the contraction), the 28 digit products with digit index sum <= 6
- * run on the tensor cores (tcgen05 kind::f16) with exact integer level sums over runs of
- * 256 terms, added in int64 and scaled back in FP64: each product term is exact up to
- * 2^-53.4 |a| |b| and the result carries an FP64 rounding error relative to the largest
- * |a| |b| of the run (the error class of an FP64 dot product).  OP_GEMM_FMA: FP64 FMA on
- * the FP64 pipe (about 2 per clock per SM on GB300). */
+ * Step-4 update, also the set-up Cholesky-QR of every mode and, for p > 128, the
+ * Newton-Schulz inverse of the Step-2 matrix).  OP_GEMM_TC: every FP64 operand is written
+ * exactly as balanced base-256 integer digits (one power-of-two exponent per row of the
+ * contraction; seven digits for the Gram, eight for the update), the digit products with
+ * digit index sum below the digit count (28 or 36) run on the tensor cores (tcgen05
+ * kind::f16) with exact integer level sums over runs of 256 terms, added in int64 and
+ * scaled back in FP64: each product term is exact up to 2^-53.4 (Gram) or 2^-61.4
+ * (update) of |a| |b| for the largest |a|, |b| of their rows, so the result carries an
+ * error of the class of an FP64 dot product.  OP_GEMM_FMA: FP64 FMA on the FP64 pipe
+ * (about 2 per clock per SM on GB300). */
 typedef enum {
   OP_GEMM_TC = 0,
   OP_GEMM_FMA = 1

@@ -4,37 +4,43 @@
 //
 // GB300 runs FP64 FMA at about 2 per clock per SM, so an FP64 Gram or update of
 // p ~ 10^3 orbitals takes seconds there.  Here every FP64 operand is written exactly as
-// seven integer digits and the products of digits run on tcgen05 (kind::f16, BF16
-// operands, FP32 accumulation in TMEM), in exact integer arithmetic:
+// ND integer digits and the products of digits run on tcgen05 (kind::f16, BF16 operands,
+// FP32 accumulation in TMEM), in exact integer arithmetic:
 //
 //   Digits.  A row r of an operand (the K-vector an output entry contracts over) gets an
-//   exponent e_r with max_k |a_rk| < 2^e_r.  X = round(a 2^(55 - e_r)) is an integer with
-//   |X| <= 2^55, written in balanced base 256: X = sum_{s=0..6} d_s 2^(8 (6 - s)),
-//   d_1..d_6 in [-128, 127], d_0 in [-128, 128] (every digit is a BF16 value exactly).
-//   The digits keep all 55 bits of X; rounding a to X costs at most 2^-56 max|a_r.|.
+//   exponent e_r with max_k |a_rk| < 2^e_r.  X = round(a 2^(B - e_r)), B = 8 ND - 1, is an
+//   integer with |X| < 2^B, written in balanced base 256: X = sum_{s<ND} d_s 2^(8(ND-1-s)),
+//   d_1.. in [-128, 127], d_0 in [-128, 128] (every digit is a BF16 value exactly).  The
+//   digits keep all B bits of X; rounding a to X costs at most 2^-(B+1) max|a_r.|.
+//   ND = 7 (B = 55) for the Gram, whose rows are orbitals over the grid (their maxima are
+//   close to their typical values); ND = 8 (B = 63) for the update, whose rows are the 2p
+//   values of [U W] at one grid point, where the largest can exceed the typical one by
+//   orders of magnitude (localised orbitals): the eighth digit keeps the update's error
+//   below that of FP64 FMA relative to the typical term.
 //
-//   Products.  sum_k X_ak X_bk = sum_{s,t} (sum_k d_s d'_t) 2^(8 (12 - s - t)); the pairs
-//   with s + t <= 6 (28 MMAs per K step) are kept, summed per level l = s + t in one TMEM
-//   accumulator each (seven accumulators of 128 x 64).  The dropped levels 7..12 weigh at
-//   most 2^-53.4 of |X_a| |X_b| per term: the error of an FP64 product.
+//   Products.  sum_k X_ak X_bk = sum_{s,t} (sum_k d_s d'_t) 2^(8 (2 ND - 2 - s - t)); the
+//   pairs with s + t <= ND - 1 (28 or 36 MMAs per K step) are kept, summed per level
+//   l = s + t in one TMEM accumulator each (ND accumulators of 128 x 64).  The dropped
+//   levels weigh at most about 2^-(B-1.6) of |X_a| |X_b| per term.
 //
 //   Exactness.  |d_s d'_t| <= 2^14, so over 256 K values a level-l sum is at most
-//   (l + 1) 2^22: levels 0..3 stay below 2^24 and are exact FP32 integers whatever the
-//   tensor core's rounding; levels 4..6 can round by a few units of their own weight
+//   (l + 1) 2^22: levels 0..3 stay within 2^24 and are exact FP32 integers whatever the
+//   tensor core's rounding; higher levels can round by a few units of their own weight
 //   (2^-32 and below of level 0).  Every 256 K values the accumulators are read out
 //   (tcgen05.ld), converted to integers and added into two int64 registers per output,
-//   hi = L0 2^24 + L1 2^16 + L2 2^8 + L3 and lo = L4 2^16 + L5 2^8 + L6 (exact), and
-//   the TMEM accumulators start afresh.  At the end of a work item the output is
-//   (2^24 hi + lo) 2^(e_a + e_b - 62) in FP64.
+//   hi = L0 2^24 + L1 2^16 + L2 2^8 + L3 and lo = sum_{l >= 4} L_l 2^(8 (ND - 1 - l))
+//   (exact), and the TMEM accumulators start afresh.  At the end of a work item the output
+//   is (2^(8 (ND - 4)) hi + lo) 2^(e_a + e_b - 2B + 8 (ND - 1)) in FP64.
 //
-// Data flow.  Split kernels write the digits as seven BF16 planes [digit][row][k]
+// Data flow.  Split kernels write the digits as ND BF16 planes [digit][row][k]
 // (k contiguous): the Gram contracts over grid points, so its split kernel transposes
 // [U W] (tile transpose through shared memory) with one exponent per column and chunk of
 // grid points; the update contracts over the 2p columns of [U W] (already contiguous) with
 // one exponent per grid point.  The MMA kernel is warp specialised: one thread issues
-// TMA loads of 32-wide K slabs of all 14 digit planes (64-byte swizzle) into a two-stage
-// ring, one thread issues the 28 MMAs per 16-wide K step, and eight warps drain the
-// accumulators.  Every wait is bounded (2 s); a role that gives up sets the error word.
+// TMA loads of 32-wide K slabs of all 2 ND digit planes (64-byte swizzle) into a
+// two-stage ring, one thread issues the digit-pair MMAs of each 16-wide K step, and eight
+// warps drain the accumulators.  Every wait is bounded (2 s); a role that gives up sets
+// the error word.
 #include <algorithm>
 
 #include "common.cuh"
@@ -46,19 +52,21 @@ namespace opevo {
 
 namespace {
 
-constexpr int kDigits = 7;                 // digits per value
-constexpr int kLevels = 7;                 // accumulated levels s + t = 0..6
+// ND digits per value (7 for the Gram, 8 for the update: see the header); ND levels
+constexpr int kMaxDigits = 8;
+constexpr int kGramDigits = 7;    // the Gram: column exponents over grid points
+constexpr int kUpdateDigits = 8;  // the update: row exponents over the 2p values of a point
 constexpr int kBM = 128, kBN = 64;         // output tile: 128 A rows x 64 B rows
 constexpr int kKS = 32;                    // K per ring stage (64-byte rows)
 constexpr int kChunkStages = 8;            // 256 K values between accumulator read-outs
 constexpr int kAPlane = kBM * kKS * 2;     // 8 KB
 constexpr int kBPlane = kBN * kKS * 2;     // 4 KB
-constexpr int kStageBytes = kDigits * (kAPlane + kBPlane);  // 84 KB
+template <int ND> constexpr int stage_bytes() { return ND * (kAPlane + kBPlane); }  // 84 / 96 KB
 constexpr int kStages = 2;
-constexpr int kSmem = kStages * kStageBytes + 1024;
+template <int ND> constexpr int smem_bytes() { return kStages * stage_bytes<ND>() + 1024; }
 constexpr int kThreads = 320;              // warp 0 TMA, warp 1 MMA, warps 2..9 drain
 constexpr int kDrainWarps = 8;
-constexpr uint32_t kTmemCols = 512;        // 7 x 64 used
+constexpr uint32_t kTmemCols = 512;        // ND x 64 used
 constexpr uint32_t kIdesc = tc::idesc_bf16(kBM, kBN);
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -142,9 +150,12 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
+template <int ND>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fp64tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
              const Job J) {
+  constexpr int kDigits = ND, kLevels = ND;
+  constexpr int kStageBytes = stage_bytes<ND>();
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[kStages], empty[kStages], accfull, accempty, fin;
   __shared__ uint32_t tmem_sh;
@@ -290,7 +301,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int l = 0; l < kLevels; ++l) L[l] = (long long)__float2int_rz(__uint_as_float(v[l][e]));
             hi[g * 4 + e] += (L[0] << 24) + (L[1] << 16) + (L[2] << 8) + L[3];
-            lo[g * 4 + e] += (L[4] << 16) + (L[5] << 8) + L[6];
+            long long lv = 0;
+#pragma unroll
+            for (int l = 4; l < kLevels; ++l) lv += L[l] << (8 * (kLevels - 1 - l));
+            lo[g * 4 + e] += lv;
           }
         }
         tc::tc_fence_before();
@@ -298,7 +312,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) tc::mbar_arrive(&accempty);
       }
       if (!ok) break;
-      // epilogue: (2^24 hi + lo) 2^(e_a + e_b - 62)
+      // epilogue: (2^(8 (ND - 4)) hi + lo) 2^(e_a + e_b - 2 (8 ND - 1) + 8 (ND - 1))
+      constexpr double kHiW = (double)(1ll << (8 * (ND - 4)));
+      constexpr int kShift = -2 * (8 * ND - 1) + 8 * (ND - 1);
       if (J.mode == MODE_GRAM) {
         // rows and columns beyond nc hold zero digits (the loads past the planes read 0)
         const int ea = ra + row < J.nc ? J.ea[ra + row] : 0;
@@ -308,8 +324,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int cb = rb + half * 32 + j;
           const int eb0 = cb < J.nc ? J.eb[cb] : 0, eb1 = cb + 1 < J.nc ? J.eb[cb + 1] : 0;
           double2 o;
-          o.x = ldexp(fma((double)hi[j], 16777216.0, (double)lo[j]), ea + eb0 - 62);
-          o.y = ldexp(fma((double)hi[j + 1], 16777216.0, (double)lo[j + 1]), ea + eb1 - 62);
+          o.x = ldexp(fma((double)hi[j], kHiW, (double)lo[j]), ea + eb0 + kShift);
+          o.y = ldexp(fma((double)hi[j + 1], kHiW, (double)lo[j + 1]), ea + eb1 + kShift);
           *reinterpret_cast<double2 *>(dst + j) = o;
         }
       } else {
@@ -321,9 +337,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int col = rb + half * 32 + j;
             if (col < J.ld) {
               double2 o;
-              o.x = ldexp(fma((double)hi[j], 16777216.0, (double)lo[j]), ea + J.eb[col] - 62);
-              o.y = ldexp(fma((double)hi[j + 1], 16777216.0, (double)lo[j + 1]),
-                          ea + J.eb[col + 1] - 62);
+              o.x = ldexp(fma((double)hi[j], kHiW, (double)lo[j]), ea + J.eb[col] + kShift);
+              o.y = ldexp(fma((double)hi[j + 1], kHiW, (double)lo[j + 1]),
+                          ea + J.eb[col + 1] + kShift);
               if (J.mode == MODE_UPDATE_DELTA) {
                 const double2 b = *reinterpret_cast<const double2 *>(J.base + r * J.ld + col);
                 o.x += b.x;
@@ -354,15 +370,18 @@ __device__ __forceinline__ int exponent_of(double mx) {
   return e;
 }
 
-// The seven balanced base-256 digits of X = round(a 2^(55 - e)) (|a| < 2^e), as BF16 bit
+// The ND balanced base-256 digits of X = round(a 2^(8 ND - 1 - e)) (|a| < 2^e), as BF16 bit
 // patterns; integer arithmetic on the bits of a.  Subnormal a (below 2^-1022) count as 0.
-__device__ __forceinline__ void digits_of(double a, int e, uint16_t (&d)[kDigits]) {
+template <int ND>
+__device__ __forceinline__ void digits_of(double a, int e, uint16_t (&d)[ND]) {
+  constexpr int kDigits = ND;
   const long long bits = __double_as_longlong(a);
   const int be = (int)((bits >> 52) & 0x7FF);
   long long X = 0;
   if (be != 0) {
     const long long mant = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;
-    const int sh = be - 1020 - e;  // a 2^(55-e) = mant 2^sh, sh <= 2 since |a| < 2^e
+    // a 2^(8 ND - 1 - e) = mant 2^sh, sh <= 8 ND - 54 since |a| < 2^e
+    const int sh = be - 1075 + 8 * ND - 1 - e;
     if (sh >= 0) {
       X = mant << sh;
     } else if (sh > -64) {
@@ -404,6 +423,7 @@ __global__ void k_decode_exp(const int *__restrict__ enc, int *__restrict__ e, i
 
 // Digit planes P[s][c][x] (x contiguous, pitch xp) of the columns of Y over grid points
 // [x0, x0 + m): 64 x 64 tiles transposed through shared memory; x in [m, xp) gets zeros.
+template <int ND>
 __global__ void __launch_bounds__(256)
     k_split_cols(const double *__restrict__ U, const double *__restrict__ W, int ld, int nc,
                  long long x0, long long m, long long xp, const int *__restrict__ ecol,
@@ -421,13 +441,14 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const int cc = threadIdx.x >> 2, rq = (threadIdx.x & 3) * 16, c = cb + cc;
   if (c >= nc) return;
+  constexpr int kDigits = ND;
   const int e = ecol[c];
   uint32_t w[kDigits][8];
 #pragma unroll
   for (int r = 0; r < 16; r += 2) {
     uint16_t d0[kDigits], d1[kDigits];
-    digits_of(tile[rq + r][cc], e, d0);
-    digits_of(tile[rq + r + 1][cc], e, d1);
+    digits_of<ND>(tile[rq + r][cc], e, d0);
+    digits_of<ND>(tile[rq + r + 1][cc], e, d1);
 #pragma unroll
     for (int s = 0; s < kDigits; ++s) w[s][r >> 1] = (uint32_t)d0[s] | ((uint32_t)d1[s] << 16);
   }
@@ -442,6 +463,7 @@ __global__ void __launch_bounds__(256)
 
 // Digit planes Q[s][x][k] of the rows of [U W] (k < kdim = ld or 2 ld; W may be null when
 // kdim = ld) over grid points [x0, x0 + m), one exponent per row; one warp per row.
+template <int ND>
 __global__ void __launch_bounds__(256)
     k_split_rows(const double *__restrict__ U, const double *__restrict__ W, int ld, int kdim,
                  long long x0, long long m, int *__restrict__ erow, uint16_t *__restrict__ Q) {
@@ -457,6 +479,7 @@ __global__ void __launch_bounds__(256)
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  constexpr int kDigits = ND;
   const int e = exponent_of(mx);
   if (lane == 0) erow[r] = e;
   for (int k = 8 * lane; k < kdim; k += 256) {
@@ -466,8 +489,8 @@ __global__ void __launch_bounds__(256)
     for (int i = 0; i < 4; ++i) {
       const double2 v = *reinterpret_cast<const double2 *>(src + 2 * i);
       uint16_t d0[kDigits], d1[kDigits];
-      digits_of(v.x, e, d0);
-      digits_of(v.y, e, d1);
+      digits_of<ND>(v.x, e, d0);
+      digits_of<ND>(v.y, e, d1);
 #pragma unroll
       for (int s = 0; s < kDigits; ++s) w[s][i] = (uint32_t)d0[s] | ((uint32_t)d1[s] << 16);
     }
@@ -481,6 +504,7 @@ __global__ void __launch_bounds__(256)
 // Digit planes B[s][j][k] of the update's coefficient columns: column j of
 // [KU - delta I; KW] (k < kdim; KW may be null when kdim = ld), one exponent per j;
 // one warp per column.
+template <int ND>
 __global__ void __launch_bounds__(256)
     k_split_coef(const double *__restrict__ KU, const double *__restrict__ KW, int ld, int kdim,
                  int delta, int *__restrict__ ecol, uint16_t *__restrict__ B) {
@@ -495,6 +519,7 @@ __global__ void __launch_bounds__(256)
   for (int k = lane; k < kdim; k += 32) mx = fmax(mx, fabs(val(k)));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  constexpr int kDigits = ND;
   const int e = exponent_of(mx);
   if (lane == 0) ecol[j] = e;
   for (int k = 8 * lane; k < kdim; k += 256) {
@@ -502,8 +527,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       uint16_t d0[kDigits], d1[kDigits];
-      digits_of(val(k + 2 * i), e, d0);
-      digits_of(val(k + 2 * i + 1), e, d1);
+      digits_of<ND>(val(k + 2 * i), e, d0);
+      digits_of<ND>(val(k + 2 * i + 1), e, d1);
 #pragma unroll
       for (int s = 0; s < kDigits; ++s) w[s][i] = (uint32_t)d0[s] | ((uint32_t)d1[s] << 16);
     }
@@ -545,20 +570,22 @@ __global__ void k_gram_scatter(const double *__restrict__ G, int nc, int ld, int
   }
 }
 
+template <int ND>
 op_status launch_mma(const CUtensorMap &mA, const CUtensorMap &mB, const Job &J,
                      cudaStream_t st) {
   if (J.nitems <= 0) return OP_OK;
-  OP_CUDA(cudaFuncSetAttribute(k_fp64tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  OP_CUDA(cudaFuncSetAttribute(k_fp64tc<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem_bytes<ND>()));
   const long long grid = std::min<long long>(J.nitems, num_sms());
-  k_fp64tc<<<(unsigned)grid, kThreads, kSmem, st>>>(mA, mB, J);
+  k_fp64tc<ND><<<(unsigned)grid, kThreads, smem_bytes<ND>(), st>>>(mA, mB, J);
   count_launch();
   OP_LAUNCH("k_fp64tc");
   return OP_OK;
 }
 
 long long chunk_rows(long long n, int ld) {
-  // digit planes of one chunk: 7 x 2 ld x rows BF16 = 28 ld rows bytes, at most 8 GiB
-  long long r = ((long long)8 << 30) / (28ll * ld);
+  // digit planes of one chunk: up to 8 x 2 ld x rows BF16 = 32 ld rows bytes, at most 8 GiB
+  long long r = ((long long)8 << 30) / (32ll * ld);
   r = r / 256 * 256;
   if (r < 4096) r = 4096;
   const long long nr = (n + 63) / 64 * 64;
@@ -617,7 +644,7 @@ Carve carve(void *ws, long long n, int ld) {
   Carve c;
   const uintptr_t p = (uintptr_t)ws;
   c.planes = (uint16_t *)(p + off);
-  off += up((size_t)kDigits * 2 * ld * (rows + 64) * 2);
+  off += up((size_t)kMaxDigits * 2 * ld * (rows + 64) * 2);
   c.e1 = (int *)(p + off);
   off += up((size_t)(rows + 2 * ld) * 4);
   c.e2 = (int *)(p + off);
@@ -627,7 +654,7 @@ Carve carve(void *ws, long long n, int ld) {
   c.G = (double *)(p + off);
   off += up((size_t)4 * ld * ld * 8);
   c.coef = (uint16_t *)(p + off);
-  off += up((size_t)kDigits * ld * 2 * ld * 2);
+  off += up((size_t)kMaxDigits * ld * 2 * ld * 2);
   c.part = (double *)(p + off);
   // the most items of any chunk, for [U W] (2 ld columns) and for U alone (ld)
   long long items = 0;
@@ -677,13 +704,13 @@ op_status gram_fp64tc(long long n, int p, int ld, const double *U, const double 
     count_launch();
     k_decode_exp<<<(nc + 255) / 256, 256, 0, st>>>(cv.enc, cv.e2, nc);
     count_launch();
-    k_split_cols<<<dim3((unsigned)(xp / 64), (nc + 63) / 64), 256, 0, st>>>(U, W, ld, nc, x0, m,
-                                                                           xp, cv.e2, cv.planes);
+    k_split_cols<kGramDigits><<<dim3((unsigned)(xp / 64), (nc + 63) / 64), 256, 0, st>>>(
+        U, W, ld, nc, x0, m, xp, cv.e2, cv.planes);
     count_launch();
     OP_LAUNCH("fp64tc split");
     CUtensorMap mA, mB;
-    OP_TRY(tma_map_3d_bf16_sw64(&mA, cv.planes, (uint64_t)xp, (uint64_t)nc, kDigits, kBM));
-    OP_TRY(tma_map_3d_bf16_sw64(&mB, cv.planes, (uint64_t)xp, (uint64_t)nc, kDigits, kBN));
+    OP_TRY(tma_map_3d_bf16_sw64(&mA, cv.planes, (uint64_t)xp, (uint64_t)nc, kGramDigits, kBM));
+    OP_TRY(tma_map_3d_bf16_sw64(&mB, cv.planes, (uint64_t)xp, (uint64_t)nc, kGramDigits, kBN));
     const int nr = gram_ranges(ntiles, m);
     long long kr = (m + nr - 1) / nr;
     kr = (kr + kKS - 1) / kKS * kKS;
@@ -701,7 +728,7 @@ op_status gram_fp64tc(long long n, int p, int ld, const double *U, const double 
     J.ea = cv.e2;
     J.eb = cv.e2;
     J.err = err;
-    OP_TRY(launch_mma(mA, mB, J, st));
+    OP_TRY(launch_mma<kGramDigits>(mA, mB, J, st));
     k_gram_acc<<<dim3(ntiles, 8), 256, 0, st>>>(cv.part, ntiles, nranges, nJ, nc, cv.G);
     count_launch();
     OP_LAUNCH("k_gram_acc");
@@ -726,22 +753,22 @@ op_status update_fp64tc(long long n, int ld, const double *U, const double *W, c
   }
   const Carve cv = carve(ws, n, ld);
   const int kdim = W ? 2 * ld : ld;
-  k_split_coef<<<(ld * 32 + 255) / 256, 256, 0, st>>>(KU, W ? KW : nullptr, ld, kdim,
-                                                      delta ? 1 : 0, cv.e2, cv.coef);
+  k_split_coef<kUpdateDigits><<<(ld * 32 + 255) / 256, 256, 0, st>>>(
+      KU, W ? KW : nullptr, ld, kdim, delta ? 1 : 0, cv.e2, cv.coef);
   count_launch();
   OP_LAUNCH("k_split_coef");
   CUtensorMap mB;
-  OP_TRY(tma_map_3d_bf16_sw64(&mB, cv.coef, (uint64_t)kdim, (uint64_t)ld, kDigits, kBN));
+  OP_TRY(tma_map_3d_bf16_sw64(&mB, cv.coef, (uint64_t)kdim, (uint64_t)ld, kUpdateDigits, kBN));
   const long long rows = chunk_rows(n, ld);
   const int ntn = (ld + kBN - 1) / kBN;
   for (long long x0 = 0; x0 < n; x0 += rows) {
     const long long m = std::min(rows, n - x0);
-    k_split_rows<<<(unsigned)((m * 32 + 255) / 256), 256, 0, st>>>(U, W, ld, kdim, x0, m, cv.e1,
-                                                                  cv.planes);
+    k_split_rows<kUpdateDigits><<<(unsigned)((m * 32 + 255) / 256), 256, 0, st>>>(
+        U, W, ld, kdim, x0, m, cv.e1, cv.planes);
     count_launch();
     OP_LAUNCH("k_split_rows");
     CUtensorMap mA;
-    OP_TRY(tma_map_3d_bf16_sw64(&mA, cv.planes, (uint64_t)kdim, (uint64_t)m, kDigits, kBM));
+    OP_TRY(tma_map_3d_bf16_sw64(&mA, cv.planes, (uint64_t)kdim, (uint64_t)m, kUpdateDigits, kBM));
     Job J{};
     J.mode = delta ? MODE_UPDATE_DELTA : MODE_UPDATE;
     J.nitems = ((m + kBM - 1) / kBM) * ntn;
@@ -754,7 +781,7 @@ op_status update_fp64tc(long long n, int ld, const double *U, const double *W, c
     J.ea = cv.e1;
     J.eb = cv.e2;
     J.err = err;
-    OP_TRY(launch_mma(mA, mB, J, st));
+    OP_TRY(launch_mma<kUpdateDigits>(mA, mB, J, st));
   }
   return OP_OK;
 }

@@ -16,12 +16,12 @@ import numpy as np
 import pytest
 
 
-def to_int(a, e):
-    """round(a 2^(55 - e)), ties away from zero, exactly (a is a float, |a| < 2^e)."""
+def to_int(a, e, nd=7):
+    """round(a 2^(8 nd - 1 - e)), ties away from zero, exactly (a is a float, |a| < 2^e)."""
     num, den = float(a).as_integer_ratio()
     sgn = -1 if num < 0 else 1
     num = abs(num)
-    sh = 55 - e
+    sh = 8 * nd - 1 - e
     if sh >= 0:
         num <<= sh
     else:
@@ -29,9 +29,9 @@ def to_int(a, e):
     return sgn * ((2 * num + den) // (2 * den))
 
 
-def digits(X):
-    d = [0] * 7
-    for s in range(6, 0, -1):
+def digits(X, nd=7):
+    d = [0] * nd
+    for s in range(nd - 1, 0, -1):
         lo8 = X & 0xFF
         dd = lo8 - 256 if lo8 >= 128 else lo8
         d[s] = dd
@@ -44,23 +44,25 @@ def exponent(mx):
     return math.frexp(mx)[1] if mx > 0 else 0
 
 
-def emulate_dot(a, b, run=256):
+def emulate_dot(a, b, run=256, nd=7):
     """The kernel's product of two contraction rows, with FP32 level sums per run."""
     ea, eb = exponent(np.abs(a).max()), exponent(np.abs(b).max())
-    da = [digits(to_int(x, ea)) for x in a]
-    db = [digits(to_int(x, eb)) for x in b]
+    da = [digits(to_int(x, ea, nd), nd) for x in a]
+    db = [digits(to_int(x, eb, nd), nd) for x in b]
     hi = lo = 0
     for k0 in range(0, len(a), run):
-        L = [np.float32(0.0)] * 7
+        L = [np.float32(0.0)] * nd
         for k in range(k0, min(k0 + run, len(a))):
-            for s in range(7):
-                for t in range(7 - s):
+            for s in range(nd):
+                for t in range(nd - s):
                     L[s + t] = np.float32(L[s + t] + np.float32(da[k][s] * db[k][t]))
         Li = [int(v) for v in L]
         hi += (Li[0] << 24) + (Li[1] << 16) + (Li[2] << 8) + Li[3]
-        lo += (Li[4] << 16) + (Li[5] << 8) + Li[6]
+        lo += sum(Li[lv] << (8 * (nd - 1 - lv)) for lv in range(4, nd))
     assert abs(hi) < 2 ** 63 and abs(lo) < 2 ** 63
-    return math.ldexp(float(hi) * 16777216.0 + float(lo), ea + eb - 62), da, db
+    B = 8 * nd - 1
+    return math.ldexp(float(hi) * 2.0 ** (8 * (nd - 4)) + float(lo),
+                      ea + eb - 2 * B + 8 * (nd - 1)), da, db
 
 
 def test_digits_reconstruct_the_integer_exactly():
@@ -108,12 +110,13 @@ def test_levels_0_to_3_are_exact_in_fp32_over_256_terms():
     assert exact[4] > 2 ** 24
 
 
+@pytest.mark.parametrize("nd", [7, 8])
 @pytest.mark.parametrize("n,scale", [(300, 1.0), (700, 1e-8), (257, 3e5)])
-def test_emulated_product_is_fp64_accurate(n, scale):
+def test_emulated_product_is_fp64_accurate(n, scale, nd):
     rng = np.random.default_rng(n)
     a = rng.standard_normal(n) * scale
     b = rng.standard_normal(n) * np.exp(rng.uniform(-3, 3, n))
-    got, _, _ = emulate_dot(a, b)
+    got, _, _ = emulate_dot(a, b, nd=nd)
     exact = sum(Fraction(x) * Fraction(y) for x, y in zip(a, b))
     # error class of an FP64 dot product, relative to the largest |a| |b| of the run
     bound = n * 2.0 ** -52 * np.abs(a).max() * np.abs(b).max()
@@ -149,3 +152,17 @@ def test_dropping_a_digit_pair_breaks_fp64_accuracy():
     got = math.ldexp(float(hi) * 16777216.0 + float(lo), ea + eb - 62)
     exact = float(sum(Fraction(x) * Fraction(y) for x, y in zip(a, b)))
     assert abs(got - exact) > 1e3 * 2.0 ** -53 * abs(exact)
+
+
+def test_eight_digits_resolve_terms_far_below_the_row_maximum():
+    # one large entry per row and many small ones (a localised orbital at a grid point):
+    # seven digits resolve the small terms to 2^-55 of the maximum, eight to 2^-63
+    rng = np.random.default_rng(11)
+    a = rng.standard_normal(512) * 1e-3
+    a[7] = 1.0
+    b = rng.standard_normal(512)
+    exact = sum(Fraction(x) * Fraction(y) for x, y in zip(a, b))
+    err7 = abs(float(Fraction(emulate_dot(a, b, nd=7)[0]) - exact))
+    err8 = abs(float(Fraction(emulate_dot(a, b, nd=8)[0]) - exact))
+    assert err8 <= 2.0 ** -60 * 512 * np.abs(b).max()
+    assert err8 < err7 / 16 or err7 == 0.0
