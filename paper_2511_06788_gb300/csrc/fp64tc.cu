@@ -238,15 +238,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc::tc_fence_after();
-          const uint32_t base = tc::smem_u32(smem + slot * kStageBytes);
+          // one descriptor per stage; an operand tile at byte offset o of the stage is the
+          // descriptor plus o / 16 (the start-address field; offsets stay below 2^18)
+          const uint64_t d0 = desc_sw64(tc::smem_u32(smem + slot * kStageBytes));
 #pragma unroll
           for (int ks = 0; ks < kKS / 16; ++ks) {
 #pragma unroll
             for (int s = 0; s < kDigits; ++s) {
-              const uint64_t ad = desc_sw64(base + s * kAPlane + ks * 32);
+              const uint64_t ad = d0 + (uint64_t)((s * kAPlane + ks * 32) >> 4);
 #pragma unroll
               for (int t = 0; t < kDigits - s; ++t) {
-                const uint64_t bd = desc_sw64(base + kDigits * kAPlane + t * kBPlane + ks * 32);
+                const uint64_t bd =
+                    d0 + (uint64_t)((kDigits * kAPlane + t * kBPlane + ks * 32) >> 4);
                 const uint32_t acc = (cstart && ks == 0 && s == 0) ? 0u : 1u;
                 tc::mma_bf16(tmem + (uint32_t)((s + t) * kBN), ad, bd, kIdesc, acc);
               }
