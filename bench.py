@@ -74,14 +74,15 @@ FP64_CG_FLOPS = {"cg_apply": 12, "cg_axpy": 10, "cg_dir": 2, "cg_init": 18, "ene
 
 
 def digit_flops(group, n, ld):
-    """BF16 tensor flops one step's FP64 Gram / update issues on the tensor cores."""
+    """BF16 tensor flops one step's FP64 Gram (7 digits: 28 digit-pair MMAs per K step) /
+    update (8 digits: 36) issues on the tensor cores."""
     if group == "gram":
         nc = 2 * ld
         nI, nJ = (nc + 127) // 128, (nc + 63) // 64
         tiles = sum(max(0, nJ - 2 * i) for i in range(nI))
         return 28 * 2 * tiles * 128 * 64 * n
     if group == "update":
-        return 28 * 2 * ((n + 127) // 128 * 128) * ((ld + 63) // 64 * 64) * 2 * ld
+        return 36 * 2 * ((n + 127) // 128 * 128) * ((ld + 63) // 64 * 64) * 2 * ld
     return 0
 KERNEL_NAME = {("cg_apply", "fp32"): "k_cg_tma", ("cg_axpy", "fp32"): "k_cg_wr",
                ("cg_apply", "fp64"): "k_cg_apply", ("cg_axpy", "fp64"): "k_cg_axpy",
@@ -464,7 +465,8 @@ def run_headline(args):
     P = headline_problem(rank)
     n, p, ld = P.n, P.p, (P.p + 7) // 8 * 8
     # roofline denominators measured by the library's own microbenchmarks, before the run
-    peaks = {k: pkg.binding.peak_rate(k, stream) for k in ("fp64_fma", "tf32_mma", "bf16_mma")}
+    peaks = {k: pkg.binding.peak_rate(k, stream)
+             for k in ("fp64_fma", "tf32_mma", "bf16_mma", "bf16_mma_n64")}
     hbm, _, peak_kind = load_peaks()
     bf16_sust = _sustained_bf16()
 
@@ -520,6 +522,9 @@ def run_headline(args):
                             "frac": a / bf16_sust, "traffic": None,
                             "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained "
                                            "(cuBLAS BF16, seconds-long loop)",
+                            "frac_of_n64_mma_peak": a / peaks["bf16_mma_n64"],
+                            "n64_peak_source": "op_peak_rate(OP_PEAK_BF16_MMA_N64) in this "
+                                               "run: the MMA shape the kernel issues",
                             "algo_flops_per_launch": fl, "avg_launch_ms": 1e3 * avg_s,
                             "share_of_step_time": tot_ms / ms}
         elif g in FP64_CG_FLOPS:
@@ -669,6 +674,40 @@ def ttr_legs(pkg, dev, stream, modes):
     return {"workload": TTR_WORKLOAD, "n": P.n, "p": P.p, "tol": 1e-6, "adapt_every": 50,
             "timing": "host wall clock from op_init_device (device-resident V and raw U0) to "
                       "the residual stop rule, residual checks included", "modes": rows}
+
+
+def run_fp64tc_kernels(args):
+    """One FP64 tensor-core Gram (seven digits) and one update (eight digits) on n = 262144
+    points, p = 256 (blocks of 0.5 GB, digit planes of 2 GB: larger than L2, a few GB on
+    the device): the small case of the kernels' ncu captures.  Prints their CUDA-event
+    times and BF16 MMA rates."""
+    import torch
+
+    import paper_2511_06788_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    n, p = 262144, 256
+    g = torch.Generator(device="cuda").manual_seed(0)
+    U = torch.randn(n, p, dtype=torch.float64, device="cuda", generator=g)
+    W = 0.1 * torch.randn(n, p, dtype=torch.float64, device="cuda", generator=g)
+    K = torch.eye(p, dtype=torch.float64, device="cuda") + \
+        0.01 * torch.randn(p, p, dtype=torch.float64, device="cuda", generator=g)
+    out = {}
+    for name, fn, fl in (("gram", lambda: pkg.binding.gram_fp64tc(U, W, p),
+                          digit_flops("gram", n, p)),
+                         ("update", lambda: pkg.binding.update_fp64tc(U, W, K, K, p),
+                          digit_flops("update", n, p))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms": ms, "bf16_tflops": fl / (ms * 1e-3) / 1e12}
+    print(json.dumps({"workload": "fp64tc_kernels_n262144_p256", "calls": out}), flush=True)
+    return 0
 
 
 def _sustained_bf16():
@@ -1116,7 +1155,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c3fp64",
                     choices=["c3fp64", "3d_wells_64", "batch64", "warmstart48", "ttr64",
-                             "batch64-ttr", "c3"])
+                             "batch64-ttr", "c3", "fp64tc_kernels"])
     ap.add_argument("--ttr-legs", default="fp64,fp64_fma,fp32,mix_bf16x3",
                     help="modes timed to residual 1e-6 beside the default workload (or none)")
     ap.add_argument("--legs", default="fp32,mix_bf16x3,fp64_fma",
@@ -1155,6 +1194,8 @@ def main():
         return run_c3(args)
     if args.workload == "3d_wells_64":
         return run_ours(args)
+    if args.workload == "fp64tc_kernels":
+        return run_fp64tc_kernels(args)
     return run_headline(args)
 
 

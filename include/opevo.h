@@ -296,7 +296,8 @@ op_status op_selftest_bounded_waits(double *seconds, void *stream);
 typedef enum {
   OP_PEAK_FP64_FMA = 0,
   OP_PEAK_TF32_MMA = 1,
-  OP_PEAK_BF16_MMA = 2
+  OP_PEAK_BF16_MMA = 2,
+  OP_PEAK_BF16_MMA_N64 = 3  /* BF16 at N = 64 (the FP64 digit products' MMA shape) */
 } op_peak_kind;
 op_status op_peak_rate(int kind, double *tflops, void *stream);
 

@@ -3,7 +3,9 @@
 //   OP_PEAK_FP64_FMA   FP64 FMA on the CUDA cores: 8 independent chains x = x a + b per
 //                      thread, 2 flops each;
 //   OP_PEAK_TF32_MMA   tcgen05.mma kind::tf32, M = 128, N = 256, K = 8 per instruction;
-//   OP_PEAK_BF16_MMA   tcgen05.mma kind::f16 (BF16), M = 128, N = 256, K = 16.
+//   OP_PEAK_BF16_MMA   tcgen05.mma kind::f16 (BF16), M = 128, N = 256, K = 16;
+//   OP_PEAK_BF16_MMA_N64  the same at N = 64, the shape of the FP64 digit products (the
+//                      tensor core takes as long for N = 64 as for N = 128: half the rate).
 // The MMA kernels run one CTA per SM; one thread issues back-to-back MMAs on operand tiles
 // resident in shared memory into two alternating TMEM accumulators (no memory traffic),
 // then waits (bounded) for their completion.  Rates are flops over the CUDA-event time of
@@ -34,7 +36,7 @@ constexpr int kPM = 128, kPN = 256;
 constexpr int kPA = kPM * 128, kPB = kPN * 128;  // one 128-byte K row per operand row
 constexpr int kPeakSmem = kPA + kPB + 1024;
 
-// kind: 1 TF32 (K = 8 per MMA), 2 BF16 (K = 16); `mmas` instructions per CTA.
+// kind: 1 TF32 (K = 8 per MMA), 2 BF16 (K = 16), 3 BF16 at N = 64; `mmas` instructions per CTA.
 __global__ void __launch_bounds__(128, 1) k_peak_mma(int kind, int mmas, int *err) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t done;
@@ -62,7 +64,8 @@ __global__ void __launch_bounds__(128, 1) k_peak_mma(int kind, int mmas, int *er
   const uint32_t tmem = tmem_sh;
   if (threadIdx.x == 0) {
     const uint32_t a = tc::smem_u32(smem), b = a + kPA;
-    const uint32_t id = kind == 1 ? tc::idesc_tf32(kPM, kPN) : tc::idesc_bf16(kPM, kPN);
+    const int nn = kind == 3 ? 64 : kPN;
+    const uint32_t id = kind == 1 ? tc::idesc_tf32(kPM, kPN) : tc::idesc_bf16(kPM, nn);
     for (int i = 0; i < mmas; ++i) {
       const uint32_t k = (uint32_t)(i & 3) * 32;  // the four 32-byte K steps of the row
       const uint64_t ad = tc::desc_sw128(a + k), bd = tc::desc_sw128(b + k);
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(128, 1) k_peak_mma(int kind, int mmas, int *er
 using namespace opevo;
 
 extern "C" op_status op_peak_rate(int kind, double *tflops, void *stream) {
-  if (!tflops || kind < OP_PEAK_FP64_FMA || kind > OP_PEAK_BF16_MMA) {
+  if (!tflops || kind < OP_PEAK_FP64_FMA || kind > OP_PEAK_BF16_MMA_N64) {
     set_error("op_peak_rate: bad kind %d or null output", kind);
     return OP_ERR_ARG;
   }
@@ -114,8 +117,10 @@ extern "C" op_status op_peak_rate(int kind, double *tflops, void *stream) {
     } else {
       const int mmas = 1 << 15;
       cudaFuncSetAttribute(k_peak_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeakSmem);
-      k_peak_mma<<<sms, 128, kPeakSmem, st>>>(kind == OP_PEAK_TF32_MMA ? 1 : 2, mmas, err);
-      flops = 2.0 * kPM * kPN * (kind == OP_PEAK_TF32_MMA ? 8 : 16) * (double)mmas * sms;
+      k_peak_mma<<<sms, 128, kPeakSmem, st>>>(
+          kind == OP_PEAK_TF32_MMA ? 1 : (kind == OP_PEAK_BF16_MMA ? 2 : 3), mmas, err);
+      flops = 2.0 * kPM * (kind == OP_PEAK_BF16_MMA_N64 ? 64 : kPN) *
+              (kind == OP_PEAK_TF32_MMA ? 8 : 16) * (double)mmas * sms;
     }
     count_launch();
     cudaEventRecord(e1, st);
