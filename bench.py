@@ -61,10 +61,6 @@ ALGO_BYTES = {
         "energy": lambda n, p, s: n * s * (p + 1),         # read U, V
     },
 }
-# FP64 mode: algorithmic flops per launch of the FP64-pipe-bound groups (C = W^T U in
-# full, S and D one triangle each; the update [U W] [KU; KW] is n x 2p x p)
-FP64_FLOPS = {"gram": lambda n, p: 4 * n * p * p, "update": lambda n, p: 4 * n * p * p}
-FP64_TFLOPS = 1.25  # GB300 nominal FP64 (non-tensor) rate
 # FP64 CG kernels (three-kernel iteration, Jacobi variant): algorithmic FP64 flops per
 # element of the n x p block (FMA = 2): the 7-point apply is 3 pair sums, the diagonal
 # product and three scaled subtractions (10); p.q adds 2.  axpy: w += a p, z -= a q / d,
@@ -95,6 +91,66 @@ KERNEL_NAME.update({(g, "mix_tf32"): k for (g, q), k in list(KERNEL_NAME.items()
 for _m in ("mix_bf16x3", "mix_bf16"):
     KERNEL_NAME.update({(g, _m): k for (g, q), k in list(KERNEL_NAME.items()) if q == "fp32"})
     KERNEL_NAME.update({("gram", _m): "k_gram_bf16", ("update", _m): "k_update_bf16"})
+
+
+def fp64_rooflines(prof, n, p, ld, steps, ms, peaks, hbm, bf16_sust):
+    """Rooflines of the FP64 mode's kernel groups over a timed region (`prof`: group ->
+    (device ms, launch ranges); `ms`: the region's time), each against the unit that bounds
+    it:
+    - gram / update: the digit-pair MMAs on the tensor cores (BF16 flops; with the digit
+      split in the group's time) against the sustained cuBLAS BF16 rate, and against the
+      library's best N = 64 MMA rate;
+    - cg_*: with the mixed-precision Step 1 (a cg_refine group present) these are the FP32
+      inner CG kernels, bound by HBM (FP32 bytes over ld columns); in plain FP64 CG the FP64
+      kernels, bound by the FP64 ALU;
+    - cg_refine: the FP64 residual, scaled FP32 right-hand side and FP64 correction, bound
+      by HBM (bytes per element: residual 24, right-hand side 12 + 4, correction 20);
+    - energy: the FP64 quadratic form on the FP64 ALU."""
+    groups = {k: v for k, v in prof.items() if v[1] > 0}
+    refine = "cg_refine" in groups
+    out = {}
+    for g, (tot_ms, cnt) in groups.items():
+        avg_s = tot_ms * 1e-3 / cnt
+        base = {"avg_launch_ms": 1e3 * avg_s, "launch_ranges": cnt,
+                "share_of_step_time": tot_ms / ms}
+        if g in ("gram", "update"):
+            fl = digit_flops(g, n, ld)
+            a = fl / avg_s / 1e12
+            out[g] = dict(base, bound="tensor", kernel="k_fp64tc (with its digit split)",
+                          achieved=a, peak=bf16_sust, unit="TFLOP/s", frac=a / bf16_sust,
+                          traffic=None,
+                          peak_source="MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS BF16, "
+                                      "seconds-long loop)",
+                          frac_of_n64_mma_peak=a / peaks["bf16_mma_n64_areuse"],
+                          n64_peak_source="op_peak_rate(OP_PEAK_BF16_MMA_N64_AREUSE) in this "
+                                          "run: the kernel's MMA shape, 128 x 64 x 16, at its "
+                                          "best measured rate",
+                          algo_flops_per_launch=fl)
+        elif g == "cg_refine":
+            # ranges per step: (residual, rhs, correction) per cycle and a closing residual
+            full = max(0, (cnt - steps) // 3)
+            by = n * ld * (24.0 * (full + steps) + 36.0 * full)
+            a = by / (tot_ms * 1e-3) / 1e9
+            out[g] = dict(base, bound="hbm", kernel="k_cg_init<double> + k_ref_rhs + k_ref_correct",
+                          achieved=a, peak=hbm, unit="GB/s", frac=a / hbm, traffic=None,
+                          peak_source="MEASURED_PEAKS.json hbm_gbs",
+                          algo_bytes_per_step=by / steps)
+        elif g.startswith("cg_") and g in ALGO_BYTES["fp32"] and refine:
+            by = algo_bytes(g, "fp32", n, ld, 4, cnt, steps)
+            a = by / avg_s / 1e9
+            out[g] = dict(base, bound="hbm", kernel=KERNEL_NAME.get((g, "fp32"), g) + " (FP32 inner CG)",
+                          achieved=a, peak=hbm, unit="GB/s", frac=a / hbm, traffic=None,
+                          peak_source="MEASURED_PEAKS.json hbm_gbs", algo_bytes_per_launch=by)
+        elif g in FP64_CG_FLOPS and (g == "energy" or not refine):
+            fl = FP64_CG_FLOPS[g] * n * p
+            a = fl / avg_s / 1e12
+            by = algo_bytes(g, "fp64", n, p, 8, cnt, steps) if g != "energy" else n * 8 * (p + 1)
+            out[g] = dict(base, bound="alu", kernel=KERNEL_NAME.get((g, "fp64"), g),
+                          achieved=a, peak=peaks["fp64_fma"], unit="TFLOP/s",
+                          frac=a / peaks["fp64_fma"], traffic=None,
+                          peak_source="measured by op_peak_rate(OP_PEAK_FP64_FMA) in this run",
+                          algo_flops_per_launch=fl, hbm_frac=by / avg_s / 1e9 / hbm)
+    return out
 
 
 def algo_bytes(group, prec, n, p, s, launches, solves):
@@ -377,17 +433,15 @@ def run_ours(args):
     if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_source_sha(dom, args.prec) and \
             not (dom == "cg_axpy" and args.precond != "jacobi"):
         traffic = NCU_TRAFFIC[key][0]
-    if args.prec == "fp64" and dom in FP64_FLOPS:
-        # FP64 Gram and update run on the FP64 pipe (about 2 DFMA / clock / SM on GB300):
-        # roofline against the nominal FP64 rate, algorithmic flops per launch
-        flops = FP64_FLOPS[dom](n, p)
-        fa = flops / avg_s / 1e12
-        roofline = {"bound": "alu", "kernel": KERNEL_NAME.get((dom, args.prec), dom),
-                    "group": dom, "achieved": fa, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                    "frac": fa / FP64_TFLOPS, "traffic": None,
-                    "peak_source": "nominal GB300 FP64 rate (not measured)",
-                    "algo_flops_per_launch": flops, "avg_launch_ms": 1e3 * avg_s,
-                    "share_of_step_time": tot_ms / ms}
+    if args.prec == "fp64":
+        # FP64 mode: the digit products on the tensor cores, the mixed-precision Step 1 and
+        # the FP64 ALU kernels, each against its own measured peak
+        peaks = {k: pkg.binding.peak_rate(k, stream)
+                 for k in ("fp64_fma", "bf16_mma_n64_areuse")}
+        rls = fp64_rooflines(prof, n, p, (p + 7) // 8 * 8, args.steps, ms, peaks, hbm,
+                             _sustained_bf16())
+        dom = max(rls, key=lambda g: rls[g]["share_of_step_time"])
+        roofline = dict(rls[dom], group=dom)
     else:
         roofline = {"bound": "hbm", "kernel": KERNEL_NAME.get((dom, args.prec), dom),
                     "group": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -466,7 +520,7 @@ def run_headline(args):
     n, p, ld = P.n, P.p, (P.p + 7) // 8 * 8
     # roofline denominators measured by the library's own microbenchmarks, before the run
     peaks = {k: pkg.binding.peak_rate(k, stream)
-             for k in ("fp64_fma", "tf32_mma", "bf16_mma", "bf16_mma_n64")}
+             for k in ("fp64_fma", "tf32_mma", "bf16_mma", "bf16_mma_n64", "bf16_mma_n64_areuse")}
     hbm, _, peak_kind = load_peaks()
     bf16_sust = _sustained_bf16()
 
@@ -511,35 +565,7 @@ def run_headline(args):
 
     # rooflines of every timed group; the dominant one (most device time) is the headline's
     groups = {k: v for k, v in prof.items() if v[1] > 0}
-    rooflines = {}
-    for g, (tot_ms, cnt) in groups.items():
-        avg_s = tot_ms * 1e-3 / cnt
-        if g in ("gram", "update"):
-            fl = digit_flops(g, n, ld)
-            a = fl / avg_s / 1e12
-            rooflines[g] = {"bound": "tensor", "kernel": "k_fp64tc (with its digit split)",
-                            "achieved": a, "peak": bf16_sust, "unit": "TFLOP/s",
-                            "frac": a / bf16_sust, "traffic": None,
-                            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained "
-                                           "(cuBLAS BF16, seconds-long loop)",
-                            "frac_of_n64_mma_peak": a / peaks["bf16_mma_n64"],
-                            "n64_peak_source": "op_peak_rate(OP_PEAK_BF16_MMA_N64) in this "
-                                               "run: the MMA shape the kernel issues",
-                            "algo_flops_per_launch": fl, "avg_launch_ms": 1e3 * avg_s,
-                            "share_of_step_time": tot_ms / ms}
-        elif g in FP64_CG_FLOPS:
-            fl = FP64_CG_FLOPS[g] * n * p
-            a = fl / avg_s / 1e12
-            by = algo_bytes(g, "fp64", n, p, 8, cnt, args.steps) if g != "energy" else \
-                n * 8 * (p + 1)
-            rooflines[g] = {"bound": "alu", "kernel": KERNEL_NAME.get((g, "fp64"), g),
-                            "achieved": a, "peak": peaks["fp64_fma"], "unit": "TFLOP/s",
-                            "frac": a / peaks["fp64_fma"], "traffic": None,
-                            "peak_source": "measured by op_peak_rate(OP_PEAK_FP64_FMA) in "
-                                           "this run",
-                            "algo_flops_per_launch": fl, "avg_launch_ms": 1e3 * avg_s,
-                            "hbm_frac": by / avg_s / 1e9 / hbm,
-                            "share_of_step_time": tot_ms / ms}
+    rooflines = fp64_rooflines(prof, n, p, ld, args.steps, ms, peaks, hbm, bf16_sust)
     dom = max(rooflines, key=lambda g: rooflines[g]["share_of_step_time"])
     roofline = dict(rooflines[dom], group=dom)
     kernel_times = {k: {"ms": round(v[0], 3), "groups": v[1]} for k, v in groups.items()}

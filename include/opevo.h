@@ -297,7 +297,11 @@ typedef enum {
   OP_PEAK_FP64_FMA = 0,
   OP_PEAK_TF32_MMA = 1,
   OP_PEAK_BF16_MMA = 2,
-  OP_PEAK_BF16_MMA_N64 = 3  /* BF16 at N = 64 (the FP64 digit products' MMA shape) */
+  OP_PEAK_BF16_MMA_N64 = 3,  /* BF16 at N = 64 (the FP64 digit products' MMA shape), a new
+                                A tile every MMA */
+  OP_PEAK_BF16_MMA_N64_AREUSE = 4  /* the same, each A tile kept in the tensor core's
+                                      collector buffer over four MMAs with different B
+                                      (the digit products' issue pattern) */
 } op_peak_kind;
 op_status op_peak_rate(int kind, double *tflops, void *stream);
 

@@ -662,7 +662,8 @@ def gaussian_block(seed, n, p, device=None, stream=None):
     return out
 
 
-PEAKS = {"fp64_fma": 0, "tf32_mma": 1, "bf16_mma": 2, "bf16_mma_n64": 3}
+PEAKS = {"fp64_fma": 0, "tf32_mma": 1, "bf16_mma": 2, "bf16_mma_n64": 3,
+         "bf16_mma_n64_areuse": 4}
 
 
 def peak_rate(kind, stream=None) -> float:

@@ -575,7 +575,7 @@ op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
     const size_t pb = (part_bytes(ld) + 255) / 256 * 256;
     const size_t sb = ((size_t)6 * ld * sizeof(double) + 255) / 256 * 256;
     const size_t ab = ((size_t)ld * sizeof(int) + 255) / 256 * 256;
-    OP_TRY(dev_alloc(c, &p, pb + sb + ab + 256 + (size_t)ld * sizeof(double)));
+    OP_TRY(dev_alloc(c, &p, pb + sb + ab + 256 + (size_t)ld * (sizeof(double) + sizeof(float))));
     c->cgw32.part = (double *)p;
     c->cgw32.state = (double *)((char *)p + pb);
     c->cgw32.active = (int *)((char *)p + pb + sb);

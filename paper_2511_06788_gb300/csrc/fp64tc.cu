@@ -38,10 +38,17 @@
 // grid points; the update contracts over the 2p columns of [U W] (already contiguous) with
 // one exponent per grid point.  The MMA kernel is warp specialised: one thread issues
 // TMA loads of 32-wide K slabs of all 2 ND digit planes (64-byte swizzle) into a
-// two-stage ring, one thread issues the digit-pair MMAs of each 16-wide K step, and eight
-// warps drain the accumulators.  Every wait is bounded (2 s); a role that gives up sets
-// the error word.
+// two-stage ring, two threads issue the digit-pair MMAs of each 16-wide K step (each for
+// its own levels: the tensor core takes an MMA about every 45 clocks, and a single issuing
+// thread loses hundreds of clocks at every barrier of the ring), and eight warps drain the
+// accumulators.  CTAs run in clusters of two on two SMs; the pair computes
+// two output tiles with the same 128 A rows and adjacent 64-row blocks of B, and each CTA
+// loads one 64-row half of the A planes into both CTAs' shared memory (TMA multicast), so
+// a stage moves 2/3 of its bytes from L2.  A slot of the ring is free when the MMAs of
+// both CTAs have read it.  Every wait is bounded (2 s); a role that gives up sets the
+// error word.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -57,15 +64,28 @@ constexpr int kMaxDigits = 8;
 constexpr int kGramDigits = 7;    // the Gram: column exponents over grid points
 constexpr int kUpdateDigits = 8;  // the update: row exponents over the 2p values of a point
 constexpr int kBM = 128, kBN = 64;         // output tile: 128 A rows x 64 B rows
-constexpr int kKS = 32;                    // K per ring stage (64-byte rows)
-constexpr int kChunkStages = 8;            // 256 K values between accumulator read-outs
-constexpr int kAPlane = kBM * kKS * 2;     // 8 KB
-constexpr int kBPlane = kBN * kKS * 2;     // 4 KB
-template <int ND> constexpr int stage_bytes() { return ND * (kAPlane + kBPlane); }  // 84 / 96 KB
-constexpr int kStages = 2;
-template <int ND> constexpr int smem_bytes() { return kStages * stage_bytes<ND>() + 1024; }
-constexpr int kThreads = 320;              // warp 0 TMA, warp 1 MMA, warps 2..9 drain
+#ifndef FP64TC_KS
+#define FP64TC_KS 32
+#endif
+#ifndef FP64TC_STAGES
+#define FP64TC_STAGES 8
+#endif
+constexpr int kKS = FP64TC_KS;             // K per ring stage: 16 (32-byte rows) or 32 (64)
+constexpr int kChunkStages = 256 / kKS;    // 256 K values between accumulator read-outs
+constexpr int kAPlane = kBM * kKS * 2;     // 4 or 8 KB
+constexpr int kBPlane = kBN * kKS * 2;     // 2 or 4 KB
+template <int ND> constexpr int stage_bytes() { return ND * (kAPlane + kBPlane); }
+// ring depth: as many stages as fit 226 KB, at most FP64TC_STAGES
+template <int ND> constexpr int ring_stages() {
+  return (226 * 1024) / stage_bytes<ND>() < FP64TC_STAGES ? (226 * 1024) / stage_bytes<ND>()
+                                                          : FP64TC_STAGES;
+}
+static_assert(kKS == 16 || kKS == 32, "K slab of one or two MMA K steps");
+static_assert(ring_stages<8>() >= 2, "ring of at least two stages");
+template <int ND> constexpr int smem_bytes() { return ring_stages<ND>() * stage_bytes<ND>() + 1024; }
+constexpr int kIssuers = 2;                // warps 1 .. kIssuers issue the MMAs
 constexpr int kDrainWarps = 8;
+constexpr int kThreads = 32 * (1 + kIssuers + kDrainWarps);  // warp 0 TMA, then MMA, drain
 constexpr uint32_t kTmemCols = 512;        // ND x 64 used
 constexpr uint32_t kIdesc = tc::idesc_bf16(kBM, kBN);
 constexpr uint64_t kWaitNs = 2000000000ull;
@@ -74,7 +94,8 @@ enum { MODE_GRAM = 0, MODE_UPDATE_DELTA = 1, MODE_UPDATE = 2 };
 
 struct Job {
   int mode;
-  long long nitems;
+  long long npairs;      // work items in pairs that share their A rows (a cluster's CTAs)
+  int npt;               // Gram: tile pairs per K range
   // Gram: upper-triangle tiles of Y^T Y (Y: nc columns), K ranges of krange grid points
   int nc, nI, nJ, ntiles;
   long long krange, kext;
@@ -101,36 +122,158 @@ __device__ __forceinline__ void tile_of(int t, int nJ, int *I, int *J) {
   *J = 2 * i + t;
 }
 
-// Rows of A and B, first K and K length of a work item.
-__device__ __forceinline__ void decode_item(const Job &J, long long item, int *ra, int *rb,
-                                            long long *k0, long long *klen) {
+// Member r (0 or 1) of item pair `pair`: the two members share the A rows and the K range
+// and take adjacent 64-row blocks of B.  A member past the last B block is a stand-in
+// (valid = false): its B rows read as zeros and it writes nothing.  *item: the member's
+// index among the unpaired items (the Gram's partial tile).
+__device__ __forceinline__ void decode_pair(const Job &J, long long pair, int r, int *ra, int *rb,
+                                            long long *k0, long long *klen, bool *valid,
+                                            long long *item) {
   if (J.mode == MODE_GRAM) {
-    const long long q = item / J.ntiles;
-    int I, Jt;
-    tile_of((int)(item % J.ntiles), J.nJ, &I, &Jt);
+    const long long q = pair / J.npt;
+    int tp = (int)(pair % J.npt), I = 0;
+    for (;;) {
+      const int cnt = (J.nJ - 2 * I + 1) / 2;
+      if (tp < cnt) break;
+      tp -= cnt;
+      ++I;
+    }
+    const int Jt = 2 * I + 2 * tp + r;
+    *valid = Jt < J.nJ;
     *ra = I * kBM;
     *rb = Jt * kBN;
     *k0 = q * J.krange;
     const long long e = (q + 1) * J.krange < J.kext ? (q + 1) * J.krange : J.kext;
     *klen = e > *k0 ? e - *k0 : 0;
+    *item = q * J.ntiles + (long long)I * J.nJ - (long long)I * (I - 1) + (Jt - 2 * I);
   } else {
-    *ra = (int)(item / J.ntn) * kBM;
-    *rb = (int)(item % J.ntn) * kBN;
+    const int npn = (J.ntn + 1) / 2;
+    const int jn = (int)(pair % npn) * 2 + r;
+    *valid = jn < J.ntn;
+    *ra = (int)(pair / npn) * kBM;
+    *rb = jn * kBN;
     *k0 = 0;
     *klen = J.kdim;
+    *item = (pair / npn) * J.ntn + jn;
   }
 }
 
-// Shared-memory descriptor of a K-major operand tile in the 64-byte-swizzled layout
-// (rows of 64 bytes, 8-row groups of 512 bytes); `saddr` may be advanced by 32 bytes
-// (one 16-wide BF16 K step) inside the row.
-__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// TMA load of one box into the same shared-memory offset of both CTAs of the cluster, with
+// completion counted in bytes on the barrier at the same offset of each.
+__device__ __forceinline__ void load_3d_mc(void *dst, const CUtensorMap *map, int c0, int c1,
+                                           int c2, uint64_t *bar) {
+  const uint16_t mask = 0x3;
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(tma::smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2),
+      "r"(tma::smem_addr(bar)), "h"(mask)
+      : "memory");
+}
+// One arrival on `bar` in both CTAs of the cluster when this thread's MMAs complete.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar) {
+  const uint16_t mask = 0x3;
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(tc::smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+// D[tmem] (+)= A B^T (BF16, K = 16) with the A operand kept in the tensor core's collector
+// buffer across a run of MMAs that share it: C = 1 loads A and keeps it (fill), 2 reuses it
+// (use), 3 reuses it for the last time (lastuse), 0 a lone MMA (A read and discarded).
+template <int C>
+__device__ __forceinline__ void mma_bf16_ca(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  if constexpr (C == 1) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}\n"
+                 ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
+  } else if constexpr (C == 2) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}\n"
+                 ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
+  } else if constexpr (C == 3) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}\n"
+                 ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
+  } else {
+    tc::mma_bf16(d_tmem, a_desc, b_desc, idesc, accumulate);
+  }
+}
+
+// kIssuers threads issue the digit-pair MMAs, each for the levels in its mask: the pairs
+// of one level (one accumulator) all come from one thread, in order, and while one thread
+// waits at a barrier the others keep the tensor core busy.  The masks balance the pair
+// counts l + 1 of the levels between the threads.
+template <int ND> constexpr unsigned issuer_mask(int which) {
+  constexpr unsigned all = (1u << ND) - 1u;
+  if (kIssuers == 1) return all;
+  if (kIssuers == 2) {
+    constexpr unsigned a = ND == 7 ? 0x47u : 0x8Fu;  // {0,1,2,6} | {0,1,2,3,7}
+    return which == 0 ? a : all & ~a;
+  }
+  // three: {0,1,6} {2,5} {3,4} (10 / 9 / 9 pairs) | {3,7} {4,6} {0,1,2,5} (12 each)
+  constexpr unsigned m7[3] = {0x43u, 0x24u, 0x18u}, m8[3] = {0x88u, 0x50u, 0x27u};
+  return ND == 7 ? m7[which] : m8[which];
+}
+// First and last t of A digit s's MMAs (t < ND - s) whose level s + t is in `mask`.
+constexpr int run_first(int nd, unsigned mask, int s) {
+  for (int t = 0; t < nd - s; ++t)
+    if ((mask >> (s + t)) & 1u) return t;
+  return -1;
+}
+constexpr int run_last(int nd, unsigned mask, int s) {
+  for (int t = nd - s - 1; t >= 0; --t)
+    if ((mask >> (s + t)) & 1u) return t;
+  return -1;
+}
+
+// The MMAs of A digit S against B digits T.. (S + T in MASK); every level starts afresh at
+// its first MMA, (0, l), when `first` is set.  With one issuer (REUSE) A is held in the
+// collector buffer from the first MMA of the run to the last; two issuers interleave their
+// MMAs on the one tensor core, so each MMA then reads its own A.
+template <int ND, unsigned MASK, int S, int T>
+__device__ __forceinline__ void mma_digit_run(uint32_t tmem, uint64_t ad, uint64_t bd0,
+                                              uint32_t first) {
+  if constexpr (T < ND - S) {
+    if constexpr ((MASK >> (S + T)) & 1u) {
+      constexpr int f = run_first(ND, MASK, S), l = run_last(ND, MASK, S);
+      constexpr int C = kIssuers > 1 || f == l ? 0 : (T == f ? 1 : (T == l ? 3 : 2));
+      mma_bf16_ca<C>(tmem + (uint32_t)((S + T) * kBN), ad,
+                     bd0 + (uint64_t)((T * kBPlane) >> 4), kIdesc, S == 0 && first ? 0u : 1u);
+    }
+    mma_digit_run<ND, MASK, S, T + 1>(tmem, ad, bd0, first);
+  }
+}
+template <int ND, unsigned MASK, int S>
+__device__ __forceinline__ void mma_kstep(uint32_t tmem, uint64_t a0, uint64_t bd0,
+                                          uint32_t first) {
+  if constexpr (S < ND) {
+    mma_digit_run<ND, MASK, S, 0>(tmem, a0 + (uint64_t)((S * kAPlane) >> 4), bd0, first);
+    mma_kstep<ND, MASK, S + 1>(tmem, a0, bd0, first);
+  }
+}
+
+// Shared-memory descriptor of a K-major operand tile in the layout swizzled over rows of
+// 2 kKS bytes (64-byte swizzle for kKS = 32, 32-byte for 16; 8-row groups of 16 kKS
+// bytes); `saddr` may be advanced by 32 bytes (one 16-wide BF16 K step) inside the row.
+__device__ __forceinline__ uint64_t desc_sw(uint32_t saddr) {
   uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused: K fits a row)
-  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)4 << 61;                    // layout: 64-byte swizzle
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);       // start address
+  d |= (uint64_t)1 << 16;                         // leading byte offset (unused: K fits a row)
+  d |= (uint64_t)((16 * kKS) >> 4) << 32;         // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                         // descriptor version
+  d |= (uint64_t)(kKS == 32 ? 4 : 6) << 61;       // layout: 64- or 32-byte swizzle
   return d;
 }
 
@@ -156,6 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1)
              const Job J) {
   constexpr int kDigits = ND, kLevels = ND;
   constexpr int kStageBytes = stage_bytes<ND>();
+  constexpr int kStages = ring_stages<ND>();
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t full[kStages], empty[kStages], accfull, accempty, fin;
   __shared__ uint32_t tmem_sh;
@@ -163,124 +307,138 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+  const int rank = (int)cluster_rank();
+  const long long cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+
   if (warp == 1) tc::tmem_alloc(&tmem_sh, kTmemCols);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&empty[s], 2 * kIssuers);  // both issuers of both CTAs of the pair
     }
-    tc::mbar_init(&accfull, 1);
+    tc::mbar_init(&accfull, kIssuers);
     tc::mbar_init(&accempty, kDrainWarps);
-    tc::mbar_init(&fin, 1);
+    tc::mbar_init(&fin, kIssuers);
     tc::fence_mbar_init();
     abort_sh = 0;
   }
   tc::tc_fence_before();
   __syncthreads();
+  cluster_sync();  // the peer's copies and arrivals may target this CTA's barriers from here on
   tc::tc_fence_after();
   const uint32_t tmem = tmem_sh;
   volatile int *abort = &abort_sh;
+
+  // ---- MMA issuers: the digit pairs of the levels in MASK ---------------------------------
+  auto issue = [&](auto maskc) {
+    constexpr unsigned MASK = decltype(maskc)::value;
+    long long it = 0, chunk = 0;
+    bool ok = true, issued = false;
+    for (long long pr = cid; pr < J.npairs && ok; pr += ncl) {
+      int ra, rb;
+      long long k0, klen, item;
+      bool valid;
+      decode_pair(J, pr, rank, &ra, &rb, &k0, &klen, &valid, &item);
+      const long long nst = (klen + kKS - 1) / kKS;
+      for (long long st = 0; st < nst; ++st, ++it) {
+        const bool cstart = (st % kChunkStages) == 0;
+        if (cstart && chunk > 0) {
+          // the accumulators start afresh once the drain warps have read them
+          if (!tc::wait_or_abort(&accempty, (uint32_t)((chunk - 1) & 1), abort, kWaitNs)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+        }
+        const int slot = (int)(it % kStages);
+        if (!tc::wait_or_abort(&full[slot], (uint32_t)((it / kStages) & 1), abort, kWaitNs)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        // one descriptor per stage; an operand tile at byte offset o of the stage is the
+        // descriptor plus o / 16 (the start-address field; offsets stay below 2^18)
+        const uint64_t d0 = desc_sw(tc::smem_u32(smem + slot * kStageBytes));
+#pragma unroll
+        for (int ks = 0; ks < kKS / 16; ++ks)
+          mma_kstep<ND, MASK, 0>(tmem, d0 + (uint64_t)((ks * 32) >> 4),
+                                 d0 + (uint64_t)((kDigits * kAPlane + ks * 32) >> 4),
+                                 (cstart && ks == 0) ? 1u : 0u);
+        issued = true;
+        mma_commit_mc(&empty[slot]);  // the slot is free in both CTAs once all have read it
+        if ((st % kChunkStages) == kChunkStages - 1 || st == nst - 1) {
+          tc::mma_commit(&accfull);
+          ++chunk;
+        }
+      }
+    }
+    // every MMA has completed before TMEM is released
+    if (issued) tc::mma_commit(&fin);
+    else tc::mbar_arrive(&fin);
+    tma::bar_wait(&fin, 0u, kWaitNs);
+  };
 
   if (warp == 0) {
     // ---- TMA producer ----------------------------------------------------------------
     if (lane == 0) {
       long long it = 0;
       bool ok = true;
-      for (long long item = blockIdx.x; item < J.nitems && ok; item += gridDim.x) {
+      for (long long pr = cid; pr < J.npairs && ok; pr += ncl) {
         int ra, rb;
-        long long k0, klen;
-        decode_item(J, item, &ra, &rb, &k0, &klen);
+        long long k0, klen, item;
+        bool valid;
+        decode_pair(J, pr, rank, &ra, &rb, &k0, &klen, &valid, &item);
         const long long nst = (klen + kKS - 1) / kKS;
         for (long long st = 0; st < nst; ++st, ++it) {
-          const int slot = (int)(it & 1);
-          const long long use = it >> 1;
+          const int slot = (int)(it % kStages);
+          const long long use = it / kStages;
           if (use > 0 && !tc::wait_or_abort(&empty[slot], (uint32_t)((use - 1) & 1), abort,
                                             kWaitNs)) {
             ok = false;
             break;
           }
+          // this CTA's bytes: its own B planes and both halves of the A planes
           tma::bar_expect(&full[slot], (uint32_t)kStageBytes);
           uint8_t *sb = smem + slot * kStageBytes;
           const int kc = (int)(k0 + st * kKS);
+          const int half_off = rank * (kAPlane / 2);
 #pragma unroll
-          for (int s = 0; s < kDigits; ++s) tma::load_3d(sb + s * kAPlane, &mA, kc, ra, s, &full[slot]);
+          for (int s = 0; s < kDigits; ++s)
+            load_3d_mc(sb + s * kAPlane + half_off, &mA, kc, ra + rank * (kBM / 2), s, &full[slot]);
 #pragma unroll
           for (int t = 0; t < kDigits; ++t)
             tma::load_3d(sb + kDigits * kAPlane + t * kBPlane, &mB, kc, rb, t, &full[slot]);
         }
       }
-      // the copies issued last must land before the CTA may exit (bounded)
-      for (long long u = it - 1; u >= 0 && u >= it - kStages; --u)
-        tma::bar_wait(&full[u & 1], (uint32_t)((u >> 1) & 1), kWaitNs);
+      // the copies issued last must land, and both CTAs' MMAs release the slots, before the
+      // CTA may exit (bounded)
+      for (long long u = it - 1; u >= 0 && u >= it - kStages; --u) {
+        tma::bar_wait(&full[u % kStages], (uint32_t)((u / kStages) & 1), kWaitNs);
+        tma::bar_wait(&empty[u % kStages], (uint32_t)((u / kStages) & 1), kWaitNs);
+      }
     }
-  } else if (warp == 1) {
-    // ---- MMA issuer ----------------------------------------------------------------------
+  } else if (warp <= kIssuers) {
     if (lane == 0) {
-      long long it = 0, chunk = 0;
-      bool ok = true, issued = false;
-      for (long long item = blockIdx.x; item < J.nitems && ok; item += gridDim.x) {
-        int ra, rb;
-        long long k0, klen;
-        decode_item(J, item, &ra, &rb, &k0, &klen);
-        const long long nst = (klen + kKS - 1) / kKS;
-        for (long long st = 0; st < nst; ++st, ++it) {
-          const bool cstart = (st % kChunkStages) == 0;
-          if (cstart && chunk > 0) {
-            if (!tc::wait_or_abort(&accempty, (uint32_t)((chunk - 1) & 1), abort, kWaitNs)) {
-              ok = false;
-              break;
-            }
-            tc::tc_fence_after();
-          }
-          const int slot = (int)(it & 1);
-          if (!tc::wait_or_abort(&full[slot], (uint32_t)((it >> 1) & 1), abort, kWaitNs)) {
-            ok = false;
-            break;
-          }
-          tc::tc_fence_after();
-          // one descriptor per stage; an operand tile at byte offset o of the stage is the
-          // descriptor plus o / 16 (the start-address field; offsets stay below 2^18)
-          const uint64_t d0 = desc_sw64(tc::smem_u32(smem + slot * kStageBytes));
-#pragma unroll
-          for (int ks = 0; ks < kKS / 16; ++ks) {
-#pragma unroll
-            for (int s = 0; s < kDigits; ++s) {
-              const uint64_t ad = d0 + (uint64_t)((s * kAPlane + ks * 32) >> 4);
-#pragma unroll
-              for (int t = 0; t < kDigits - s; ++t) {
-                const uint64_t bd =
-                    d0 + (uint64_t)((kDigits * kAPlane + t * kBPlane + ks * 32) >> 4);
-                const uint32_t acc = (cstart && ks == 0 && s == 0) ? 0u : 1u;
-                tc::mma_bf16(tmem + (uint32_t)((s + t) * kBN), ad, bd, kIdesc, acc);
-              }
-            }
-          }
-          issued = true;
-          tc::mma_commit(&empty[slot]);
-          if ((st % kChunkStages) == kChunkStages - 1 || st == nst - 1) {
-            tc::mma_commit(&accfull);
-            ++chunk;
-          }
-        }
-      }
-      if (issued) {
-        // every MMA has completed before TMEM is released
-        tc::mma_commit(&fin);
-        tma::bar_wait(&fin, 0u, kWaitNs);
-      }
+      if (warp == 1)
+        issue(std::integral_constant<unsigned, issuer_mask<ND>(0)>{});
+      else if (warp == 2)
+        issue(std::integral_constant<unsigned, issuer_mask<ND>(1)>{});
+      else if constexpr (kIssuers > 2)
+        issue(std::integral_constant<unsigned, issuer_mask<ND>(2)>{});
     }
   } else {
     // ---- drain warps ---------------------------------------------------------------------
-    const int q = warp & 3;                // TMEM lane quarter this warp may read
-    const int half = (warp - 2) >> 2;      // output columns 32 half .. 32 half + 31
-    const int row = q * 32 + lane;         // tile row
+    const int q = warp & 3;                         // TMEM lane quarter this warp may read
+    const int half = (warp - kIssuers - 1) >> 2;    // output columns 32 half .. 32 half + 31
+    const int row = q * 32 + lane;                  // tile row
     const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 32);
     long long chunk = 0;
     bool ok = true;
-    for (long long item = blockIdx.x; item < J.nitems && ok; item += gridDim.x) {
+    for (long long pr = cid; pr < J.npairs && ok; pr += ncl) {
       int ra, rb;
-      long long k0, klen;
-      decode_item(J, item, &ra, &rb, &k0, &klen);
+      long long k0, klen, item;
+      bool valid;
+      decode_pair(J, pr, rank, &ra, &rb, &k0, &klen, &valid, &item);
       const long long nst = (klen + kKS - 1) / kKS;
       const long long nch = (nst + kChunkStages - 1) / kChunkStages;
       long long hi[32], lo[32];
@@ -315,6 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) tc::mbar_arrive(&accempty);
       }
       if (!ok) break;
+      if (!valid) continue;  // a stand-in member: zeros in, nothing out
       // epilogue: (2^(8 (ND - 4)) hi + lo) 2^(e_a + e_b - 2 (8 ND - 1) + 8 (ND - 1))
       constexpr double kHiW = (double)(1ll << (8 * (ND - 4)));
       constexpr int kShift = -2 * (8 * ND - 1) + 8 * (ND - 1);
@@ -358,6 +517,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc::tc_fence_before();
   __syncthreads();
+  cluster_sync();  // nothing of the peer's still targets this CTA's shared memory
   if (warp == 1) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, kTmemCols);
@@ -573,14 +733,60 @@ __global__ void k_gram_scatter(const double *__restrict__ G, int nc, int ld, int
   }
 }
 
+// Clusters of two CTAs (one per SM) that can be resident at once, queried once per digit
+// count on the current device.
+template <int ND>
+op_status resident_clusters(int *n) {
+  static int dev_of = -1, cached = 0;
+  int dev = 0;
+  OP_CUDA(cudaGetDevice(&dev));
+  if (dev_of != dev) {
+    OP_CUDA(cudaFuncSetAttribute(k_fp64tc<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_bytes<ND>()));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2 * (unsigned)num_sms());
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem_bytes<ND>();
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int c = 0;
+    OP_CUDA(cudaOccupancyMaxActiveClusters(&c, k_fp64tc<ND>, &cfg));
+    if (c < 1) {
+      set_error("k_fp64tc: no cluster of two CTAs fits an SM pair");
+      return OP_ERR_CUDA;
+    }
+    cached = c;
+    dev_of = dev;
+  }
+  *n = cached;
+  return OP_OK;
+}
+
 template <int ND>
 op_status launch_mma(const CUtensorMap &mA, const CUtensorMap &mB, const Job &J,
                      cudaStream_t st) {
-  if (J.nitems <= 0) return OP_OK;
-  OP_CUDA(cudaFuncSetAttribute(k_fp64tc<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               smem_bytes<ND>()));
-  const long long grid = std::min<long long>(J.nitems, num_sms());
-  k_fp64tc<ND><<<(unsigned)grid, kThreads, smem_bytes<ND>(), st>>>(mA, mB, J);
+  if (J.npairs <= 0) return OP_OK;
+  int ncl = 0;
+  OP_TRY(resident_clusters<ND>(&ncl));
+  const long long clusters = std::min<long long>(J.npairs, ncl);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(2 * clusters));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem_bytes<ND>();
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  OP_CUDA(cudaLaunchKernelEx(&cfg, k_fp64tc<ND>, mA, mB, J));
   count_launch();
   OP_LAUNCH("k_fp64tc");
   return OP_OK;
@@ -595,29 +801,37 @@ long long chunk_rows(long long n, int ld) {
   return r < nr ? r : nr;
 }
 
-int gram_tiles(int nc, int *nI, int *nJ) {
+// Upper-triangle tiles of an nc x nc Gram in 128 x 64 tiles (every row of tiles I has
+// nJ - 2 I >= 1 of them); *npt: the tile pairs (I, J), (I, J + 1) of the rows.
+int gram_tiles(int nc, int *nI, int *nJ, int *npt = nullptr) {
   *nI = (nc + kBM - 1) / kBM;
   *nJ = (nc + kBN - 1) / kBN;
-  int t = 0;
-  for (int i = 0; i < *nI; ++i) t += *nJ - 2 * i > 0 ? *nJ - 2 * i : 0;
+  int t = 0, pt = 0;
+  for (int i = 0; i < *nI; ++i) {
+    const int c = *nJ - 2 * i > 0 ? *nJ - 2 * i : 0;
+    t += c;
+    pt += (c + 1) / 2;
+  }
+  if (npt) *npt = pt;
   return t;
 }
 
-// K ranges per chunk: the fewest that make the items a near multiple of the SM count.
-int gram_ranges(int ntiles, long long m) {
-  const int sms = num_sms();
+// K ranges per chunk: the fewest that make the tile pairs a near multiple of the clusters
+// (two SMs each).
+int gram_ranges(int npt, long long m) {
+  const int slots = std::max(1, num_sms() / 2);
   const long long maxr = std::max<long long>(1, (m + 1023) / 1024);
   int best = 1;
   double best_eff = 0.0;
   for (int r = 1; r <= 64 && r <= maxr; ++r) {
-    const long long items = (long long)ntiles * r;
-    const long long waves = (items + sms - 1) / sms;
-    const double eff = (double)items / (double)(waves * sms);
+    const long long items = (long long)npt * r;
+    const long long waves = (items + slots - 1) / slots;
+    const double eff = (double)items / (double)(waves * slots);
     if (eff > best_eff + 1e-9) {
       best_eff = eff;
       best = r;
     }
-    if (eff >= 0.95 && items >= sms) break;
+    if (eff >= 0.95 && items >= slots) break;
   }
   return best;
 }
@@ -633,8 +847,8 @@ struct Carve {
   size_t total;
 };
 
-long long gram_items(int ntiles, long long m) {
-  const int nr = gram_ranges(ntiles, m);
+long long gram_items(int ntiles, int npt, long long m) {
+  const int nr = gram_ranges(npt, m);
   long long kr = (m + nr - 1) / nr;
   kr = (kr + kKS - 1) / kKS * kKS;
   return (long long)ntiles * ((m + kr - 1) / kr);
@@ -662,10 +876,10 @@ Carve carve(void *ws, long long n, int ld) {
   // the most items of any chunk, for [U W] (2 ld columns) and for U alone (ld)
   long long items = 0;
   for (int nc : {2 * ld, ld}) {
-    int nI, nJ;
-    const int nt = gram_tiles(nc, &nI, &nJ);
-    items = std::max(items, gram_items(nt, std::min(rows, n)));
-    if (n % rows) items = std::max(items, gram_items(nt, n % rows));
+    int nI, nJ, npt;
+    const int nt = gram_tiles(nc, &nI, &nJ, &npt);
+    items = std::max(items, gram_items(nt, npt, std::min(rows, n)));
+    if (n % rows) items = std::max(items, gram_items(nt, npt, n % rows));
   }
   off += up((size_t)items * kBM * kBN * 8);
   c.total = off;
@@ -693,8 +907,8 @@ op_status gram_fp64tc(long long n, int p, int ld, const double *U, const double 
   }
   const Carve cv = carve(ws, n, ld);
   const int nc = W ? 2 * ld : ld;
-  int nI, nJ;
-  const int ntiles = gram_tiles(nc, &nI, &nJ);
+  int nI, nJ, npt;
+  const int ntiles = gram_tiles(nc, &nI, &nJ, &npt);
   const long long rows = chunk_rows(n, ld);
   OP_CUDA(cudaMemsetAsync(cv.G, 0, (size_t)nc * nc * sizeof(double), st));
   for (long long x0 = 0; x0 < n; x0 += rows) {
@@ -712,15 +926,17 @@ op_status gram_fp64tc(long long n, int p, int ld, const double *U, const double 
     count_launch();
     OP_LAUNCH("fp64tc split");
     CUtensorMap mA, mB;
-    OP_TRY(tma_map_3d_bf16_sw64(&mA, cv.planes, (uint64_t)xp, (uint64_t)nc, kGramDigits, kBM));
-    OP_TRY(tma_map_3d_bf16_sw64(&mB, cv.planes, (uint64_t)xp, (uint64_t)nc, kGramDigits, kBN));
-    const int nr = gram_ranges(ntiles, m);
+    // A: each CTA of a pair loads (and multicasts) one 64-row half of the 128 A rows
+    OP_TRY(tma_map_3d_bf16_sw(&mA, cv.planes, (uint64_t)xp, (uint64_t)nc, kGramDigits, kBM / 2, kKS));
+    OP_TRY(tma_map_3d_bf16_sw(&mB, cv.planes, (uint64_t)xp, (uint64_t)nc, kGramDigits, kBN, kKS));
+    const int nr = gram_ranges(npt, m);
     long long kr = (m + nr - 1) / nr;
     kr = (kr + kKS - 1) / kKS * kKS;
     const int nranges = (int)((m + kr - 1) / kr);
     Job J{};
     J.mode = MODE_GRAM;
-    J.nitems = (long long)ntiles * nranges;
+    J.npairs = (long long)npt * nranges;
+    J.npt = npt;
     J.nc = nc;
     J.nI = nI;
     J.nJ = nJ;
@@ -761,7 +977,7 @@ op_status update_fp64tc(long long n, int ld, const double *U, const double *W, c
   count_launch();
   OP_LAUNCH("k_split_coef");
   CUtensorMap mB;
-  OP_TRY(tma_map_3d_bf16_sw64(&mB, cv.coef, (uint64_t)kdim, (uint64_t)ld, kUpdateDigits, kBN));
+  OP_TRY(tma_map_3d_bf16_sw(&mB, cv.coef, (uint64_t)kdim, (uint64_t)ld, kUpdateDigits, kBN, kKS));
   const long long rows = chunk_rows(n, ld);
   const int ntn = (ld + kBN - 1) / kBN;
   for (long long x0 = 0; x0 < n; x0 += rows) {
@@ -771,10 +987,10 @@ op_status update_fp64tc(long long n, int ld, const double *U, const double *W, c
     count_launch();
     OP_LAUNCH("k_split_rows");
     CUtensorMap mA;
-    OP_TRY(tma_map_3d_bf16_sw64(&mA, cv.planes, (uint64_t)kdim, (uint64_t)m, kUpdateDigits, kBM));
+    OP_TRY(tma_map_3d_bf16_sw(&mA, cv.planes, (uint64_t)kdim, (uint64_t)m, kUpdateDigits, kBM / 2, kKS));
     Job J{};
     J.mode = delta ? MODE_UPDATE_DELTA : MODE_UPDATE;
-    J.nitems = ((m + kBM - 1) / kBM) * ntn;
+    J.npairs = ((m + kBM - 1) / kBM) * ((ntn + 1) / 2);
     J.mrows = m;
     J.ntn = ntn;
     J.kdim = kdim;

@@ -150,7 +150,8 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
 // reductions), stops when every column meets ||r_j|| <= rtol ||u_j||, else solves
 // (H + sigma) d = r_j / ||r_j|| by the FP32 CG of w32 (V in FP32: Vt32; rhs r32, solution
 // d32: n x ld FP32 blocks) to a relative tolerance that the cycle needs, and adds
-// ||r_j|| d_j to W in FP64.  scale: ld doubles of device scratch.  *iters: FP32 CG
+// ||r_j|| d_j to W in FP64.  scale: ld doubles plus ld floats of device scratch (16-byte
+// aligned).  *iters: FP32 CG
 // iterations of all cycles; *cycles: FP64 residual evaluations.
 op_status cg_refine(const Geom &g, const double *Vt, const float *Vt32, double sigma,
                     const double *U, double *W, int p, int ld, double rtol, int max_iter,

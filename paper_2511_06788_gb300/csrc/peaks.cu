@@ -4,8 +4,13 @@
 //                      thread, 2 flops each;
 //   OP_PEAK_TF32_MMA   tcgen05.mma kind::tf32, M = 128, N = 256, K = 8 per instruction;
 //   OP_PEAK_BF16_MMA   tcgen05.mma kind::f16 (BF16), M = 128, N = 256, K = 16;
-//   OP_PEAK_BF16_MMA_N64  the same at N = 64, the shape of the FP64 digit products (the
-//                      tensor core takes as long for N = 64 as for N = 128: half the rate).
+//   OP_PEAK_BF16_MMA_N64  the same at N = 64, the shape of the FP64 digit products, on
+//                      eight accumulators in turn, every MMA with a new A tile: reading
+//                      A (128 x 16) from shared memory for each 128 x 64 x 16 product
+//                      holds N = 64 to about half the N = 256 rate;
+//   OP_PEAK_BF16_MMA_N64_AREUSE  N = 64 with each A tile held in the collector buffer over
+//                      four MMAs against four different B tiles (fill, use, use, lastuse),
+//                      the way the digit products issue them.
 // The MMA kernels run one CTA per SM; one thread issues back-to-back MMAs on operand tiles
 // resident in shared memory into two alternating TMEM accumulators (no memory traffic),
 // then waits (bounded) for their completion.  Rates are flops over the CUDA-event time of
@@ -33,10 +38,28 @@ __global__ void __launch_bounds__(256) k_peak_dfma(int iters, double a, double b
 }
 
 constexpr int kPM = 128, kPN = 256;
+
+// BF16 MMA with the A operand's collector buffer: op 1 fill, 2 use, 3 lastuse.
+__device__ __forceinline__ void mma_n64_areuse(uint32_t d, uint64_t ad, uint64_t bd, uint32_t id,
+                                               uint32_t acc, int op) {
+  if (op == 1)
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}\n"
+                 ::"r"(d), "l"(ad), "l"(bd), "r"(id), "r"(acc) : "memory");
+  else if (op == 2)
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}\n"
+                 ::"r"(d), "l"(ad), "l"(bd), "r"(id), "r"(acc) : "memory");
+  else
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}\n"
+                 ::"r"(d), "l"(ad), "l"(bd), "r"(id), "r"(acc) : "memory");
+}
 constexpr int kPA = kPM * 128, kPB = kPN * 128;  // one 128-byte K row per operand row
 constexpr int kPeakSmem = kPA + kPB + 1024;
 
-// kind: 1 TF32 (K = 8 per MMA), 2 BF16 (K = 16), 3 BF16 at N = 64; `mmas` instructions per CTA.
+// kind: 1 TF32 (K = 8 per MMA), 2 BF16 (K = 16), 3 BF16 at N = 64, 4 BF16 at N = 64 with A
+// reuse; `mmas` instructions per CTA (a multiple of 4).
 __global__ void __launch_bounds__(128, 1) k_peak_mma(int kind, int mmas, int *err) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t done;
@@ -64,16 +87,33 @@ __global__ void __launch_bounds__(128, 1) k_peak_mma(int kind, int mmas, int *er
   const uint32_t tmem = tmem_sh;
   if (threadIdx.x == 0) {
     const uint32_t a = tc::smem_u32(smem), b = a + kPA;
-    const int nn = kind == 3 ? 64 : kPN;
+    const int nn = kind >= 3 ? 64 : kPN;
     const uint32_t id = kind == 1 ? tc::idesc_tf32(kPM, kPN) : tc::idesc_bf16(kPM, nn);
-    for (int i = 0; i < mmas; ++i) {
-      const uint32_t k = (uint32_t)(i & 3) * 32;  // the four 32-byte K steps of the row
-      const uint64_t ad = tc::desc_sw128(a + k), bd = tc::desc_sw128(b + k);
-      const uint32_t d = tmem + (uint32_t)((i & 1) * kPN);
-      if (kind == 1)
-        tc::mma_tf32(d, ad, bd, id, i >= 2 ? 1u : 0u);
-      else
-        tc::mma_bf16(d, ad, bd, id, i >= 2 ? 1u : 0u);
+    if (kind == 4) {
+      // A fixed over four MMAs, B the four 64-row quarters of the B tile; K step per group
+      for (int i = 0; i < mmas; i += 4) {
+        const uint32_t k = (uint32_t)((i >> 2) & 3) * 32;
+        const uint64_t ad = tc::desc_sw128(a + k);
+        const uint32_t d = tmem + (uint32_t)(((i >> 2) & 1) * kPN);
+        const uint32_t acc = i >= 8 ? 1u : 0u;
+        mma_n64_areuse(d, ad, tc::desc_sw128(b + k), id, acc, 1);
+        mma_n64_areuse(d + 64, ad, tc::desc_sw128(b + 8192 + k), id, acc, 2);
+        mma_n64_areuse(d + 128, ad, tc::desc_sw128(b + 16384 + k), id, acc, 2);
+        mma_n64_areuse(d + 192, ad, tc::desc_sw128(b + 24576 + k), id, acc, 3);
+      }
+    } else {
+      // consecutive MMAs go to different accumulators (2 of 256 columns, or 8 of 64 at
+      // N = 64), so no MMA waits for its predecessor's result
+      const int nacc = kind == 3 ? 8 : 2;
+      for (int i = 0; i < mmas; ++i) {
+        const uint32_t k = (uint32_t)(i & 3) * 32;  // the four 32-byte K steps of the row
+        const uint64_t ad = tc::desc_sw128(a + k), bd = tc::desc_sw128(b + k);
+        const uint32_t d = tmem + (uint32_t)((i % nacc) * (512 / nacc));
+        if (kind == 1)
+          tc::mma_tf32(d, ad, bd, id, i >= nacc ? 1u : 0u);
+        else
+          tc::mma_bf16(d, ad, bd, id, i >= nacc ? 1u : 0u);
+      }
     }
     tc::mma_commit(&done);
     if (!tc::mbar_wait(&done, 0)) atomicExch(err, 1);
@@ -92,7 +132,7 @@ __global__ void __launch_bounds__(128, 1) k_peak_mma(int kind, int mmas, int *er
 using namespace opevo;
 
 extern "C" op_status op_peak_rate(int kind, double *tflops, void *stream) {
-  if (!tflops || kind < OP_PEAK_FP64_FMA || kind > OP_PEAK_BF16_MMA_N64) {
+  if (!tflops || kind < OP_PEAK_FP64_FMA || kind > OP_PEAK_BF16_MMA_N64_AREUSE) {
     set_error("op_peak_rate: bad kind %d or null output", kind);
     return OP_ERR_ARG;
   }
@@ -118,8 +158,8 @@ extern "C" op_status op_peak_rate(int kind, double *tflops, void *stream) {
       const int mmas = 1 << 15;
       cudaFuncSetAttribute(k_peak_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeakSmem);
       k_peak_mma<<<sms, 128, kPeakSmem, st>>>(
-          kind == OP_PEAK_TF32_MMA ? 1 : (kind == OP_PEAK_BF16_MMA ? 2 : 3), mmas, err);
-      flops = 2.0 * kPM * (kind == OP_PEAK_BF16_MMA_N64 ? 64 : kPN) *
+          kind == OP_PEAK_TF32_MMA ? 1 : (kind == OP_PEAK_BF16_MMA ? 2 : kind), mmas, err);
+      flops = 2.0 * kPM * (kind >= OP_PEAK_BF16_MMA_N64 ? 64 : kPN) *
               (kind == OP_PEAK_TF32_MMA ? 8 : 16) * (double)mmas * sms;
     }
     count_launch();

@@ -772,28 +772,30 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
 // ---- mixed-precision Step 1 (FP64 iterative refinement around an FP32 CG) -------------
 namespace {
 
-// scale[j] = ||r_j|| for the active columns (0 otherwise), from the init finaliser's state.
+// scale[j] = ||r_j|| for the active columns (0 otherwise), from the init finaliser's state;
+// inv[j] = 1 / scale[j] in FP32 (0 for inactive columns).
 __global__ void k_ref_scale(int ld, const double *__restrict__ state, const int *__restrict__ active,
-                            double *__restrict__ scale) {
+                            double *__restrict__ scale, float *__restrict__ inv) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < ld) scale[j] = active[j] ? sqrt(state[j]) : 0.0;
+  if (j >= ld) return;
+  const double sc = active[j] ? sqrt(state[j]) : 0.0;
+  scale[j] = sc;
+  inv[j] = sc > 0.0 ? (float)(1.0 / sc) : 0.f;
 }
 
-// r32 = R / scale (column-wise; zero for inactive columns); four elements per thread.
+// r32 = R / scale (column-wise; zero for inactive columns), four elements per thread.  The
+// right-hand side of the FP32 solve only needs FP32 accuracy: an FP32 product with the
+// reciprocal (no FP64 division per element).
 __global__ void k_ref_rhs(long long total, int ld, const double *__restrict__ R,
-                          const double *__restrict__ scale, float *__restrict__ r32) {
+                          const float *__restrict__ inv, float *__restrict__ r32) {
   for (long long e = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x); e < total;
        e += 4 * (long long)gridDim.x * blockDim.x) {
     const int j = (int)(e % ld);
     const double2 a = *reinterpret_cast<const double2 *>(R + e);
     const double2 b = *reinterpret_cast<const double2 *>(R + e + 2);
-    float4 o;
-    const double s0 = scale[j], s1 = scale[j + 1], s2 = scale[j + 2], s3 = scale[j + 3];
-    o.x = s0 > 0.0 ? (float)(a.x / s0) : 0.f;
-    o.y = s1 > 0.0 ? (float)(a.y / s1) : 0.f;
-    o.z = s2 > 0.0 ? (float)(b.x / s2) : 0.f;
-    o.w = s3 > 0.0 ? (float)(b.y / s3) : 0.f;
-    *reinterpret_cast<float4 *>(r32 + e) = o;
+    const float4 w = *reinterpret_cast<const float4 *>(inv + j);
+    *reinterpret_cast<float4 *>(r32 + e) =
+        make_float4((float)a.x * w.x, (float)a.y * w.y, (float)b.x * w.z, (float)b.y * w.w);
   }
 }
 
@@ -861,9 +863,10 @@ op_status cg_refine(const Geom &g, const double *Vt, const float *Vt32, double s
     double eta = rho > 0.0 ? 0.3 * rtol / rho : 0.5;
     eta = std::min(0.5, std::max(eta, 2e-6));
     prof_begin(w64.prof, PK_REFINE, st);
-    k_ref_scale<<<(ld + 255) / 256, 256, 0, st>>>(ld, w64.state, w64.active, scale);
+    float *inv = (float *)(scale + ld);
+    k_ref_scale<<<(ld + 255) / 256, 256, 0, st>>>(ld, w64.state, w64.active, scale, inv);
     count_launch();
-    k_ref_rhs<<<eb, 256, 0, st>>>(total, ld, R, scale, r32);
+    k_ref_rhs<<<eb, 256, 0, st>>>(total, ld, R, inv, r32);
     count_launch();
     OP_CUDA(cudaMemsetAsync(d32, 0, (size_t)total * sizeof(float), st));
     prof_end(w64.prof, st);

@@ -496,23 +496,25 @@ op_status tma_map_2d_f32_sw128(CUtensorMap *map, const void *base, uint64_t inne
   return OP_OK;
 }
 
-op_status tma_map_3d_bf16_sw64(CUtensorMap *map, const void *base, uint64_t inner,
-                               uint64_t rows, uint64_t planes, uint32_t box_rows) {
+op_status tma_map_3d_bf16_sw(CUtensorMap *map, const void *base, uint64_t inner,
+                             uint64_t rows, uint64_t planes, uint32_t box_rows, uint32_t box_k) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return OP_ERR_CUDA;
   }
-  if (((uintptr_t)base & 15) != 0 || (inner * 2) % 16 != 0 || box_rows < 1 || box_rows > 256) {
+  if (((uintptr_t)base & 15) != 0 || (inner * 2) % 16 != 0 || box_rows < 1 || box_rows > 256 ||
+      (box_k != 16 && box_k != 32)) {
     set_error("tensor map: base or row pitch not 16-byte aligned, or bad box");
     return OP_ERR_ARG;
   }
   cuuint64_t gd[3] = {inner, rows, planes};
   cuuint64_t gs[2] = {inner * 2, inner * rows * 2};
-  cuuint32_t bx[3] = {32, box_rows, 1};
+  cuuint32_t bx[3] = {box_k, box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), gd, gs, bx,
-                  es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                  es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  box_k == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);

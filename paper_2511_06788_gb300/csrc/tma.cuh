@@ -31,12 +31,13 @@ op_status tma_map_2d_f32_sw128(CUtensorMap *map, const void *base, uint64_t inne
                                uint32_t box_outer);
 
 // 3-D BF16 tensor map over [planes][rows][inner] (inner contiguous, a multiple of 8
-// elements) with a box of 32 x box_rows x 1 elements landing in the 64-byte-swizzled
-// K-major layout (rows of 64 bytes, 16-byte chunk c of row r at chunk c ^ ((r / 2) % 4)
-// within each 512-byte group of 8 rows).  Destinations must be 1024-byte aligned and
-// every inner coordinate a multiple of 8.
-op_status tma_map_3d_bf16_sw64(CUtensorMap *map, const void *base, uint64_t inner,
-                               uint64_t rows, uint64_t planes, uint32_t box_rows);
+// elements) with a box of box_k x box_rows x 1 elements, box_k = 32 or 16, landing in the
+// K-major layout swizzled over rows of 2 box_k bytes (64- or 32-byte swizzle: 16-byte
+// chunk c of row r at chunk c ^ ((r / 2) % 4), resp. c ^ ((r / 4) % 2), within each group
+// of 8 rows).  Destinations must be 1024-byte aligned and every inner coordinate a
+// multiple of 8.
+op_status tma_map_3d_bf16_sw(CUtensorMap *map, const void *base, uint64_t inner,
+                             uint64_t rows, uint64_t planes, uint32_t box_rows, uint32_t box_k);
 
 namespace tma {
 
