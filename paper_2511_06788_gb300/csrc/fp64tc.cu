@@ -574,8 +574,17 @@ __global__ void k_colexp(const double *__restrict__ U, const double *__restrict_
   const long long per = (m + gridDim.y - 1) / gridDim.y;
   const long long r0 = (long long)blockIdx.y * per;
   const long long r1 = r0 + per < m ? r0 + per : m;
-  double mx = 0.0;
-  for (long long r = r0; r < r1; ++r) mx = fmax(mx, fabs(X[(x0 + r) * ld + cc]));
+  const double *col = X + x0 * ld + cc;
+  double mx = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+  long long r = r0;
+  for (; r + 4 <= r1; r += 4) {  // four independent loads in flight per thread
+    mx = fmax(mx, fabs(col[r * ld]));
+    m1 = fmax(m1, fabs(col[(r + 1) * ld]));
+    m2 = fmax(m2, fabs(col[(r + 2) * ld]));
+    m3 = fmax(m3, fabs(col[(r + 3) * ld]));
+  }
+  for (; r < r1; ++r) mx = fmax(mx, fabs(col[r * ld]));
+  mx = fmax(fmax(mx, m1), fmax(m2, m3));
   if (mx > 0.0) atomicMax(enc + c, exponent_of(mx) + 4096);
 }
 
