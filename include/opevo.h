@@ -266,7 +266,10 @@ op_status op_profile_read(op_ctx *ctx, int kind, double *total_ms, long long *la
 
 /* Checkpoint / resume.  The paper has no counterpart; the scheme is a one-step map,
  * so a context restored from a checkpoint continues bit-identically: the state is
- * U, the Step-1 warm start W, sigma, tau and the step statistics.
+ * U, the Step-1 warm start W, sigma, tau and the step statistics, and for FP64 contexts
+ * with the mixed-precision Step 1 also the block before the last update (the next
+ * Step 1 starts from that block's residual carried over the update, which restore
+ * rebuilds).
  * op_checkpoint_size: bytes of a checkpoint of ctx (0 for NULL).
  * op_checkpoint: writes the state into caller-owned host memory buf (len >= size).
  * op_restore: loads a state written by op_checkpoint into a context of the same

@@ -238,8 +238,14 @@ op_status update_fp64(op_ctx *c, const double *U, const double *W, const double 
 
 // Step 1 for the context: CG in the block precision, or (FP64 contexts) iterative
 // refinement around an FP32 CG.
+// recycle (step_impl): the first residual may be carried over from the last step;
+// *fresh: the refinement's R block now holds U - (H + sigma) W formed by the stencil.
 template <typename T>
-op_status solve_step1(op_ctx *c, const T *U, T *W, double rtol, int max_iter, int *iters) {
+op_status solve_step1(op_ctx *c, const T *U, T *W, double rtol, int max_iter, int *iters,
+                      bool recycle = false, bool *fresh = nullptr) {
+  const bool carry = recycle && c->rec_ok;
+  c->rec_ok = false;
+  if (fresh) *fresh = false;
   if constexpr (std::is_same<T, double>::value) {
     if (c->refine) {
       c->cgw32.Q = c->U2;  // the update's output block is free during Step 1
@@ -247,7 +253,7 @@ op_status solve_step1(op_ctx *c, const T *U, T *W, double rtol, int max_iter, in
       return cg_refine(c->g, (const double *)c->Vt, c->Vt32, c->sigma, U, W, c->p, c->ld, rtol,
                        max_iter, c->cgw, c->cgw32, (float *)c->cgw.P,
                        (float *)c->cgw.P + (size_t)c->n * c->ld, c->ref_scale, iters, &cycles,
-                       c->st);
+                       c->st, carry ? (const double *)c->U2 : nullptr, fresh);
     }
   }
   return cg_solve<T>(c->g, (const T *)c->Vt, c->sigma, U, W, c->p, c->ld, rtol, max_iter, c->cgw,
@@ -257,6 +263,7 @@ op_status solve_step1(op_ctx *c, const T *U, T *W, double rtol, int max_iter, in
 template <typename T> op_status step_impl(op_ctx *c) {
   NvtxRange step_range("opevo step");
   int iters = 0;
+  bool fresh = false;  // Step 1 left a stencil-formed residual for the next step
   if (c->pb.flow == OP_FLOW_L2) {
     // the L2 gradient flow: W = -(H + sigma) U
     NvtxRange r("step 1: W = -(H + sigma) U");
@@ -268,7 +275,7 @@ template <typename T> op_status step_impl(op_ctx *c) {
     // Step 1: W = (H + sigma)^-1 U, warm-started from the previous W
     NvtxRange r("step 1: CG");
     OP_TRY(solve_step1<T>(c, (const T *)c->U, (T *)c->W, cg_rtol_for(c), cg_max_iter(c),
-                          &iters));
+                          &iters, true, &fresh));
   }
   NvtxRange r_rest("Grams, core, update, energy");
   // inner matrices <W,U>, <W,W>, <U,U>
@@ -343,11 +350,14 @@ template <typename T> op_status step_impl(op_ctx *c) {
   c->stats.steps += 1;
   c->stats.last_cg_iters = iters;
   c->stats.cg_iters += iters;
+  // the step is complete: U2 holds the block before the update, R its residual with W
+  c->rec_ok = fresh;
   return OP_OK;
 }
 
 // r = ||H U - U Theta||_F / (||H + sigma||_G sqrt(p)), Theta = U^T H U.
 template <typename T> op_status residual_impl(op_ctx *c, double *r) {
+  if (c) c->rec_ok = false;  // its scratch or its result replaces a carried residual
   T *Y = (T *)c->cgw.Q, *Z = (T *)c->cgw.R;
   prof_begin(&c->prof, PK_RESIDUAL, c->st);
   OP_TRY(launch_apply<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, Y, c->ld, c->st));
@@ -377,6 +387,7 @@ template <typename T> op_status residual_impl(op_ctx *c, double *r) {
 }
 
 template <typename T> op_status eig_impl(op_ctx *c, double *lam, int kind) {
+  if (c) c->rec_ok = false;  // its scratch or its result replaces a carried residual
   if (kind == OP_EIG_RITZ) {
     T *Y = (T *)c->cgw.Q;
     OP_TRY(launch_apply<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, Y, c->ld, c->st));
@@ -420,6 +431,7 @@ op_status cholqr_check(op_ctx *c) {
 // mode: the midpoint scheme preserves U^T U, so the orthogonality error U0 starts
 // with stays for the whole run (an FP32 Cholesky-QR gave 1e-5 at p = 1024).
 template <typename T> op_status orthonormalise_impl(op_ctx *c, const double *U0_dev) {
+  if (c) c->rec_ok = false;  // its scratch or its result replaces a carried residual
   const size_t blk = (size_t)c->n * c->ld * sizeof(double);
   const size_t gbytes = gram_workspace_bytes(c->n, c->ld, 8);
   void *A64 = nullptr, *Q64 = nullptr, *gws = nullptr, *tc_tmp = nullptr;
@@ -498,6 +510,7 @@ template <typename T> op_status orthonormalise_impl(op_ctx *c, const double *U0_
 
 template <typename T>
 op_status init_impl(op_ctx *c, const double *V, const double *U0, bool device) {
+  if (c) c->rec_ok = false;  // its scratch or its result replaces a carried residual
   const long long n = c->n;
   const int ld = c->ld;
   const size_t blk = (size_t)n * ld * sizeof(T);
@@ -778,6 +791,7 @@ op_status init_seeded(op_ctx **out, const op_problem *pb, const double *V,
 // sigma ~ lambda_p - 2 lambda_1.  Changes below 10 % are skipped.  The previous
 // sigma and tau are returned for the energy guard.  Synchronises the context's stream.
 op_status opevo::retune_shift(op_ctx *c, double *prev_sigma, double *prev_tau) {
+  if (c) c->rec_ok = false;  // its scratch or its result replaces a carried residual
   std::vector<double> lam(c->p);
   OP_TRY(c->prec == OP_FP64 ? eig_impl<double>(c, lam.data(), OP_EIG_RITZ)
                             : eig_impl<float>(c, lam.data(), OP_EIG_RITZ));
@@ -905,19 +919,23 @@ op_status op_solve(op_ctx *c, double tol, int max_steps, int stop, op_stats *st)
 
 namespace {
 struct CkptHeader {
-  char magic[8];  // "OPEVOCK1"
+  char magic[8];  // "OPEVOCK2"
   long long n;
   int p, ld, prec, elem;
   double sigma, tau, sigma0, Lb, E, g_rel;
   int adapt_off, expect_iters;
+  int carried;  // the block before the last update follows W (the carried residual's U)
   op_stats stats;
 };
-const char kCkptMagic[8] = {'O', 'P', 'E', 'V', 'O', 'C', 'K', '1'};
+const char kCkptMagic[8] = {'O', 'P', 'E', 'V', 'O', 'C', 'K', '2'};
+// blocks of a checkpoint: U, W, and with the mixed-precision Step 1 the block before the
+// last update, from which restore rebuilds the residual the next Step 1 starts from
+int ckpt_blocks(const op_ctx *c) { return c->refine ? 3 : 2; }
 }  // namespace
 
 size_t op_checkpoint_size(const op_ctx *c) {
   if (!c) return 0;
-  return sizeof(CkptHeader) + 2 * (size_t)c->n * c->ld * c->elem;
+  return sizeof(CkptHeader) + ckpt_blocks(c) * (size_t)c->n * c->ld * c->elem;
 }
 
 op_status op_checkpoint(op_ctx *c, void *buf, size_t len) {
@@ -941,12 +959,15 @@ op_status op_checkpoint(op_ctx *c, void *buf, size_t len) {
   h.g_rel = c->g_rel;
   h.adapt_off = c->adapt_off;
   h.expect_iters = c->cgw.expect_iters;
+  h.carried = c->rec_ok ? 1 : 0;
   h.stats = c->stats;
   const size_t blk = (size_t)c->n * c->ld * c->elem;
   char *out = (char *)buf;
   memcpy(out, &h, sizeof(h));
   OP_CUDA(cudaMemcpyAsync(out + sizeof(h), c->U, blk, cudaMemcpyDeviceToHost, c->st));
   OP_CUDA(cudaMemcpyAsync(out + sizeof(h) + blk, c->W, blk, cudaMemcpyDeviceToHost, c->st));
+  if (ckpt_blocks(c) > 2)
+    OP_CUDA(cudaMemcpyAsync(out + sizeof(h) + 2 * blk, c->U2, blk, cudaMemcpyDeviceToHost, c->st));
   OP_CUDA(cudaStreamSynchronize(c->st));
   return OP_OK;
 }
@@ -967,6 +988,14 @@ op_status op_restore(op_ctx *c, const void *buf, size_t len) {
   const char *in = (const char *)buf;
   OP_CUDA(cudaMemcpyAsync(c->U, in + sizeof(h), blk, cudaMemcpyHostToDevice, c->st));
   OP_CUDA(cudaMemcpyAsync(c->W, in + sizeof(h) + blk, blk, cudaMemcpyHostToDevice, c->st));
+  c->rec_ok = false;
+  if (ckpt_blocks(c) > 2 && h.carried) {
+    // the carried residual: the same values the checkpointed context held
+    OP_CUDA(cudaMemcpyAsync(c->U2, in + sizeof(h) + 2 * blk, blk, cudaMemcpyHostToDevice, c->st));
+    OP_TRY(refine_residual(c->g, (const double *)c->Vt, h.sigma, (const double *)c->U2,
+                           (const double *)c->W, c->ld, c->cgw, c->st));
+    c->rec_ok = true;
+  }
   OP_CUDA(cudaStreamSynchronize(c->st));
   c->sigma = h.sigma;
   c->tau = h.tau;
@@ -991,6 +1020,7 @@ op_status op_energy(op_ctx *c, double *E) {
 }
 
 op_status op_get_U(op_ctx *c, double *U_host) {
+  if (c) c->rec_ok = false;  // its scratch or its result replaces a carried residual
   if (!c || !U_host) {
     set_error("op_get_U: null argument");
     return OP_ERR_ARG;

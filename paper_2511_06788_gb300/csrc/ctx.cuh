@@ -33,6 +33,10 @@ struct op_ctx {
   // FP64 contexts with the mixed-precision Step 1: V in FP32, the FP32 CG's scratch (its
   // blocks alias the FP64 CG blocks Q and U2, its rhs and solution the FP64 block P)
   bool refine;
+  // the refinement's R block holds U2 - (H + sigma) W, formed by the stencil at the end of
+  // the last step (U2: the block before that step's update): the next Step 1 may start
+  // from R + U - U2.  Cleared by every call that writes R, U2, W or sigma otherwise.
+  bool rec_ok;
   float *Vt32;
   CGWork cgw32;
   double *ref_scale;

@@ -151,12 +151,21 @@ op_status cg_solve(const Geom &g, const T *Vt, double sigma, const T *U, T *W, i
 // (H + sigma) d = r_j / ||r_j|| by the FP32 CG of w32 (V in FP32: Vt32; rhs r32, solution
 // d32: n x ld FP32 blocks) to a relative tolerance that the cycle needs, and adds
 // ||r_j|| d_j to W in FP64.  scale: ld doubles plus ld floats of device scratch (16-byte
-// aligned).  *iters: FP32 CG
-// iterations of all cycles; *cycles: FP64 residual evaluations.
+// aligned).  *iters: FP32 CG iterations of all cycles; *cycles: FP64 residual evaluations.
+// Uprev (may be null): the block U was before the last update while w64's R block still
+// holds Uprev - (H + sigma) W for the current W and sigma; the first residual is then
+// R + U - Uprev, one pass over three blocks instead of a stencil apply.  *fresh (may be
+// null): whether the residual left in w64's R was formed by the stencil.
 op_status cg_refine(const Geom &g, const double *Vt, const float *Vt32, double sigma,
                     const double *U, double *W, int p, int ld, double rtol, int max_iter,
                     CGWork &w64, CGWork &w32, float *r32, float *d32, double *scale, int *iters,
-                    int *cycles, cudaStream_t st);
+                    int *cycles, cudaStream_t st, const double *Uprev = nullptr,
+                    bool *fresh = nullptr);
+
+// w64's R block = U - (H + sigma) W, element by element as the refinement forms it (the
+// same values whatever the launch shape); used to rebuild a carried residual on restore.
+op_status refine_residual(const Geom &g, const double *Vt, double sigma, const double *U,
+                          const double *W, int ld, CGWork &w64, cudaStream_t st);
 
 // FP32 CG direction kernel on 3-D grids with TMA-staged stencil planes (stencil_tma.cu).
 struct CgTmaGeom {

@@ -245,6 +245,36 @@ __global__ void __launch_bounds__(256) k_cg_init(Geom g, const T *__restrict__ V
   block_colsum<T, NC>(acc, ld, part);
 }
 
+// R = R + U - Uprev (the residual of the block before an update, carried to the block
+// after it with the same W: U - (H+sigma) W = (Uprev - (H+sigma) W) + (U - Uprev));
+// part[b][.][j] = R_j.R_j, U_j.U_j.  Resets the control words as k_cg_init does.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ref_recycle(long long n, const T *__restrict__ U,
+                                                     const T *__restrict__ Uprev,
+                                                     T *__restrict__ R, int ld,
+                                                     double *__restrict__ part, int *ctl) {
+  ROW_PROLOGUE(n)
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    ctl[1] = 0;
+    ctl[2] = 0;
+    ctl[3] = 0;
+  }
+  T acc[2][N] = {};
+  for (long long i = i0; i < n; i += istep) {
+    const long long o = i * (long long)ld + col;
+    const Pack<T> u = Pack<T>::load(U + o), up = Pack<T>::load(Uprev + o);
+    Pack<T> r = Pack<T>::load(R + o);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      r.v[k] += u.v[k] - up.v[k];
+      acc[0][k] += r.v[k] * r.v[k];
+      acc[1][k] += u.v[k] * u.v[k];
+    }
+    r.store(R + o);
+  }
+  block_colsum<T, 2>(acc, ld, part);
+}
+
 // ---- three-kernel iteration (FP64: no arithmetic is recomputed) -----------------
 // Q = (H+sigma) P; part[b][0][j] = P_j . Q_j.
 template <typename T>
@@ -819,10 +849,21 @@ __global__ void k_ref_correct(long long total, int ld, const float *__restrict__
 
 }  // namespace
 
+op_status refine_residual(const Geom &g, const double *Vt, double sigma, const double *U,
+                          const double *W, int ld, CGWork &w64, cudaStream_t st) {
+  RowShape s = row_shape(ld, Pack<double>::N);
+  const int nb = grid_blocks(g.n, s.rows);
+  k_cg_init<double, false, false><<<dim3(nb, s.gy), s.block, 0, st>>>(
+      g, Vt, g.cdiag + sigma, U, W, (double *)w64.R, nullptr, ld, w64.part, w64.ctl);
+  count_launch();
+  OP_LAUNCH("refine_residual");
+  return OP_OK;
+}
+
 op_status cg_refine(const Geom &g, const double *Vt, const float *Vt32, double sigma,
                     const double *U, double *W, int p, int ld, double rtol, int max_iter,
                     CGWork &w64, CGWork &w32, float *r32, float *d32, double *scale, int *iters,
-                    int *cycles, cudaStream_t st) {
+                    int *cycles, cudaStream_t st, const double *Uprev, bool *fresh) {
   RowShape s = row_shape(ld, Pack<double>::N);
   const int nb = grid_blocks(g.n, s.rows);
   const dim3 grid(nb, s.gy);
@@ -838,8 +879,11 @@ op_status cg_refine(const Geom &g, const double *Vt, const float *Vt32, double s
   for (; cyc < 12; ++cyc) {
     prof_begin(w64.prof, PK_REFINE, st);
     // R = U - (H + sigma) W and the column norms; active columns: ||r_j|| > rtol ||u_j||
-    k_cg_init<double, false, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, nullptr, ld,
-                                                             w64.part, w64.ctl);
+    if (cyc == 0 && Uprev)
+      k_ref_recycle<double><<<grid, s.block, 0, st>>>(g.n, U, Uprev, R, ld, w64.part, w64.ctl);
+    else
+      k_cg_init<double, false, false><<<grid, s.block, 0, st>>>(g, Vt, sg, U, W, R, nullptr, ld,
+                                                               w64.part, w64.ctl);
     count_launch();
     k_cg_fin_init<<<fb, 256, 0, st>>>(w64.part, nb, 2, ld, p, rtol * rtol, w64.state, w64.active,
                                       w64.ctl);
@@ -882,6 +926,7 @@ op_status cg_refine(const Geom &g, const double *Vt, const float *Vt32, double s
   }
   *iters = inner;
   *cycles = cyc + 1;
+  if (fresh) *fresh = cyc > 0 || !Uprev;
   return OP_OK;
 }
 

@@ -83,7 +83,9 @@ def test_g_residual_and_orthogonality_of_a_non_orthonormal_U(problem, prec):
         sigma = s.stats()["sigma"]
         buf = s.checkpoint()
         elem = 8 if prec == "fp64" else 4
-        hdr = buf.size - 2 * n * ld * elem
+        # the header, then U (then W, and for FP64 contexts the block before the last
+        # update); the header is shorter than a block
+        hdr = buf.size % (n * ld * elem)
         dt = np.float64 if prec == "fp64" else np.float32
         Ublk = buf[hdr:hdr + n * ld * elem].view(dt).reshape(n, ld)
         rng = np.random.default_rng(4)
