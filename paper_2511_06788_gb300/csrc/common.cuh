@@ -107,10 +107,15 @@ struct RowShape {
   int rows;    // rows per block
   int gy;      // column chunks
 };
+// Blocks of the row kernels: up to kRowChunk vectors of a row (512 bytes) by as many rows
+// as make 256 threads; wider blocks go as column chunks (grid.y), each chunk's CTAs
+// resident together and sweeping the grid points in order, so that the rows a stencil
+// reads one z plane away are still in L2 (a z plane of one chunk: nx ny 512 bytes).
+constexpr int kRowChunk = 32;
 inline RowShape row_shape(int ld, int vec) {
   RowShape s;
   s.nv = ld / vec;
-  int bx = s.nv < 256 ? s.nv : 256;
+  int bx = s.nv < kRowChunk ? s.nv : kRowChunk;
   int by = 256 / bx;
   if (by < 1) by = 1;
   s.block = dim3(bx, by, 1);
