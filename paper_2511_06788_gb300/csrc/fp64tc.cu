@@ -84,7 +84,12 @@ static_assert(kKS == 16 || kKS == 32, "K slab of one or two MMA K steps");
 static_assert(ring_stages<8>() >= 2, "ring of at least two stages");
 template <int ND> constexpr int smem_bytes() { return ring_stages<ND>() * stage_bytes<ND>() + 1024; }
 constexpr int kIssuers = 2;                // warps 1 .. kIssuers issue the MMAs
-constexpr int kDrainWarps = 8;
+#ifndef FP64TC_DRAIN_WARPS
+#define FP64TC_DRAIN_WARPS 8
+#endif
+constexpr int kDrainWarps = FP64TC_DRAIN_WARPS;   // 4 lane quarters x column groups
+constexpr int kDrainCols = 4 * kBN / kDrainWarps;  // output columns per drain thread
+static_assert(kDrainCols % 4 == 0 && kDrainCols >= 4, "drain column groups of four");
 constexpr int kThreads = 32 * (1 + kIssuers + kDrainWarps);  // warp 0 TMA, then MMA, drain
 constexpr uint32_t kTmemCols = 512;        // ND x 64 used
 constexpr uint32_t kIdesc = tc::idesc_bf16(kBM, kBN);
@@ -429,9 +434,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---- drain warps ---------------------------------------------------------------------
     const int q = warp & 3;                         // TMEM lane quarter this warp may read
-    const int half = (warp - kIssuers - 1) >> 2;    // output columns 32 half .. 32 half + 31
+    const int half = (warp - kIssuers - 1) >> 2;    // output columns kDrainCols half + ...
     const int row = q * 32 + lane;                  // tile row
-    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 32);
+    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * kDrainCols);
     long long chunk = 0;
     bool ok = true;
     for (long long pr = cid; pr < J.npairs && ok; pr += ncl) {
@@ -441,9 +446,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       decode_pair(J, pr, rank, &ra, &rb, &k0, &klen, &valid, &item);
       const long long nst = (klen + kKS - 1) / kKS;
       const long long nch = (nst + kChunkStages - 1) / kChunkStages;
-      long long hi[32], lo[32];
+      long long hi[kDrainCols], lo[kDrainCols];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
+      for (int j = 0; j < kDrainCols; ++j) hi[j] = lo[j] = 0;
       for (long long c = 0; c < nch; ++c, ++chunk) {
         if (!warp_wait(&accfull, (uint32_t)(chunk & 1), abort)) {
           ok = false;
@@ -451,7 +456,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc::tc_fence_after();
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
+        for (int g = 0; g < kDrainCols / 4; ++g) {
           uint32_t v[kLevels][4];
 #pragma unroll
           for (int l = 0; l < kLevels; ++l) tmem_ld4(tbase + (uint32_t)(l * kBN + g * 4), v[l]);
@@ -480,10 +485,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (J.mode == MODE_GRAM) {
         // rows and columns beyond nc hold zero digits (the loads past the planes read 0)
         const int ea = ra + row < J.nc ? J.ea[ra + row] : 0;
-        double *dst = J.part + (item * kBM + row) * kBN + half * 32;
+        double *dst = J.part + (item * kBM + row) * kBN + half * kDrainCols;
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-          const int cb = rb + half * 32 + j;
+        for (int j = 0; j < kDrainCols; j += 2) {
+          const int cb = rb + half * kDrainCols + j;
           const int eb0 = cb < J.nc ? J.eb[cb] : 0, eb1 = cb + 1 < J.nc ? J.eb[cb + 1] : 0;
           double2 o;
           o.x = ldexp(fma((double)hi[j], kHiW, (double)lo[j]), ea + eb0 + kShift);
@@ -495,8 +500,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (r < J.mrows) {
           const int ea = J.ea[r];
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            const int col = rb + half * 32 + j;
+          for (int j = 0; j < kDrainCols; j += 2) {
+            const int col = rb + half * kDrainCols + j;
             if (col < J.ld) {
               double2 o;
               o.x = ldexp(fma((double)hi[j], kHiW, (double)lo[j]), ea + J.eb[col] + kShift);
