@@ -785,6 +785,15 @@ def run_batch(args):
     ms = max_over_ranks(ms, dev, ws)
     value = job_value(units, args.steps, ws, ms)
     iters = [batch.stats(i)["last_cg_iters"] for i in range(len(probs))]
+    # the replay's own cost: every problem frozen (its kernels return at once), so a step is
+    # the launch of the same 65 grids and nothing else; a single persistent launch could
+    # save at most this
+    batch.solve(1e30, 2, stop=pkg.binding.OP_STOP_ERR_E, check_every=1, raise_on_max=False)
+    batch.step(3)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    batch.step(20)
+    frozen_ms = (time.perf_counter() - t0) * 1e3 / 20
     batch.close()
     # the same problems stepped one context at a time (per-problem launches)
     t0 = time.perf_counter()
@@ -804,6 +813,7 @@ def run_batch(args):
             "tiles": {"rows_per_item_and_gram_rows": None, "autotune_ms_per_step": tune_ms},
             "per_problem_loop": {"value": units / (loop_ms * 1e-3), "ms_per_step": loop_ms},
             "last_cg_iters_range": [min(iters), max(iters)], "gpu_launches": launches,
+            "replay_all_frozen_ms_per_step": frozen_ms,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
