@@ -986,6 +986,57 @@ def run_c3(args):
     return 0
 
 
+def run_net48(args):
+    """The warm-start network's forward pass (inference) and one training step at 48^3,
+    p = 64, widths (24, 48, 96), random parameters, with the forward convolutions on the
+    tensor cores (BF16, the default) and on FP32 CUDA cores; CUDA-event times (median of
+    5 after 2 warm-up calls) and the forward convolutions' flop rate."""
+    import torch
+
+    import paper_2511_06788_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    N, p, widths = 48, 64, (24, 48, 96)
+    P = syn.warm_start_problem(1, N=N, p=p)
+    V = torch.from_numpy(P.V).to(dev)
+    Us = torch.from_numpy(np.linalg.qr(syn.gaussian_block(3, P.n, p))[0]).to(dev, torch.float32)
+    # grid level of each of the 11 layers (the U-Net of include/opnet.h): 0 N, 1 N/2, 2 N/4
+    levels = (0, 0, 1, 1, 2, 2, 1, 1, 0, 0, 0)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[2]
+
+    out = {}
+    with pkg.Net(N, P.lo, P.hi, p, widths) as net:
+        layers = net.layers()
+        theta = syn.uniform_init(0, [(t * ci, t * ci * co, co) for t, ci, co in layers])
+        flops = sum(2.0 * (N >> lv) ** 3 * t * ci * co for lv, (t, ci, co) in zip(levels, layers))
+        for kind in ("bf16_tc", "fp32"):
+            net.set_conv(kind)
+            net.set_params(theta.astype(np.float32))
+            fwd = timed(lambda: net.forward(V))
+            trn = timed(lambda: net.train_step(V, Us, 1e-4, 0.1))
+            out[kind] = {"forward_ms": fwd, "train_step_ms": trn,
+                         "forward_conv_tflops": flops / (fwd * 1e-3) / 1e12}
+    print(json.dumps({"workload": "net48_p64_widths24-48-96", "forward_conv_flops": flops,
+                      "modes": out,
+                      "forward_speedup": out["fp32"]["forward_ms"] / out["bf16_tc"]["forward_ms"],
+                      "timing": "CUDA events, median of 5 after 2 warm-up calls; each call "
+                                "synchronises (opnet API)"}), flush=True)
+    return 0
+
+
 def run_warmstart(args):
     """Learned warm start on 48^3, p = 64 (V = 4-16 Gaussian wells, no harmonic term).
 
@@ -1191,7 +1242,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c3fp64",
                     choices=["c3fp64", "3d_wells_64", "batch64", "warmstart48", "ttr64",
-                             "batch64-ttr", "c3", "fp64tc_kernels"])
+                             "batch64-ttr", "c3", "fp64tc_kernels", "net48"])
     ap.add_argument("--ttr-legs", default="fp64,fp64_fma,fp32,mix_bf16x3",
                     help="modes timed to residual 1e-6 beside the default workload (or none)")
     ap.add_argument("--legs", default="fp32,mix_bf16x3,fp64_fma",
@@ -1232,6 +1283,8 @@ def main():
         return run_ours(args)
     if args.workload == "fp64tc_kernels":
         return run_fp64tc_kernels(args)
+    if args.workload == "net48":
+        return run_net48(args)
     return run_headline(args)
 
 

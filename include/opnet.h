@@ -50,8 +50,9 @@
  *
  * Parameters are updated by Adam (Kingma and Ba, 2015), FP32 master weights.
  *
- * Conventions: as opevo.h.  All compute is FP32 with FP32 accumulation inside
- * a layer; the loss's p x p algebra is FP64.  Device pointers are 16-byte
+ * Conventions: as opevo.h.  The forward convolutions run on the tensor cores with
+ * BF16 operands and FP32 accumulation (opnet_set_conv selects FP32 CUDA cores); the
+ * rest is FP32 with FP32 accumulation inside a layer; the loss's p x p algebra is FP64.  Device pointers are 16-byte
  * aligned and caller-owned.  Calls are ordered on the network's stream and
  * return after it has been synchronised, except where stated.
  */
@@ -88,6 +89,24 @@ op_status opnet_layer(const opnet *net, int i, int *taps, int *cin, int *cout);
  * resets the Adam moments and step counter. */
 op_status opnet_set_params(opnet *net, const float *theta_host, long long count);
 op_status opnet_get_params(opnet *net, float *theta_host, long long count);
+
+/* Arithmetic of the forward convolutions (the 11 layers of every forward pass, in
+ * inference and in training):
+ *   OPNET_CONV_BF16_TC  tcgen05 tensor cores, BF16 operands (activations and weights
+ *                       rounded to nearest), FP32 accumulation; the default;
+ *   OPNET_CONV_FP32     FP32 CUDA cores, FP32 accumulation.
+ * The backward pass is FP32 either way.  OP_ERR_ARG for a NULL net or another kind. */
+typedef enum { OPNET_CONV_FP32 = 0, OPNET_CONV_BF16_TC = 1 } opnet_conv_kind;
+op_status opnet_set_conv(opnet *net, int kind);
+
+/* One convolution layer on its own (the network's kernels, for kernel-level checks):
+ * Z = conv(X, W) + bias and A = silu(Z), X [N^3][cin], W [taps * cin][cout] (row-major,
+ * the parameter layout above), bias [cout] or NULL, Z and A [N^3][cout] (either may be
+ * NULL), all FP32 device arrays; taps 27 (3x3x3, zero padded) or 1; 1 <= cout <= 128,
+ * cin <= 512, N <= 512; X 16-byte aligned.  `kind` as opnet_set_conv.  Allocates and
+ * frees a small scratch and synchronises `stream` (cudaStream_t, may be NULL). */
+op_status opnet_conv(int kind, const float *X, int N, int taps, int cin, int cout,
+                     const float *W, const float *bias, float *Z, float *A, void *stream);
 
 /* Y = net(V): V is N^3 FP64 values (device), Y is N^3 x p FP32 (device, ld = p). */
 op_status opnet_forward(opnet *net, const double *V_dev, float *Y_dev);

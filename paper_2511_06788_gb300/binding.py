@@ -127,6 +127,8 @@ def lib():
         "opnet_layer": (i32, [vp, i32, P(i32), P(i32), P(i32)]),
         "opnet_set_params": (i32, [vp, P(C.c_float), C.c_longlong]),
         "opnet_get_params": (i32, [vp, P(C.c_float), C.c_longlong]),
+        "opnet_set_conv": (i32, [vp, i32]),
+        "opnet_conv": (i32, [i32, vp, i32, i32, i32, i32, vp, vp, vp, vp, vp]),
         "opnet_forward": (i32, [vp, vp, vp]),
         "opnet_infer": (i32, [vp, vp, vp]),
         "opnet_loss_grad": (i32, [vp, vp, vp, f64, P(f64), P(C.c_float), C.c_longlong]),
@@ -564,6 +566,22 @@ def update_fp64tc(U, W, KU, KW, p, out=None, stream=None):
     return out
 
 
+def net_conv(kind, X, N, taps, W, bias=None, stream=None):
+    """One layer of the network's convolution (opnet_conv): X (N^3 x cin) and W
+    (taps * cin x cout) float32 CUDA tensors, bias (cout) or None; returns (Z, A)."""
+    import torch
+    n, cin = X.shape
+    cout = W.shape[1]
+    Z = torch.empty(n, cout, dtype=torch.float32, device=X.device)
+    A = torch.empty_like(Z)
+    check(lib().opnet_conv(Net.CONV[kind], C.c_void_p(X.data_ptr()), int(N), int(taps), int(cin),
+                           int(cout), C.c_void_p(W.data_ptr()),
+                           C.c_void_p(bias.data_ptr() if bias is not None else 0),
+                           C.c_void_p(Z.data_ptr()), C.c_void_p(A.data_ptr()),
+                           _stream_ptr(stream)))
+    return Z, A
+
+
 class Net:
     """The learned warm start (include/opnet.h): a 3-level conv U-Net V -> Y (n x p).
 
@@ -600,6 +618,13 @@ class Net:
 
     def __exit__(self, *a):
         self.close()
+
+    CONV = {"fp32": 0, "bf16_tc": 1}
+
+    def set_conv(self, kind):
+        """Arithmetic of the forward convolutions: "bf16_tc" (tensor cores, the default) or
+        "fp32" (CUDA cores)."""
+        check(lib().opnet_set_conv(self._net, self.CONV[kind]))
 
     def layers(self):
         """[(taps, Cin, Cout)] of the 11 layers."""

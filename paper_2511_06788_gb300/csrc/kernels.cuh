@@ -167,6 +167,17 @@ op_status cg_refine(const Geom &g, const double *Vt, const float *Vt32, double s
 op_status refine_residual(const Geom &g, const double *Vt, double sigma, const double *U,
                           const double *W, int ld, CGWork &w64, cudaStream_t st);
 
+// Forward convolution of the learned warm start on the tensor cores (conv_tc.cu): X
+// [N^3][cin] FP32, W [taps * cin][cout] FP32 (taps 27: the 3x3x3 cross-correlation, zero
+// padded; taps 1: pointwise), BF16 operands with FP32 accumulation; Z = conv + bias and
+// A = silu(Z) ([N^3][cout] FP32, either may be null).  cout <= 128.  scratch: device memory
+// of conv_tc_scratch_bytes (the BF16 weights, K-major), 16-byte aligned; *err is set when a
+// bounded wait of the kernel gives up.
+size_t conv_tc_scratch_bytes(int taps, int cin, int cout);
+op_status conv_bf16_tc(const float *X, int N, int taps, int cin, int cout, const float *W,
+                       const float *bias, float *Z, float *A, void *scratch, size_t scratch_bytes,
+                       int *err, cudaStream_t st);
+
 // FP32 CG direction kernel on 3-D grids with TMA-staged stencil planes (stencil_tma.cu).
 struct CgTmaGeom {
   int nx, ny, nz, ld;

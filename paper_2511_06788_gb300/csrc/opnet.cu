@@ -15,6 +15,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -466,6 +467,10 @@ using namespace opevo;
 struct opnet {
   opnet_config cfg;
   int N, p, c0, c1, c2;
+  int conv_kind;         // OPNET_CONV_*: the forward convolutions' arithmetic
+  void *conv_ws;         // BF16 weights of the tensor-core convolution (one layer at a time)
+  size_t conv_ws_bytes;
+  int *dev_err;          // set when a bounded wait of a tensor-core kernel gives up
   long long n0, n1, n2;  // points at the three levels
   Layer L[kLayers];
   long long nparam;
@@ -532,6 +537,10 @@ op_status fwd_layer(opnet *net, int i, const float *X) {
   const Layer &l = net->L[i];
   const float *W = net->theta + l.woff;
   const float *b = W + (long long)l.taps * l.cin * l.cout;
+  if (net->conv_kind == OPNET_CONV_BF16_TC)
+    return conv_bf16_tc(X, l.grid, l.taps, l.cin, l.cout, W, b, net->Z[i],
+                        i == L_OUT ? nullptr : net->A[i], net->conv_ws, net->conv_ws_bytes,
+                        net->dev_err, net->st);
   return conv(net, X, l.grid, l.taps, l.cin, l.cout, W, b, net->Z[i],
               i == L_OUT ? nullptr : net->A[i]);
 }
@@ -675,9 +684,22 @@ op_status loss(opnet *net, const float *Us, double gamma, bool want_grad) {
   return OP_OK;
 }
 
+// After the stream has been synchronised: a tensor-core kernel that gave up a bounded wait.
+op_status check_dev_err(opnet *net) {
+  int h = 0;
+  OP_CUDA(cudaMemcpy(&h, net->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    OP_CUDA(cudaMemset(net->dev_err, 0, sizeof(int)));
+    set_error("opnet: a tensor-core convolution gave up a bounded device wait");
+    return OP_ERR_TIMEOUT;
+  }
+  return OP_OK;
+}
+
 op_status read_loss(opnet *net, double *out) {
   OP_CUDA(cudaMemcpyAsync(net->hsc, net->dsc, sizeof(double), cudaMemcpyDeviceToHost, net->st));
   OP_CUDA(cudaStreamSynchronize(net->st));
+  OP_TRY(check_dev_err(net));
   if (out) *out = net->hsc[0];
   if (!isfinite(net->hsc[0])) {
     set_error("opnet: non-finite loss");
@@ -779,10 +801,25 @@ op_status opnet_create(opnet **out, const opnet_config *cfg) {
   NET_ALLOC(net->dsc, 8);
   NET_ALLOC(net->KY, (long long)p * p);
   NET_ALLOC(net->KU, (long long)p * p);
+  NET_ALLOC(net->dev_err, 4);
 #undef NET_ALLOC
   if (s == OP_OK) {
     net->gram_bytes = gram_workspace_bytes(n0, p, 4);
     s = net_alloc(net, &net->gram_ws, net->gram_bytes);
+  }
+  if (s == OP_OK) {
+    // the tensor-core convolutions (the default): scratch for the widest layer's weights
+    net->conv_kind = OPNET_CONV_BF16_TC;
+    net->conv_ws_bytes = 0;
+    for (int i = 0; i < kLayers; ++i)
+      net->conv_ws_bytes = std::max(net->conv_ws_bytes,
+                                    conv_tc_scratch_bytes(net->L[i].taps, net->L[i].cin,
+                                                          net->L[i].cout));
+    s = net_alloc(net, &net->conv_ws, net->conv_ws_bytes);
+  }
+  if (s == OP_OK) {
+    const cudaError_t e = cudaMemsetAsync(net->dev_err, 0, 4 * sizeof(int), net->st);
+    if (e != cudaSuccess) s = cuda_status(e, "opnet_create: memset");
   }
   if (s == OP_OK && cudaMallocHost((void **)&net->hsc, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -855,7 +892,7 @@ op_status opnet_forward(opnet *net, const double *V, float *Y) {
   OP_CUDA(cudaMemcpyAsync(Y, net->Z[L_OUT], (size_t)net->n0 * net->p * sizeof(float),
                           cudaMemcpyDeviceToDevice, net->st));
   OP_CUDA(cudaStreamSynchronize(net->st));
-  return OP_OK;
+  return check_dev_err(net);
 }
 
 op_status opnet_infer(opnet *net, const double *V, double *U0) {
@@ -866,6 +903,62 @@ op_status opnet_infer(opnet *net, const double *V, double *U0) {
   OP_TRY(forward(net, V));
   OP_TRY(launch_unpad_to(net->n0, net->p, net->p, net->Z[L_OUT], 4, U0, 8, net->st));
   OP_CUDA(cudaStreamSynchronize(net->st));
+  return check_dev_err(net);
+}
+
+op_status opnet_conv(int kind, const float *X, int N, int taps, int cin, int cout,
+                     const float *W, const float *bias, float *Z, float *A, void *stream) {
+  if (!X || !W || (!Z && !A) || N < 1 || N > 512 || (taps != 1 && taps != 27) || cin < 1 ||
+      cin > 512 || cout < 1 || cout > 128 ||
+      (kind != OPNET_CONV_FP32 && kind != OPNET_CONV_BF16_TC)) {
+    set_error("opnet_conv: bad arguments");
+    return OP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (kind == OPNET_CONV_FP32) {
+    ConvArgs a;
+    a.X = X;
+    a.W = W;
+    a.bias = bias;
+    a.Z = Z;
+    a.A = A;
+    a.N = N;
+    a.taps = taps;
+    a.cin = cin;
+    a.cout = cout;
+    const long long n = (long long)N * N * N;
+    k_conv<<<dim3((unsigned)((n + CM - 1) / CM), (unsigned)((cout + CN - 1) / CN)), 256, 0, st>>>(a);
+    count_launch();
+    OP_LAUNCH("k_conv");
+    OP_CUDA(cudaStreamSynchronize(st));
+    return OP_OK;
+  }
+  const size_t wb = conv_tc_scratch_bytes(taps, cin, cout);
+  void *ws = nullptr;
+  OP_CUDA(cudaMalloc(&ws, wb + 256));
+  int *err = (int *)((char *)ws + wb);
+  auto ck = [](cudaError_t e, const char *what) {
+    return e == cudaSuccess ? OP_OK : cuda_status(e, what);
+  };
+  op_status s = ck(cudaMemsetAsync(err, 0, sizeof(int), st), "opnet_conv: memset");
+  if (s == OP_OK) s = conv_bf16_tc(X, N, taps, cin, cout, W, bias, Z, A, ws, wb, err, st);
+  int h = 0;
+  if (s == OP_OK) s = ck(cudaStreamSynchronize(st), "opnet_conv");
+  if (s == OP_OK) s = ck(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost), "opnet_conv");
+  cudaFree(ws);
+  if (s == OP_OK && h) {
+    set_error("opnet_conv: a bounded device wait gave up");
+    s = OP_ERR_TIMEOUT;
+  }
+  return s;
+}
+
+op_status opnet_set_conv(opnet *net, int kind) {
+  if (!net || (kind != OPNET_CONV_FP32 && kind != OPNET_CONV_BF16_TC)) {
+    set_error("opnet_set_conv: null net or unknown kind %d", kind);
+    return OP_ERR_ARG;
+  }
+  net->conv_kind = kind;
   return OP_OK;
 }
 

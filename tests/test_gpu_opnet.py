@@ -7,11 +7,17 @@
 - a network trained on blocks the scheme itself converged gives starting blocks
   from which the scheme needs fewer steps than from random ones.
 
-Tolerances.  The network runs in FP32 with FP32 accumulation over at most
-27 x 144 products per output and FP32 sums over at most 2048 points per
-weight-gradient partial (partials summed in FP64).  Forward outputs agree to a
-few 1e-6 of their scale; gradients, which pass through up to 22 such layers,
-to 1e-4 relative per layer.
+Tolerances.  With the FP32 convolutions (opnet_set_conv OPNET_CONV_FP32) the network
+runs in FP32 with FP32 accumulation over at most 27 x 144 products per output and FP32
+sums over at most 2048 points per weight-gradient partial (partials summed in FP64).
+Forward outputs agree to a few 1e-6 of their scale; gradients, which pass through up to
+22 such layers, to 1e-4 relative per layer.
+
+The tensor-core convolutions (the default) round activations and weights to BF16 and
+accumulate in FP32.  A layer is checked against the oracle's convolution of the
+BF16-rounded operands (then only the FP32 accumulation differs: K 2^-23 sum |x w| per
+output); a whole forward pass against the FP32 one (BF16 rounding, 2^-9 per operand,
+through 11 layers).
 """
 import numpy as np
 import pytest
@@ -30,11 +36,12 @@ DEV = torch.device("cuda:0")
 GAMMA = 0.1
 
 
-def setup(N, widths, p, seed=0):
+def setup(N, widths, p, seed=0, conv="fp32"):
     table = unet.layer_table(*widths, p)
     theta = syn.uniform_init(seed, unet.fans(table)).astype(np.float32).astype(np.float64)
     P = syn.warm_start_problem(seed + 5, N=N, p=p)
     net = pkg.Net(N, P.lo, P.hi, p, widths)
+    net.set_conv(conv)
     net.set_params(theta)
     V = torch.from_numpy(P.V).to(DEV)
     return net, theta, P, V
@@ -178,3 +185,58 @@ def test_trained_warm_start_beats_random_starts():
     assert np.all(rows[:, 1] < rows[:, 0]), rows          # every warm start has lower energy
     assert rows[:, 3].mean() < rows[:, 2].mean(), rows    # and gets within 1e-3 sooner
     net.close()
+
+
+def bf16(x):
+    """Round float32 values to BF16 (nearest, ties to even), returned as float64."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("N,taps,cin,cout", [(10, 27, 4, 24), (13, 27, 16, 8), (8, 27, 6, 128),
+                                             (9, 27, 144, 48), (11, 1, 48, 64), (4, 27, 96, 16)])
+def test_tensor_core_conv_layer_matches_oracle(N, taps, cin, cout):
+    rng = np.random.default_rng(N * 1000 + cin + cout)
+    n = N ** 3
+    X = rng.standard_normal((n, cin)).astype(np.float32)
+    W = (rng.standard_normal((taps * cin, cout)) / np.sqrt(taps * cin)).astype(np.float32)
+    b = rng.standard_normal(cout).astype(np.float32)
+    Z, A = pkg.binding.net_conv("bf16_tc", torch.from_numpy(X).to(DEV), N, taps,
+                                torch.from_numpy(W).to(DEV), torch.from_numpy(b).to(DEV))
+    Z, A = Z.double().cpu().numpy(), A.double().cpu().numpy()
+    Xr, Wr = bf16(X), bf16(W)
+    if taps == 27:
+        ref = unet.conv3(Xr, N, Wr.reshape(27, cin, cout), b.astype(np.float64))
+        mag = unet.conv3(np.abs(Xr), N, np.abs(Wr).reshape(27, cin, cout), np.abs(b))
+    else:
+        ref = Xr @ Wr + b
+        mag = np.abs(Xr) @ np.abs(Wr) + np.abs(b)
+    tol = (taps * cin + 2) * 2.0 ** -23 * mag + 1e-30
+    assert np.all(np.abs(Z - ref) <= tol), float((np.abs(Z - ref) / tol).max())
+    silu = ref / (1.0 + np.exp(-ref))
+    assert np.all(np.abs(A - silu) <= 2 * tol + 4 * 2.0 ** -24 * np.abs(silu))
+    # the operands really were rounded: the unrounded product differs by far more
+    if taps == 27:
+        exact = unet.conv3(X.astype(np.float64), N, W.astype(np.float64).reshape(27, cin, cout),
+                           b.astype(np.float64))
+        assert np.abs(exact - ref).max() > 100 * np.abs(Z - ref).max()
+
+
+def test_tensor_core_conv_rejects_bad_arguments():
+    X = torch.zeros(64, 8, device=DEV)
+    W = torch.zeros(27 * 8, 200, device=DEV)          # more than 128 output channels
+    with pytest.raises(pkg.OpError):
+        pkg.binding.net_conv("bf16_tc", X, 4, 27, W)
+
+
+def test_tensor_core_forward_close_to_fp32_forward():
+    N, widths, p = 16, (8, 16, 24), 16
+    net, theta, P, V = setup(N, widths, p, conv="bf16_tc")
+    Y_tc = net.forward(V).double().cpu().numpy()
+    net.set_conv("fp32")
+    Y_32 = net.forward(V).double().cpu().numpy()
+    net.close()
+    rel = np.linalg.norm(Y_tc - Y_32) / np.linalg.norm(Y_32)
+    # BF16 operand rounding (2^-9 relative) through 11 layers, not FP32-level agreement
+    assert 1e-5 < rel < 3e-2, rel
