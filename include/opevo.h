@@ -235,6 +235,38 @@ op_status op_step(op_ctx *ctx, int nsteps, op_stats *st);
  * OP_ERR_STATE if max_steps ran out first.  `st` may be NULL. */
 op_status op_solve(op_ctx *ctx, double tol, int max_steps, int stop, op_stats *st);
 
+/* Communication of row-sharded steps (op_step_sharded), counted over the call. */
+typedef struct {
+  int slabs;                 /* slabs the grid was split into                          */
+  long long halo_copies;     /* plane copies into a neighbour's halo                   */
+  long long halo_bytes;      /* bytes of those copies (n_plane x ld FP64 values each)   */
+  long long reductions;      /* sums over the slabs (the all-reduces of a multi-GPU run) */
+  long long reduction_bytes; /* FP64 bytes one slab contributes to them, summed         */
+} op_shard_stats;
+
+/* Advance `nsteps` time steps of an OP_FP64 context (G flow) with the grid split into
+ * `nslab` slabs of whole planes along its slowest axis (z in 3-D, y in 2-D; sizes differ
+ * by at most one plane), the row sharding a multi-GPU run would use.  The scheme needs no
+ * orthogonalisation (§1, Theorem 4.1), so the slabs exchange only
+ *   - one halo plane per face before each stencil apply: once per Step-1 CG iteration
+ *     (the direction block), once at the CG start (W) and once for the energy (U+), and
+ *   - sums over the slabs: three p-vectors at the CG start, two reductions of p and of
+ *     2p values per CG iteration, the three p x p inner matrices <W,U>, <W,W>, <U,U> per
+ *     step (Steps 2-3 of §4.1 are then computed once) and p values for the energy.
+ * Step 4 is local to each slab.  Step 1 is the FP64 block CG of the context's
+ * cg_precond (whatever `step1` selects), each column stopping at ||r_j|| <= rtol ||u_j||
+ * with the context's tolerance rule; the Gram and update use the context's fp64_gemm.
+ * The results equal op_step's up to the order of the sums.
+ * On this single-device library the slabs are buffers of their own on the context's
+ * device (allocated by the call: about 6 (n/nslab + 2 n_plane) x ld FP64 values per slab
+ * beside the context, freed on return), processed one after another on the context's
+ * stream; U and W are copied into the slabs at the start and back at the end, so the
+ * context continues with op_step or any other call.  `comm` (may be NULL) receives the
+ * exchanges the steps made.  OP_ERR_ARG for other precisions, the L2 flow, nslab outside
+ * 1 .. planes or nsteps < 0.  Synchronises once per CG iteration.  `st` may be NULL. */
+op_status op_step_sharded(op_ctx *ctx, int nslab, int nsteps, op_stats *st,
+                          op_shard_stats *comm);
+
 /* E(U) = 1/2 tr(U^T H U) (§2.2) of the current U, unshifted H. Synchronises. */
 op_status op_energy(op_ctx *ctx, double *E);
 

@@ -35,7 +35,7 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "grid_spacing", "hamiltonian", "spectrum_lower_bound", "default_sigma", "default_tau",
     "gershgorin_norm", "householder_orthonormalize", "cholesky_qr", "inner", "SourceSolver",
-    "block_cg", "block_pcg_jacobi", "core_matrices", "update", "scheme_step", "energy", "residuals",
+    "block_cg", "block_pcg_jacobi", "core_matrices", "core_from_inner", "update", "scheme_step", "energy", "residuals",
     "paper_eigenvalues", "ritz_values", "orth_error", "energy_lower_bound", "run",
     "RunResult", "step_coefficients", "midpoint_coefficients", "l2_flow_step",
     "cayley_coefficients",
@@ -241,10 +241,16 @@ def core_matrices(W: np.ndarray, U: np.ndarray, tau: float):
     Step 3: (tau/2) A = I - B + (tau/2) <GU,U> B.
     Returns (A, B, M) with M the Step-2 matrix (M - I is PSD by Lemma 3.1).
     """
-    p = U.shape[1]
-    I = np.eye(p)
-    C = inner(W, U)          # <GU, U>
-    S = inner(W, W)          # <GU, GU>
+    return core_from_inner(inner(W, U), inner(W, W), tau)
+
+
+def core_from_inner(C: np.ndarray, S: np.ndarray, tau: float):
+    """Steps 2 and 3 of §4.1 from the inner matrices C = <GU, U> and S = <GU, GU>.
+
+    The same arithmetic as core_matrices, for callers that hold C and S but not the
+    blocks (a row-sharded run sums them over its slabs).  Returns (A, B, M).
+    """
+    I = np.eye(C.shape[0])
     M = I + (tau * tau / 4.0) * S - (tau * tau / 4.0) * (C @ C)
     B = np.linalg.solve(M, I)
     A = (2.0 / tau) * (I - B + (tau / 2.0) * (C @ B))

@@ -47,6 +47,14 @@ class OpStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class OpShardStats(C.Structure):
+    _fields_ = [("slabs", C.c_int), ("halo_copies", C.c_longlong), ("halo_bytes", C.c_longlong),
+                ("reductions", C.c_longlong), ("reduction_bytes", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class OpnetConfig(C.Structure):
     _fields_ = [("N", C.c_int), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("p", C.c_int),
                 ("width", C.c_int * 3), ("stream", C.c_void_p)]
@@ -82,6 +90,7 @@ def lib():
         "op_gaussian_block": (i32, [C.c_ulonglong, C.c_longlong, i32, vp, vp]),
         "op_step": (i32, [vp, i32, P(OpStats)]),
         "op_solve": (i32, [vp, f64, i32, i32, P(OpStats)]),
+        "op_step_sharded": (i32, [vp, i32, i32, P(OpStats), P(OpShardStats)]),
         "op_energy": (i32, [vp, P(f64)]),
         "op_residual": (i32, [vp, P(f64)]),
         "op_get_U": (i32, [vp, P(f64)]),
@@ -266,6 +275,14 @@ class Solver:
         st = OpStats()
         check(lib().op_step(self._ctx, int(nsteps), C.byref(st)))
         return st.as_dict()
+
+    def step_sharded(self, nslab, nsteps=1):
+        """op_step_sharded: `nsteps` steps with the grid split into `nslab` slabs along its
+        slowest axis (FP64 contexts).  Returns (stats, communication) dicts."""
+        st, comm = OpStats(), OpShardStats()
+        check(lib().op_step_sharded(self._ctx, int(nslab), int(nsteps), C.byref(st),
+                                    C.byref(comm)))
+        return st.as_dict(), comm.as_dict()
 
     def solve(self, tol, max_steps, stop=OP_STOP_RESIDUAL, raise_on_max=True) -> dict:
         st = OpStats()

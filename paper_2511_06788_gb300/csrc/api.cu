@@ -180,18 +180,6 @@ op_status check_problem(const op_problem *pb) {
   return OP_OK;
 }
 
-double cg_rtol_for(op_ctx *c) {
-  if (c->pb.cg_rtol > 0.0) return c->pb.cg_rtol;
-  const double floor = c->prec == OP_FP64 ? 1e-13 : 1e-6;
-  double r = 0.1 * c->g_rel;
-  if (!(r < 1e-2)) r = 1e-2;
-  if (c->cg_cap > 0.0 && r > c->cg_cap) r = c->cg_cap;
-  if (r < floor) r = floor;
-  return r;
-}
-
-int cg_max_iter(op_ctx *c) { return c->pb.cg_max_iter > 0 ? c->pb.cg_max_iter : 2000; }
-
 template <typename T> op_status energy_impl(op_ctx *c) {
   OP_TRY(launch_quad<T>(c->g, (const T *)c->Vt, 0.0, (const T *)c->U, c->ld, c->part, c->dsc + 4,
                         c->st, c->dev_err));
@@ -790,6 +778,18 @@ op_status init_seeded(op_ctx **out, const op_problem *pb, const double *V,
 // lambda_p) / ((lambda_p + sigma) (lambda_{p+1} + sigma)), which is largest at
 // sigma ~ lambda_p - 2 lambda_1.  Changes below 10 % are skipped.  The previous
 // sigma and tau are returned for the energy guard.  Synchronises the context's stream.
+double opevo::cg_rtol_for(op_ctx *c) {
+  if (c->pb.cg_rtol > 0.0) return c->pb.cg_rtol;
+  const double floor = c->prec == OP_FP64 ? 1e-13 : 1e-6;
+  double r = 0.1 * c->g_rel;
+  if (!(r < 1e-2)) r = 1e-2;
+  if (c->cg_cap > 0.0 && r > c->cg_cap) r = c->cg_cap;
+  if (r < floor) r = floor;
+  return r;
+}
+
+int opevo::cg_max_iter(op_ctx *c) { return c->pb.cg_max_iter > 0 ? c->pb.cg_max_iter : 2000; }
+
 op_status opevo::retune_shift(op_ctx *c, double *prev_sigma, double *prev_tau) {
   if (c) c->rec_ok = false;  // its scratch or its result replaces a carried residual
   std::vector<double> lam(c->p);

@@ -58,4 +58,7 @@ namespace opevo {
 // Adaptive shift (op_problem.adapt_every): re-tune c->sigma and c->tau from the Ritz
 // values of the current U; the previous values are returned (api.cu).
 op_status retune_shift(op_ctx *c, double *prev_sigma, double *prev_tau);
+// Step-1 CG tolerance and iteration cap of the context's next step (api.cu).
+double cg_rtol_for(op_ctx *c);
+int cg_max_iter(op_ctx *c);
 }  // namespace opevo
