@@ -50,10 +50,11 @@
  *
  * Parameters are updated by Adam (Kingma and Ba, 2015), FP32 master weights.
  *
- * Conventions: as opevo.h.  The forward convolutions run on the tensor cores with
- * BF16 operands and FP32 accumulation (opnet_set_conv selects FP32 CUDA cores); the
- * rest is FP32 with FP32 accumulation inside a layer; the loss's p x p algebra is FP64.  Device pointers are 16-byte
- * aligned and caller-owned.  Calls are ordered on the network's stream and
+ * Conventions: as opevo.h.  The forward convolutions and the data gradients of layers
+ * with at most 128 input channels run on the tensor cores with BF16 operands and FP32
+ * accumulation (opnet_set_conv selects FP32 CUDA cores); the rest is FP32 with FP32
+ * accumulation inside a layer; the loss's p x p algebra is FP64.  Device pointers are
+ * 16-byte aligned and caller-owned.  Calls are ordered on the network's stream and
  * return after it has been synchronised, except where stated.
  */
 #ifndef OPNET_H
@@ -95,7 +96,10 @@ op_status opnet_get_params(opnet *net, float *theta_host, long long count);
  *   OPNET_CONV_BF16_TC  tcgen05 tensor cores, BF16 operands (activations and weights
  *                       rounded to nearest), FP32 accumulation; the default;
  *   OPNET_CONV_FP32     FP32 CUDA cores, FP32 accumulation.
- * The backward pass is FP32 either way.  OP_ERR_ARG for a NULL net or another kind. */
+ * In training, the data gradients of the layers (opnet_conv_dgrad's arithmetic) follow the
+ * same choice for layers with at most 128 input channels, and run on the FP32 CUDA cores
+ * otherwise; the weight gradients and the rest of the backward pass are FP32 either way.
+ * OP_ERR_ARG for a NULL net or another kind. */
 typedef enum { OPNET_CONV_FP32 = 0, OPNET_CONV_BF16_TC = 1 } opnet_conv_kind;
 op_status opnet_set_conv(opnet *net, int kind);
 
@@ -107,6 +111,17 @@ op_status opnet_set_conv(opnet *net, int kind);
  * frees a small scratch and synchronises `stream` (cudaStream_t, may be NULL). */
 op_status opnet_conv(int kind, const float *X, int N, int taps, int cin, int cout,
                      const float *W, const float *bias, float *Z, float *A, void *stream);
+
+/* The data gradient of that layer (the network's backward kernels, for kernel-level
+ * checks): dX = d loss / d X for dZ = d loss / d Z, i.e. the adjoint of the correlation,
+ *   dX[m][ci] = sum_t sum_co dZ[m - off_t][co] W[t cin + ci][co]   (zero outside the grid),
+ * computed as the forward convolution of dZ with the tap-reversed, transposed weights.
+ * dZ [N^3][cout] (16-byte aligned), W [taps * cin][cout], dX [N^3][cin], FP32 device
+ * arrays; taps 27 or 1; cin, cout <= 512, N <= 512.  OPNET_CONV_BF16_TC: on the tensor
+ * cores (BF16 dZ and W, FP32 accumulation) when cin <= 128, else as OPNET_CONV_FP32 (FP32
+ * CUDA cores).  Allocates and frees a small scratch and synchronises `stream`. */
+op_status opnet_conv_dgrad(int kind, const float *dZ, int N, int taps, int cin, int cout,
+                           const float *W, float *dX, void *stream);
 
 /* Y = net(V): V is N^3 FP64 values (device), Y is N^3 x p FP32 (device, ld = p). */
 op_status opnet_forward(opnet *net, const double *V_dev, float *Y_dev);

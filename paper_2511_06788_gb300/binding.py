@@ -138,6 +138,7 @@ def lib():
         "opnet_get_params": (i32, [vp, P(C.c_float), C.c_longlong]),
         "opnet_set_conv": (i32, [vp, i32]),
         "opnet_conv": (i32, [i32, vp, i32, i32, i32, i32, vp, vp, vp, vp, vp]),
+        "opnet_conv_dgrad": (i32, [i32, vp, i32, i32, i32, i32, vp, vp, vp]),
         "opnet_forward": (i32, [vp, vp, vp]),
         "opnet_infer": (i32, [vp, vp, vp]),
         "opnet_loss_grad": (i32, [vp, vp, vp, f64, P(f64), P(C.c_float), C.c_longlong]),
@@ -597,6 +598,19 @@ def net_conv(kind, X, N, taps, W, bias=None, stream=None):
                            C.c_void_p(Z.data_ptr()), C.c_void_p(A.data_ptr()),
                            _stream_ptr(stream)))
     return Z, A
+
+
+def net_conv_dgrad(kind, dZ, N, taps, W, stream=None):
+    """The data gradient of one layer (opnet_conv_dgrad): dZ (N^3 x cout) and W
+    (taps * cin x cout) float32 CUDA tensors; returns dX (N^3 x cin)."""
+    import torch
+    n, cout = dZ.shape
+    cin = W.shape[0] // taps
+    dX = torch.empty(n, cin, dtype=torch.float32, device=dZ.device)
+    check(lib().opnet_conv_dgrad(Net.CONV[kind], C.c_void_p(dZ.data_ptr()), int(N), int(taps),
+                                 int(cin), int(cout), C.c_void_p(W.data_ptr()),
+                                 C.c_void_p(dX.data_ptr()), _stream_ptr(stream)))
+    return dX
 
 
 class Net:

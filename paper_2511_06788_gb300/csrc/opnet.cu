@@ -1,11 +1,13 @@
 // Learned warm start: the 3-level convolutional U-Net of opnet.h, its subspace
 // loss, hand-written backward pass and Adam, all on the device.
 //
-// Every convolution is an implicit GEMM on FP32 CUDA cores:
+// Every convolution is an implicit GEMM, on the tensor cores (conv_tc.cu, BF16 operands,
+// the default for the forward and for the data gradients of layers with at most 128
+// input channels) or on FP32 CUDA cores (k_conv below):
 //   forward  out[m][co] = b[co] + sum_k A[m][k] W[k][co],  A[m][t Cin + ci] = X[m + off_t][ci]
 //   dgrad    the same kernel on dZ with the tap-reversed, transposed weights
 //            (dX[m][ci] = sum_t sum_co dZ[m - off_t][co] W[t][ci][co]);
-//   wgrad    dW[k][co] = sum_m A[m][k] dZ[m][co] (split over point chunks, partials
+//   wgrad    (FP32 CUDA cores) dW[k][co] = sum_m A[m][k] dZ[m][co] (split over point chunks, partials
 //            summed in a fixed order), with a row of ones appended to A so that
 //            the same pass yields db = sum_m dZ[m] as row K of the (K + 1) x Cout
 //            block that W and b form in the parameter vector.
@@ -586,6 +588,40 @@ op_status forward(opnet *net, const double *V) {
   return OP_OK;
 }
 
+// Data gradient of a convolution layer, the adjoint of its correlation:
+//   dX[m][ci] = sum_t sum_co dZ[m - off_t][co] W[t cin + ci][co],
+// as the forward convolution kernel on dZ with the tap-reversed, transposed weights
+// (k_flip into Wf, taps * cin * cout floats of scratch).  OPNET_CONV_BF16_TC runs it on the
+// tensor cores when cin <= 128 (the kernel's output-channel limit; BF16 operands, FP32
+// accumulation), otherwise it runs on the FP32 CUDA cores.  tc_ws: scratch of
+// conv_tc_scratch_bytes(taps, cout, cin) bytes for the tensor-core form.
+op_status conv_dgrad(int kind, const float *dZ, int N, int taps, int cin, int cout,
+                     const float *W, float *Wf, float *dX, void *tc_ws, size_t tc_bytes, int *err,
+                     cudaStream_t st) {
+  const long long K = (long long)taps * cin;
+  k_flip<<<ew_blocks(K * cout), 256, 0, st>>>(W, taps, cin, cout, Wf);
+  count_launch();
+  OP_LAUNCH("k_flip");
+  if (kind == OPNET_CONV_BF16_TC && cin <= 128)
+    return conv_bf16_tc(dZ, N, taps, cout, cin, Wf, nullptr, dX, nullptr, tc_ws, tc_bytes, err,
+                        st);
+  ConvArgs a;
+  a.X = dZ;
+  a.W = Wf;
+  a.bias = nullptr;
+  a.Z = dX;
+  a.A = nullptr;
+  a.N = N;
+  a.taps = taps;
+  a.cin = cout;
+  a.cout = cin;
+  const long long n = (long long)N * N * N;
+  k_conv<<<dim3((unsigned)((n + CM - 1) / CM), (unsigned)((cin + CN - 1) / CN)), 256, 0, st>>>(a);
+  count_launch();
+  OP_LAUNCH("k_conv");
+  return OP_OK;
+}
+
 // Gradient of layer i's parameters from its input X and dZ; dX (if not null) = d loss / d X.
 op_status back_layer(opnet *net, int i, const float *X, const float *dZ, float *dX) {
   const Layer &l = net->L[i];
@@ -614,12 +650,9 @@ op_status back_layer(opnet *net, int i, const float *X, const float *dZ, float *
   k_reduce_parts<<<ew_blocks(cnt), 256, 0, st>>>(net->part, splits, cnt, net->grad + l.woff);
   count_launch();
   OP_LAUNCH("k_wgrad");
-  if (dX) {
-    k_flip<<<ew_blocks((long long)K * l.cout), 256, 0, st>>>(net->theta + l.woff, l.taps, l.cin,
-                                                               l.cout, net->Wf);
-    count_launch();
-    OP_TRY(conv(net, dZ, l.grid, l.taps, l.cout, l.cin, net->Wf, nullptr, dX, nullptr));
-  }
+  if (dX)
+    OP_TRY(conv_dgrad(net->conv_kind, dZ, l.grid, l.taps, l.cin, l.cout, net->theta + l.woff,
+                      net->Wf, dX, net->conv_ws, net->conv_ws_bytes, net->dev_err, st));
   return OP_OK;
 }
 
@@ -811,10 +844,15 @@ op_status opnet_create(opnet **out, const opnet_config *cfg) {
     // the tensor-core convolutions (the default): scratch for the widest layer's weights
     net->conv_kind = OPNET_CONV_BF16_TC;
     net->conv_ws_bytes = 0;
-    for (int i = 0; i < kLayers; ++i)
-      net->conv_ws_bytes = std::max(net->conv_ws_bytes,
-                                    conv_tc_scratch_bytes(net->L[i].taps, net->L[i].cin,
-                                                          net->L[i].cout));
+    for (int i = 0; i < kLayers; ++i) {
+      const Layer &l = net->L[i];
+      net->conv_ws_bytes =
+          std::max(net->conv_ws_bytes, conv_tc_scratch_bytes(l.taps, l.cin, l.cout));
+      // the tensor-core data gradient: the same kernel with cin and cout exchanged
+      if (l.cin <= 128)
+        net->conv_ws_bytes =
+            std::max(net->conv_ws_bytes, conv_tc_scratch_bytes(l.taps, l.cout, l.cin));
+    }
     s = net_alloc(net, &net->conv_ws, net->conv_ws_bytes);
   }
   if (s == OP_OK) {
@@ -948,6 +986,39 @@ op_status opnet_conv(int kind, const float *X, int N, int taps, int cin, int cou
   cudaFree(ws);
   if (s == OP_OK && h) {
     set_error("opnet_conv: a bounded device wait gave up");
+    s = OP_ERR_TIMEOUT;
+  }
+  return s;
+}
+
+op_status opnet_conv_dgrad(int kind, const float *dZ, int N, int taps, int cin, int cout,
+                           const float *W, float *dX, void *stream) {
+  if (!dZ || !W || !dX || N < 1 || N > 512 || (taps != 1 && taps != 27) || cin < 1 ||
+      cin > 512 || cout < 1 || cout > 512 ||
+      (kind != OPNET_CONV_FP32 && kind != OPNET_CONV_BF16_TC) || ((uintptr_t)dZ & 15)) {
+    set_error("opnet_conv_dgrad: bad arguments");
+    return OP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t wf = ((size_t)taps * cin * cout * sizeof(float) + 255) / 256 * 256;
+  const size_t wb = conv_tc_scratch_bytes(taps, cout, cin);
+  void *ws = nullptr;
+  OP_CUDA(cudaMalloc(&ws, wf + wb + 256));
+  float *Wf = (float *)ws;
+  void *tc = (char *)ws + wf;
+  int *err = (int *)((char *)ws + wf + wb);
+  auto ck = [](cudaError_t e, const char *what) {
+    return e == cudaSuccess ? OP_OK : cuda_status(e, what);
+  };
+  op_status s = ck(cudaMemsetAsync(err, 0, sizeof(int), st), "opnet_conv_dgrad: memset");
+  if (s == OP_OK) s = conv_dgrad(kind, dZ, N, taps, cin, cout, W, Wf, dX, tc, wb, err, st);
+  int h = 0;
+  if (s == OP_OK) s = ck(cudaStreamSynchronize(st), "opnet_conv_dgrad");
+  if (s == OP_OK)
+    s = ck(cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost), "opnet_conv_dgrad");
+  cudaFree(ws);
+  if (s == OP_OK && h) {
+    set_error("opnet_conv_dgrad: a bounded device wait gave up");
     s = OP_ERR_TIMEOUT;
   }
   return s;

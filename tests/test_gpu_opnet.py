@@ -17,7 +17,10 @@ The tensor-core convolutions (the default) round activations and weights to BF16
 accumulate in FP32.  A layer is checked against the oracle's convolution of the
 BF16-rounded operands (then only the FP32 accumulation differs: K 2^-23 sum |x w| per
 output); a whole forward pass against the FP32 one (BF16 rounding, 2^-9 per operand,
-through 11 layers).
+through 11 layers).  A layer's data gradient (opnet_conv_dgrad, the same kernel on dZ with
+the tap-reversed, transposed weights) is checked the same way against the oracle's
+adjoint, and the whole loss gradient with tensor-core forward and data gradients against
+the FP32 one.
 """
 import numpy as np
 import pytest
@@ -228,6 +231,62 @@ def test_tensor_core_conv_rejects_bad_arguments():
     W = torch.zeros(27 * 8, 200, device=DEV)          # more than 128 output channels
     with pytest.raises(pkg.OpError):
         pkg.binding.net_conv("bf16_tc", X, 4, 27, W)
+
+
+@pytest.mark.parametrize("kind", ["fp32", "bf16_tc"])
+@pytest.mark.parametrize("N,taps,cin,cout", [(10, 27, 4, 24), (9, 27, 24, 48), (8, 27, 144, 48),
+                                             (11, 1, 24, 64), (7, 27, 96, 96), (5, 27, 6, 10)])
+def test_layer_data_gradient_matches_oracle(kind, N, taps, cin, cout):
+    """opnet_conv_dgrad against the oracle's adjoint (conv3_backward): on the tensor cores
+    (cin <= 128) with BF16-rounded dZ and W, within the FP32 accumulation bound of
+    taps x cout terms; on the FP32 CUDA cores (and for cin > 128) with the unrounded ones."""
+    rng = np.random.default_rng(N * 100 + cin + 7 * cout)
+    n = N ** 3
+    dZ = rng.standard_normal((n, cout)).astype(np.float32)
+    W = (rng.standard_normal((taps * cin, cout)) / np.sqrt(taps * cin)).astype(np.float32)
+    dX = pkg.binding.net_conv_dgrad(kind, torch.from_numpy(dZ).to(DEV), N, taps,
+                                    torch.from_numpy(W).to(DEV)).double().cpu().numpy()
+    assert dX.shape == (n, cin)
+    tc = kind == "bf16_tc" and cin <= 128
+    dZr, Wr = (bf16(dZ), bf16(W)) if tc else (dZ.astype(np.float64), W.astype(np.float64))
+    X0 = np.zeros((n, cin))
+    if taps == 27:
+        ref = unet.conv3_backward(X0, N, Wr.reshape(27, cin, cout), dZr)[0]
+        mag = unet.conv3_backward(X0, N, np.abs(Wr).reshape(27, cin, cout), np.abs(dZr))[0]
+    else:
+        ref = dZr @ Wr.T
+        mag = np.abs(dZr) @ np.abs(Wr).T
+    tol = (taps * cout + 2) * 2.0 ** -23 * mag + 1e-30
+    assert np.all(np.abs(dX - ref) <= tol), float((np.abs(dX - ref) / tol).max())
+    if tc and taps == 27:
+        # the operands really were rounded: the unrounded adjoint differs by far more
+        exact = unet.conv3_backward(X0, N, W.astype(np.float64).reshape(27, cin, cout),
+                                    dZ.astype(np.float64))[0]
+        assert np.abs(exact - ref).max() > 100 * np.abs(dX - ref).max()
+
+
+def test_layer_data_gradient_rejects_bad_arguments():
+    dZ = torch.zeros(64, 8, device=DEV)
+    with pytest.raises(pkg.OpError):
+        pkg.binding.net_conv_dgrad("bf16_tc", dZ, 4, 9, torch.zeros(9 * 8, 8, device=DEV))
+
+
+def test_tensor_core_gradient_close_to_fp32_gradient():
+    """The whole network's loss gradient with the tensor-core forward and data gradients
+    against the FP32 one: BF16 rounding (2^-9 per operand) through the 11 forward and up
+    to 11 data-gradient layers, so agreement to a few percent per layer, not to FP32."""
+    N, widths, p = 16, (8, 16, 24), 16
+    net, theta, P, V = setup(N, widths, p, seed=2, conv="bf16_tc")
+    Us = torch.from_numpy(target(P.n, p, 5)).to(DEV, torch.float32)
+    loss_tc, g_tc = net.loss_grad(V, Us, GAMMA)
+    net.set_conv("fp32")
+    loss_32, g_32 = net.loss_grad(V, Us, GAMMA)
+    net.close()
+    assert loss_tc == pytest.approx(loss_32, rel=2e-2)
+    table = unet.layer_table(*widths, p)
+    for (name, *_), sl in zip(table, layer_slices(table)):
+        rel = np.linalg.norm(g_tc[sl] - g_32[sl]) / np.linalg.norm(g_32[sl])
+        assert 1e-6 < rel < 0.1, (name, rel)
 
 
 def test_tensor_core_forward_close_to_fp32_forward():
