@@ -269,11 +269,8 @@ op_status conv_bf16_tc(const float *X, int N, int taps, int cin, int cout, const
       W, a.K, cout, a.Kp, a.coutp, (uint16_t *)scratch);
   count_launch();
   OP_LAUNCH("k_conv_wt");
-  static int attr_set = 0;
-  if (!attr_set) {
-    OP_CUDA(cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kCSmem));
-    attr_set = 1;
-  }
+  // per device, so set on every call (cheap)
+  OP_CUDA(cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kCSmem));
   const long long n = (long long)N * N * N;
   k_conv_tc<<<(unsigned)((n + kCM - 1) / kCM), 256, kCSmem, st>>>(a);
   count_launch();

@@ -325,12 +325,20 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
 }
 
 
+// Resident CTAs per SM of the kernel for MODE on the current device; the first call on a
+// device also sets the kernel's shared-memory attribute there (attributes are per device).
 template <int MODE>
 int resident_ctas() {
-  static int cached = -1;
+  constexpr int kMaxDev = 64;
+  static int cached[kMaxDev] = {};
   static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    dev = 0;
+  }
   std::lock_guard<std::mutex> lk(mu);
-  if (cached < 0) {
+  if (cached[dev] < 1) {
     constexpr int NS = Slot<MODE>::ns;
     const int bytes = smem_bytes<MODE, NS>();
     cudaFuncSetAttribute(k_cg_tma<MODE, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -339,9 +347,9 @@ int resident_ctas() {
                                                       bytes) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
-    cached = per_sm;
+    cached[dev] = per_sm;
   }
-  return cached;
+  return cached[dev];
 }
 
 // Geometry and persistent grid shared by every mode (so that all of them write the
