@@ -25,8 +25,9 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\**\s*(op_[A-Za-z_0-9]*)\s*\(",
-                            src, flags=re.M)
+        names += re.findall(
+            r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\**\s*((?:op|opnet)_[A-Za-z_0-9]*)\s*\(",
+            src, flags=re.M)
     return sorted(set(names))
 
 
@@ -48,6 +49,60 @@ def test_binding_covers_every_declared_symbol(lib):
     src = open(binding.__file__).read()
     missing = [n for n in declared_functions() if f'"{n}"' not in src]
     assert not missing, missing
+
+
+def test_header_declares_the_network_api():
+    names = declared_functions()
+    for required in ("opnet_create", "opnet_forward", "opnet_infer", "opnet_loss_grad",
+                     "opnet_train_step", "opnet_conv", "opnet_conv_dgrad", "opnet_destroy"):
+        assert required in names
+
+
+STRUCTS = {
+    # C struct -> (binding class name, fields)
+    "op_problem": ("OpProblem", ["dim", "shape", "lo", "hi", "p", "sigma", "tau", "prec",
+                                 "cg_rtol", "cg_max_iter", "check_every", "adapt_every",
+                                 "cg_precond", "flow", "fp64_gemm", "step1"]),
+    "op_stats": ("OpStats", ["steps", "last_cg_iters", "cg_iters", "energy", "err_E",
+                             "residual", "g_residual", "orth", "sigma", "tau", "ms"]),
+    "op_shard_stats": ("OpShardStats", ["slabs", "halo_copies", "halo_bytes", "reductions",
+                                        "reduction_bytes"]),
+    "opnet_config": ("OpnetConfig", ["N", "lo", "hi", "p", "width", "stream"]),
+}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """sizeof and offsetof of every struct the binding mirrors, from the C compiler on the
+    headers themselves, equal the ctypes layout (a field added to one side only fails)."""
+    import shutil
+    import subprocess
+    from paper_2511_06788_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "opevo.h"',
+             '#include "opnet.h"', "int main(void) {"]
+    for st, (_, fields) in STRUCTS.items():
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fields:
+            lines.append(f'  printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        st, key, val = line.split()
+        got[(st, key)] = int(val)
+    for st, (cls_name, fields) in STRUCTS.items():
+        cls = getattr(binding, cls_name)
+        assert [f for f, _ in cls._fields_] == fields, st
+        assert C.sizeof(cls) == got[(st, "size")], st
+        for f in fields:
+            assert getattr(cls, f).offset == got[(st, f)], (st, f)
 
 
 def test_version_string(lib):
