@@ -1,4 +1,4 @@
-"""The row-sharded step on CPU ranks (gloo, world sizes 2 and 3).
+"""The row-sharded step on CPU ranks (gloo, world sizes 2, 3 and 4).
 
 Each rank owns a slab of whole z planes of the grid (the split op_step_sharded uses:
 sizes differ by at most one plane, the first slabs take the extra planes) plus one halo
@@ -174,7 +174,8 @@ def _worker(rank, ws, port, out, shape, p, nsteps, jacobi):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("ws,jacobi", [(2, True), (3, False)], ids=["ws2_jacobi", "ws3_cg"])
+@pytest.mark.parametrize("ws,jacobi", [(2, True), (3, False), (4, True)],
+                         ids=["ws2_jacobi", "ws3_cg", "ws4_jacobi"])
 def test_row_sharded_step_on_gloo_ranks_matches_the_unsplit_step(ws, jacobi):
     shape, p, nsteps = (9, 8, 11), 5, 3
     port = free_port()
